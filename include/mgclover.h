@@ -1,0 +1,209 @@
+/*
+ * mgclover.h -- C ABI of a GB300 (sm_103a) multigrid solver for the
+ * even-odd preconditioned Wilson-clover Dirac equation
+ *
+ *     [D(U) + m] psi = eta                 (Osborn et al., Lattice 2010, Eq. 1)
+ *
+ * solved by flexible GCR on the reduced even-odd system, preconditioned by a
+ * recursive adaptive-multigrid K-cycle whose coarse operator is the Galerkin
+ * projection R D_p P of the full even-odd preconditioned operator
+ * (section "Red-black preconditioning"; section "Implementation").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status: MG_OK (0) or a negative MG_ERR_*.
+ *   No C++ exception crosses this boundary.  mg_strerror() names a status.
+ * - A context owns all of its internal device memory (gauge and clover
+ *   fields, null vectors, prolongators, coarse links, Krylov spaces).  It is
+ *   bound to one CUDA device and one stream, is single-stream and is not
+ *   thread-safe.  Calls return after the stream has drained (the results are
+ *   visible to the caller on any stream).
+ * - Caller buffers are plain pointers.  `where` says whether they are host
+ *   (MG_HOST) or device (MG_DEVICE) memory; the library never keeps them.
+ * - Lattice dims are {Lx, Ly, Lz, Lt}; all four must be even (even-odd
+ *   preconditioning) and x is the fastest index.
+ * - Fine vectors (spinors): complex128, layout [rhs][t][z][y][x][spin 4][colour 3].
+ * - Gauge field: complex128, layout [t][z][y][x][mu 4][a 3][b 3], mu = x,y,z,t;
+ *   U_mu(x) is the link from x to x+mu.
+ * - Coarse vectors of level l >= 1: complex128, layout
+ *   [rhs][t_c][z_c][y_c][x_c][chirality 2][Nv_{l-1}].
+ * - Gamma matrices: DeGrand-Rossi chiral basis, gamma_5 = diag(1,1,-1,-1);
+ *   chirality of a spin index is spin/2.  Fermion boundary conditions are
+ *   periodic in x, y, z and antiperiodic in t; the gauge field is periodic.
+ * - The operator (the paper does not write it out; this is the reading used):
+ *     D psi(x) = A(x) psi(x)
+ *              - 1/2 sum_mu [(1-gamma_mu) U_mu(x) psi(x+mu) + (1+gamma_mu) U_mu(x-mu)^dag psi(x-mu)]
+ *     A(x) = (4 + m0) + csw (i/4) sum_{mu != nu} sigma_{mu nu} F_{mu nu}(x),
+ *   sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu], F = (Q - Q^dag)/8 made traceless,
+ *   Q the sum of the four plaquette leaves.  D_ee = A_e, D_oo = A_o.
+ * - Working precision is internal: FP64 for the outer GCR, FP32 for the
+ *   multigrid preconditioner, FP32/FP16/BF16 storage for prolongators and
+ *   coarse links (mg_params.storage).  The ABI always exchanges complex128.
+ */
+#ifndef MGCLOVER_H
+#define MGCLOVER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MG_API __attribute__((visibility("default")))
+#else
+#define MG_API
+#endif
+
+#define MG_MAX_LEVELS 4
+
+enum mg_status {
+  MG_OK = 0,
+  MG_ERR_ARG = -1,             /* null pointer, bad enum, nrhs < 1, tol <= 0 ...      */
+  MG_ERR_DIMS = -2,            /* odd extent, block not dividing a lattice extent,   */
+                               /* even-odd requested on a level with an odd extent   */
+  MG_ERR_NV = -3,              /* Nv < 1, Nv too large for the block, Nv unsupported */
+  MG_ERR_STATE = -4,           /* call order: e.g. solve before gauge/mass/setup      */
+  MG_ERR_GS_BREAKDOWN = -5,    /* null vectors locally linearly dependent in a block */
+  MG_ERR_SINGULAR_CLOVER = -6, /* a clover block (or coarse X) is numerically singular */
+  MG_ERR_NOT_CONVERGED = -7,   /* psi holds the best iterate; info has its residual  */
+  MG_ERR_NAN = -8,             /* NaN/Inf in an input or in a Krylov scalar           */
+  MG_ERR_CUDA = -9,            /* a CUDA runtime call failed                          */
+  MG_ERR_ALLOC = -10           /* device or pinned host allocation failed             */
+};
+
+enum mg_where { MG_HOST = 0, MG_DEVICE = 1 };
+
+/* Operators for mg_apply.  `level` selects the lattice (0 = fine). */
+enum mg_op {
+  MG_OP_D = 0,          /* full D (fine) or D_hat (coarse), whole lattice                 */
+  MG_OP_DP = 1,         /* D_p = D diag(M)^{-1} = 1 + H M^{-1}, whole lattice              */
+  MG_OP_DR = 2,         /* D_r = 1 - H_eo M_o^{-1} H_oe M_e^{-1}; reads the even sites of  */
+                        /* `in`, writes even sites of `out` and zeros its odd sites        */
+  MG_OP_BR = 3,         /* b_r = b_e - H_eo M_o^{-1} b_o (odd sites of out set to zero)    */
+  MG_OP_M = 4,          /* site-local M (clover A on the fine level, X on coarse levels)    */
+  MG_OP_MINV = 5,       /* M^{-1}                                                          */
+  MG_OP_HOP = 6,        /* hopping term H alone                                            */
+  MG_OP_R = 7,          /* restriction R = P^dag: level l vector -> level l+1 vector       */
+  MG_OP_P = 8           /* prolongation P: level l+1 vector -> level l vector              */
+};
+
+enum mg_prec { MG_FP64 = 0, MG_FP32 = 1 };
+enum mg_storage { MG_STORE_FP32 = 0, MG_STORE_FP16 = 1, MG_STORE_BF16 = 2 };
+enum mg_mode { MG_MODE_MG = 0, MG_MODE_EO_GCR = 1 };
+enum mg_coarse_op { MG_COARSE_DP = 0, MG_COARSE_D = 1 };
+
+/* Multigrid parameters (section "Implementation"; section "Setup procedure").
+ * Arrays are indexed by the level they map FROM: block[l], nv[l] build P_l
+ * from level l to level l+1. */
+typedef struct {
+  int levels;                     /* total levels including the fine one (1..MG_MAX_LEVELS)      */
+  int block[MG_MAX_LEVELS][4];    /* aggregation block {bx,by,bz,bt} of P_l                      */
+  int nv[MG_MAX_LEVELS];          /* null vectors of P_l (coarse dof per site = 2*nv[l])         */
+  int setup_iters;                /* inverse-iteration passes per null vector (cap)              */
+  int setup_inner;                /* GCR iterations on D_p per pass                              */
+  double setup_rq_tol;            /* stop a vector when |dRQ| < setup_rq_tol * RQ                */
+  int nu_pre, nu_post;            /* minimal-residual smoothing steps on D_r                     */
+  double tol_coarse;              /* relative residual target of every coarse GCR (paper: ~0.1) */
+  int maxit_coarse;               /* iteration cap of every coarse GCR                           */
+  int restart_coarse;             /* GCR restart length on coarse levels                         */
+  int restart_fine;               /* GCR restart length of the outer solver                      */
+  int maxit_fine;                 /* outer iteration cap                                         */
+  int storage;                    /* mg_storage of prolongators and coarse links                 */
+  int coarse_op;                  /* mg_coarse_op: Galerkin projection of D_p (paper) or of D    */
+  uint64_t seed;                  /* Philox4x32-10 key of the setup's random start vectors       */
+} mg_params;
+
+typedef struct {
+  double setup_ms;                          /* wall time of mg_setup                          */
+  int vectors[MG_MAX_LEVELS];               /* null vectors built per transfer                */
+  int passes[MG_MAX_LEVELS];                /* inverse-iteration passes summed over vectors   */
+  double rq_last[MG_MAX_LEVELS];            /* Rayleigh quotient of the last vector found     */
+  int coarse_sites[MG_MAX_LEVELS];          /* sites of the coarse lattice of each transfer   */
+} mg_setup_info;
+
+typedef struct {
+  int outer_iterations;                     /* outer GCR iterations (summed over rhs)         */
+  int restarts;                             /* outer restarts (true-residual recomputations)  */
+  long long coarse_iterations[MG_MAX_LEVELS]; /* GCR iterations run on each coarse level    */
+  double true_residual;                     /* max over rhs of ||eta - D psi|| / ||eta||      */
+  double solve_ms;                          /* wall time of the call                          */
+  long long dslash_launches;                /* fine hopping-term launches in the call         */
+} mg_solve_info;
+
+/* Name of a status code (static string). */
+MG_API const char* mg_strerror(int status);
+
+/* Detail of the last failed call on this thread (empty after a success).
+ * Valid until the next call on the same thread. */
+MG_API const char* mg_last_error(void);
+
+/* Fill `p` with the defaults: 2 levels, 4^4 blocks, Nv = 24, 20 passes of 8
+ * GCR iterations, RQ tolerance 0.05, nu_post = 4, coarse tolerance 0.1,
+ * coarse restart 32 / cap 50, outer restart 16 / cap 500, FP32 storage,
+ * Galerkin projection of D_p, seed 3. */
+MG_API int mg_default_params(mg_params* p);
+
+/* Create a context for a lattice of `dims` on CUDA device `device`; kernels
+ * run on `cuda_stream` (a cudaStream_t, NULL = legacy default stream).
+ * Errors: MG_ERR_ARG, MG_ERR_DIMS (an extent is odd or < 2), MG_ERR_CUDA. */
+MG_API int mg_create(void** ctx_out, const int dims[4], int device, void* cuda_stream);
+
+/* Release the context and all device memory it owns.  NULL is a no-op. */
+MG_API int mg_destroy(void* ctx);
+
+/* Copy in the gauge field (layout above).  Invalidates the clover field and
+ * any multigrid setup. */
+MG_API int mg_load_gauge(void* ctx, const void* U, int where);
+
+/* Set the clover coefficient csw and the bare mass m0 and build A and A^{-1}
+ * in FP64 (plus the FP32 copies the preconditioner uses) from the loaded
+ * gauge field.  Invalidates the multigrid setup.  Errors: MG_ERR_STATE (no
+ * gauge), MG_ERR_SINGULAR_CLOVER (a 6x6 chiral block has a pivot below
+ * 1e-12 of its largest entry). */
+MG_API int mg_set_clover(void* ctx, double csw, double m0);
+
+/* Set multigrid parameters (copied).  Invalidates the setup.  Errors:
+ * MG_ERR_ARG, MG_ERR_DIMS (a block does not divide its lattice, or a level
+ * below the coarsest has an odd extent), MG_ERR_NV. */
+MG_API int mg_set_params(void* ctx, const mg_params* p);
+
+/* Run the setup ("Setup procedure"): for every transfer l, find nv[l]
+ * near-null vectors of level l's D_p by inverse iteration (unless injected by
+ * mg_set_null_vectors), split them by chirality, block-orthonormalise them
+ * into P_l, and build the Galerkin coarse links and their site inverses.
+ * `info` may be NULL.  Errors: MG_ERR_STATE, MG_ERR_GS_BREAKDOWN,
+ * MG_ERR_SINGULAR_CLOVER (a coarse X block), MG_ERR_CUDA. */
+MG_API int mg_setup(void* ctx, mg_setup_info* info);
+
+/* Inject (set) or read (get) the nv raw null vectors of transfer `level`:
+ * complex128 [k][level-l lattice vector layout].  Injected vectors replace
+ * the inverse iteration of that level at the next mg_setup (used by tests
+ * and to reuse a setup).  get returns the vectors of the last setup. */
+MG_API int mg_set_null_vectors(void* ctx, int level, const void* V, int nv, int where);
+MG_API int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where);
+
+/* Solve D psi = eta for nrhs right-hand sides (layout above) to
+ * ||eta - D psi|| / ||eta|| <= tol, in MG_MODE_MG (multigrid-preconditioned
+ * FGCR; needs mg_setup) or MG_MODE_EO_GCR (plain FP64 even-odd GCR).  `info`
+ * may be NULL.  Errors: MG_ERR_STATE, MG_ERR_ARG, MG_ERR_NAN,
+ * MG_ERR_NOT_CONVERGED (psi holds the best iterate), MG_ERR_CUDA. */
+MG_API int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
+             mg_solve_info* info);
+
+/* Apply operator `op` (enum mg_op) of level `level` to nrhs vectors of that
+ * level (for MG_OP_R the output is a level+1 vector, for MG_OP_P the input
+ * is).  `prec` selects FP64 or FP32 arithmetic on the fine level; coarse
+ * levels compute in FP32 from their storage format.  Coarse levels and R/P
+ * need mg_setup.  Errors: MG_ERR_ARG, MG_ERR_STATE, MG_ERR_DIMS (MG_OP_DR or
+ * MG_OP_BR on a level with an odd extent), MG_ERR_CUDA. */
+MG_API int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, int prec, int where);
+
+/* Lattice size of level `level` after setup (dims_out[4] = {Lx,Ly,Lz,Lt})
+ * and its dof per site (12 on the fine level, 2*nv[level-1] on coarse ones). */
+MG_API int mg_level_info(void* ctx, int level, int dims_out[4], int* ndof_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGCLOVER_H */

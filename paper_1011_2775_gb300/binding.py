@@ -1,0 +1,225 @@
+"""ctypes binding of libmgclover (the C ABI in ``include/mgclover.h``).
+
+Argument marshalling only: every computation runs in the CUDA library.  The
+functions carry the C names; buffers may be numpy arrays (host memory,
+``MG_HOST``) or torch tensors (CUDA tensors are passed as device pointers,
+``MG_DEVICE``; CPU tensors as host pointers).  All buffers are complex128 and
+C-contiguous in the layouts the header documents.
+
+If ``libmgclover.so`` has not been built, loading raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmgclover.so")
+
+MG_MAX_LEVELS = 4
+# status
+MG_OK, MG_ERR_ARG, MG_ERR_DIMS, MG_ERR_NV, MG_ERR_STATE = 0, -1, -2, -3, -4
+MG_ERR_GS_BREAKDOWN, MG_ERR_SINGULAR_CLOVER, MG_ERR_NOT_CONVERGED, MG_ERR_NAN = -5, -6, -7, -8
+MG_ERR_CUDA, MG_ERR_ALLOC = -9, -10
+# where
+MG_HOST, MG_DEVICE = 0, 1
+# operators
+MG_OP_D, MG_OP_DP, MG_OP_DR, MG_OP_BR, MG_OP_M, MG_OP_MINV, MG_OP_HOP, MG_OP_R, MG_OP_P = range(9)
+MG_FP64, MG_FP32 = 0, 1
+MG_STORE_FP32, MG_STORE_FP16, MG_STORE_BF16 = 0, 1, 2
+MG_MODE_MG, MG_MODE_EO_GCR = 0, 1
+MG_COARSE_DP, MG_COARSE_D = 0, 1
+
+EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
+            "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
+            "mg_solve", "mg_apply", "mg_level_info"]
+
+
+class mg_params(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int),
+                ("block", (ctypes.c_int * 4) * MG_MAX_LEVELS),
+                ("nv", ctypes.c_int * MG_MAX_LEVELS),
+                ("setup_iters", ctypes.c_int),
+                ("setup_inner", ctypes.c_int),
+                ("setup_rq_tol", ctypes.c_double),
+                ("nu_pre", ctypes.c_int),
+                ("nu_post", ctypes.c_int),
+                ("tol_coarse", ctypes.c_double),
+                ("maxit_coarse", ctypes.c_int),
+                ("restart_coarse", ctypes.c_int),
+                ("restart_fine", ctypes.c_int),
+                ("maxit_fine", ctypes.c_int),
+                ("storage", ctypes.c_int),
+                ("coarse_op", ctypes.c_int),
+                ("seed", ctypes.c_uint64)]
+
+
+class mg_setup_info(ctypes.Structure):
+    _fields_ = [("setup_ms", ctypes.c_double),
+                ("vectors", ctypes.c_int * MG_MAX_LEVELS),
+                ("passes", ctypes.c_int * MG_MAX_LEVELS),
+                ("rq_last", ctypes.c_double * MG_MAX_LEVELS),
+                ("coarse_sites", ctypes.c_int * MG_MAX_LEVELS)]
+
+
+class mg_solve_info(ctypes.Structure):
+    _fields_ = [("outer_iterations", ctypes.c_int),
+                ("restarts", ctypes.c_int),
+                ("coarse_iterations", ctypes.c_longlong * MG_MAX_LEVELS),
+                ("true_residual", ctypes.c_double),
+                ("solve_ms", ctypes.c_double),
+                ("dslash_launches", ctypes.c_longlong)]
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {mg_strerror(status)} ({status}): {mg_last_error()}")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1011_2775_gb300.build.build() "
+                               "(nvcc, sm_103a); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.mg_strerror.restype = ctypes.c_char_p
+        L.mg_strerror.argtypes = [ip]
+        L.mg_last_error.restype = ctypes.c_char_p
+        L.mg_last_error.argtypes = []
+        sig = {
+            "mg_default_params": [ctypes.POINTER(mg_params)],
+            "mg_create": [ctypes.POINTER(vp), ctypes.POINTER(ip), ip, vp],
+            "mg_destroy": [vp],
+            "mg_load_gauge": [vp, vp, ip],
+            "mg_set_clover": [vp, dp, dp],
+            "mg_set_params": [vp, ctypes.POINTER(mg_params)],
+            "mg_setup": [vp, ctypes.POINTER(mg_setup_info)],
+            "mg_set_null_vectors": [vp, ip, vp, ip, ip],
+            "mg_get_null_vectors": [vp, ip, vp, ip, ip],
+            "mg_solve": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
+            "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
+            "mg_level_info": [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ip
+        _lib = L
+    return _lib
+
+
+def mg_strerror(status: int) -> str:
+    return lib().mg_strerror(int(status)).decode()
+
+
+def mg_last_error() -> str:
+    return lib().mg_last_error().decode()
+
+
+def _check(status: int, where: str, allow=()):
+    if status != MG_OK and status not in allow:
+        raise MGError(status, where)
+    return status
+
+
+def _buf(x, writable=False):
+    """(pointer, where) of a complex128 C-contiguous numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.complex128 or not x.flags["C_CONTIGUOUS"]:
+            raise TypeError("buffers must be C-contiguous complex128")
+        if writable and not x.flags["WRITEABLE"]:
+            raise TypeError("output buffer is read-only")
+        return ctypes.c_void_p(x.ctypes.data), MG_HOST
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype != torch.complex128 or not x.is_contiguous():
+            raise TypeError("tensors must be contiguous complex128")
+        return ctypes.c_void_p(x.data_ptr()), (MG_DEVICE if x.is_cuda else MG_HOST)
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+# ----------------------------------------------------------------------------- C names
+def mg_default_params() -> mg_params:
+    p = mg_params()
+    _check(lib().mg_default_params(ctypes.byref(p)), "mg_default_params")
+    return p
+
+
+def mg_create(dims, device: int = 0, stream: int | None = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(v) for v in dims])
+    _check(lib().mg_create(ctypes.byref(h), d, int(device), ctypes.c_void_p(stream or 0)), "mg_create")
+    return h
+
+
+def mg_destroy(ctx) -> None:
+    _check(lib().mg_destroy(ctx), "mg_destroy")
+
+
+def mg_load_gauge(ctx, U) -> None:
+    p, w = _buf(U)
+    _check(lib().mg_load_gauge(ctx, p, w), "mg_load_gauge")
+
+
+def mg_set_clover(ctx, csw: float, m0: float) -> None:
+    _check(lib().mg_set_clover(ctx, float(csw), float(m0)), "mg_set_clover")
+
+
+def mg_set_params(ctx, params: mg_params) -> None:
+    _check(lib().mg_set_params(ctx, ctypes.byref(params)), "mg_set_params")
+
+
+def mg_setup(ctx) -> mg_setup_info:
+    info = mg_setup_info()
+    _check(lib().mg_setup(ctx, ctypes.byref(info)), "mg_setup")
+    return info
+
+
+def mg_set_null_vectors(ctx, level: int, V, nv: int) -> None:
+    p, w = _buf(V)
+    _check(lib().mg_set_null_vectors(ctx, int(level), p, int(nv), w), "mg_set_null_vectors")
+
+
+def mg_get_null_vectors(ctx, level: int, V, nv: int) -> None:
+    p, w = _buf(V, writable=True)
+    _check(lib().mg_get_null_vectors(ctx, int(level), p, int(nv), w), "mg_get_null_vectors")
+
+
+def mg_solve(ctx, psi, eta, nrhs: int, tol: float, mode: int = MG_MODE_MG, allow_not_converged=False):
+    """Returns ``(status, mg_solve_info)``."""
+    pp, wp = _buf(psi, writable=True)
+    pe, we = _buf(eta)
+    if wp != we:
+        raise TypeError("psi and eta must both be host or both be device buffers")
+    info = mg_solve_info()
+    st = lib().mg_solve(ctx, pp, pe, int(nrhs), float(tol), int(mode), wp, ctypes.byref(info))
+    _check(st, "mg_solve", allow=(MG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return st, info
+
+
+def mg_apply(ctx, op: int, level: int, out, x, nrhs: int = 1, prec: int = MG_FP64) -> None:
+    po, wo = _buf(out, writable=True)
+    pi, wi = _buf(x)
+    if wo != wi:
+        raise TypeError("in and out must both be host or both be device buffers")
+    _check(lib().mg_apply(ctx, int(op), int(level), po, pi, int(nrhs), int(prec), wo), "mg_apply")
+
+
+def mg_level_info(ctx, level: int):
+    d = (ctypes.c_int * 4)()
+    n = ctypes.c_int()
+    _check(lib().mg_level_info(ctx, int(level), d, ctypes.byref(n)), "mg_level_info")
+    return tuple(d), n.value

@@ -1,0 +1,413 @@
+// The C ABI of libmgclover (declared and documented in include/mgclover.h).
+//
+// Every entry point converts internal exceptions to a status code and keeps
+// the message for mg_last_error().  Host buffers are staged through device
+// memory owned by the context; device buffers are read and written in place.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "coarse.h"
+#include "internal.h"
+
+namespace {
+thread_local std::string g_last_error;
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    g_last_error.clear();
+    return f();
+  } catch (const mg::Error& e) {
+    g_last_error = e.what;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return MG_ERR_ALLOC;
+  } catch (const std::exception& e) {
+    g_last_error = e.what();
+    return MG_ERR_CUDA;
+  }
+}
+
+mg::Ctx* as_ctx(void* p) {
+  if (!p) mg::raise(MG_ERR_ARG, "null context");
+  mg::Ctx* c = static_cast<mg::Ctx*>(p);
+  MG_CUDA(cudaSetDevice(c->device));
+  return c;
+}
+
+// size (complex numbers) of one vector of level `level` under the current params
+size_t level_vec_complex(mg::Ctx* c, int level, int* ndof_out) {
+  int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
+  int ndof = 12;
+  for (int l = 0; l < level; l++) {
+    for (int m = 0; m < 4; m++) d[m] /= c->params.block[l][m];
+    ndof = 2 * c->params.nv[l];
+  }
+  if (ndof_out) *ndof_out = ndof;
+  return (size_t)d[0] * d[1] * d[2] * d[3] * ndof;
+}
+
+// device pointer for a caller buffer: the buffer itself or a staging copy
+struct Staged {
+  mg::DBuf own;
+  double* ptr = nullptr;
+};
+
+void stage_in(mg::Ctx* c, Staged& st, const void* user, size_t bytes, int where) {
+  if (where == MG_DEVICE) {
+    st.ptr = const_cast<double*>(static_cast<const double*>(user));
+    return;
+  }
+  st.own.alloc(bytes);
+  st.ptr = st.own.as<double>();
+  MG_CUDA(cudaMemcpyAsync(st.ptr, user, bytes, cudaMemcpyHostToDevice, c->stream));
+}
+
+void stage_out_alloc(Staged& st, void* user, size_t bytes, int where) {
+  if (where == MG_DEVICE) {
+    st.ptr = static_cast<double*>(user);
+    return;
+  }
+  st.own.alloc(bytes);
+  st.ptr = st.own.as<double>();
+}
+
+void stage_out_finish(mg::Ctx* c, Staged& st, void* user, size_t bytes, int where) {
+  if (where == MG_HOST) MG_CUDA(cudaMemcpyAsync(user, st.ptr, bytes, cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+}
+
+void check_where(int where) {
+  if (where != MG_HOST && where != MG_DEVICE) mg::raise(MG_ERR_ARG, "where must be MG_HOST or MG_DEVICE");
+}
+}  // namespace
+
+extern "C" {
+
+const char* mg_strerror(int status) {
+  switch (status) {
+    case MG_OK: return "ok";
+    case MG_ERR_ARG: return "invalid argument";
+    case MG_ERR_DIMS: return "invalid lattice or block dimensions";
+    case MG_ERR_NV: return "invalid number of null vectors";
+    case MG_ERR_STATE: return "call out of order (missing gauge, clover, parameters or setup)";
+    case MG_ERR_GS_BREAKDOWN: return "block Gram-Schmidt breakdown (locally dependent null vectors)";
+    case MG_ERR_SINGULAR_CLOVER: return "singular clover or coarse diagonal block";
+    case MG_ERR_NOT_CONVERGED: return "solver did not converge";
+    case MG_ERR_NAN: return "NaN or Inf encountered";
+    case MG_ERR_CUDA: return "CUDA runtime error";
+    case MG_ERR_ALLOC: return "allocation failed";
+    default: return "unknown status";
+  }
+}
+
+const char* mg_last_error(void) { return g_last_error.c_str(); }
+
+int mg_default_params(mg_params* p) {
+  if (!p) return MG_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->levels = 2;
+  for (int l = 0; l < MG_MAX_LEVELS; l++) {
+    for (int m = 0; m < 4; m++) p->block[l][m] = 4;
+    p->nv[l] = 24;
+  }
+  p->setup_iters = 20;
+  p->setup_inner = 8;
+  p->setup_rq_tol = 0.05;
+  p->nu_pre = 0;
+  p->nu_post = 4;
+  p->tol_coarse = 0.1;
+  p->maxit_coarse = 50;
+  p->restart_coarse = 32;
+  p->restart_fine = 16;
+  p->maxit_fine = 500;
+  p->storage = MG_STORE_FP32;
+  p->coarse_op = MG_COARSE_DP;
+  p->seed = 3;
+  return MG_OK;
+}
+
+int mg_create(void** ctx_out, const int dims[4], int device, void* cuda_stream) {
+  return guarded([&]() {
+    if (!ctx_out || !dims) mg::raise(MG_ERR_ARG, "null argument");
+    *ctx_out = nullptr;
+    for (int m = 0; m < 4; m++)
+      if (dims[m] < 2 || dims[m] % 2) mg::raise(MG_ERR_DIMS, "every lattice extent must be even and >= 2");
+    const double vol = (double)dims[0] * dims[1] * dims[2] * dims[3];
+    if (vol > 2.0e9) mg::raise(MG_ERR_DIMS, "lattice too large");
+    MG_CUDA(cudaSetDevice(device));
+    std::unique_ptr<mg::Ctx> c(new mg::Ctx());
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    for (int m = 0; m < 4; m++) {
+      c->dims[m] = dims[m];
+      c->g.L[m] = dims[m];
+    }
+    c->V = (size_t)vol;
+    c->Vh = c->V / 2;
+    c->g.Vh = (int)c->Vh;
+    c->g.xh = dims[0] / 2;
+    c->g.apbc = 1;
+    c->ws.init();
+    mg_default_params(&c->params);
+    *ctx_out = c.release();
+    return MG_OK;
+  });
+}
+
+int mg_destroy(void* ctx) {
+  if (!ctx) return MG_OK;
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+    return MG_OK;
+  });
+}
+
+int mg_load_gauge(void* ctx, const void* U, int where) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!U) mg::raise(MG_ERR_ARG, "null gauge field");
+    check_where(where);
+    const size_t bytes = sizeof(double) * 2 * 36 * c->V;
+    Staged st;
+    stage_in(c, st, U, bytes, where);
+    if (!c->gauge64.get()) {
+      c->gauge64.alloc(sizeof(double) * 2 * 36 * c->V);
+      c->gauge32.alloc(sizeof(float) * 2 * 36 * c->V);
+    }
+    mg::pack_gauge(c->g, st.ptr, c->gauge64.as<double>(), c->gauge32.as<float>(), c->stream);
+    c->sync();
+    c->have_gauge = true;
+    c->have_clover = false;
+    c->mg.reset();
+    return MG_OK;
+  });
+}
+
+int mg_set_clover(void* ctx, double csw, double m0) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!c->have_gauge) mg::raise(MG_ERR_STATE, "load the gauge field first");
+    if (!std::isfinite(csw) || !std::isfinite(m0)) mg::raise(MG_ERR_ARG, "non-finite csw or m0");
+    if (!c->clov64.get()) {
+      c->clov64.alloc(sizeof(double) * 144 * c->Vh);
+      c->clovinv64.alloc(sizeof(double) * 144 * c->Vh);
+      c->clov32.alloc(sizeof(float) * 144 * c->Vh);
+      c->clovinv32.alloc(sizeof(float) * 144 * c->Vh);
+    }
+    c->mg.reset();
+    c->have_clover = false;
+    mg::build_clover(c->g, c->gauge64.as<double>(), csw, m0, c->clov64.as<double>(), c->clovinv64.as<double>(),
+                     c->clov32.as<float>(), c->clovinv32.as<float>(), c->ws.flags.as<int>(), c->stream);
+    if (c->read_flag(mg::FLAG_SINGULAR, true)) mg::raise(MG_ERR_SINGULAR_CLOVER, "singular clover block");
+    c->csw = csw;
+    c->m0 = m0;
+    c->have_clover = true;
+    return MG_OK;
+  });
+}
+
+int mg_set_params(void* ctx, const mg_params* p) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!p) mg::raise(MG_ERR_ARG, "null params");
+    if (p->levels < 1 || p->levels > MG_MAX_LEVELS) mg::raise(MG_ERR_ARG, "levels out of range");
+    if (p->setup_iters < 1 || p->setup_inner < 1 || !(p->setup_rq_tol >= 0)) mg::raise(MG_ERR_ARG, "bad setup effort");
+    if (p->nu_pre < 0 || p->nu_post < 0) mg::raise(MG_ERR_ARG, "negative smoothing steps");
+    if (!(p->tol_coarse > 0) || p->maxit_coarse < 1 || p->restart_coarse < 1 || p->restart_coarse > 64)
+      mg::raise(MG_ERR_ARG, "bad coarse solver parameters");
+    if (p->restart_fine < 1 || p->restart_fine > 64 || p->maxit_fine < 1) mg::raise(MG_ERR_ARG, "bad outer solver parameters");
+    if (p->storage < MG_STORE_FP32 || p->storage > MG_STORE_BF16) mg::raise(MG_ERR_ARG, "bad storage");
+    if (p->coarse_op != MG_COARSE_DP && p->coarse_op != MG_COARSE_D) mg::raise(MG_ERR_ARG, "bad coarse_op");
+    int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
+    int ndof = 12;
+    for (int l = 0; l + 1 < p->levels; l++) {
+      int nb = 1;
+      for (int m = 0; m < 4; m++) {
+        const int b = p->block[l][m];
+        if (b < 1 || d[m] % b) mg::raise(MG_ERR_DIMS, "block does not divide the lattice");
+        nb *= b;
+      }
+      const int nv = p->nv[l];
+      if (nv < 1 || nv > 40) mg::raise(MG_ERR_NV, "nv must be in [1, 40]");
+      if (nv > nb * ndof / 2) mg::raise(MG_ERR_NV, "nv exceeds the dimension of a block's chiral subspace");
+      for (int m = 0; m < 4; m++) d[m] /= p->block[l][m];
+      ndof = 2 * nv;
+      // every level below the coarsest runs an even-odd preconditioned solve
+      if (l + 2 < p->levels)
+        for (int m = 0; m < 4; m++)
+          if (d[m] % 2) mg::raise(MG_ERR_DIMS, "a level below the coarsest has an odd extent");
+    }
+    c->params = *p;
+    c->have_params = true;
+    c->mg.reset();
+    c->solve_work.reset();
+    c->injected.assign(MG_MAX_LEVELS, std::vector<double>());
+    return MG_OK;
+  });
+}
+
+int mg_setup(void* ctx, mg_setup_info* info) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
+    if (info) std::memset(info, 0, sizeof(*info));
+    mg::mg_build(c, info);
+    return MG_OK;
+  });
+}
+
+int mg_set_null_vectors(void* ctx, int level, const void* V, int nv, int where) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    check_where(where);
+    if (!V) mg::raise(MG_ERR_ARG, "null vectors");
+    if (level < 0 || level + 1 >= c->params.levels) mg::raise(MG_ERR_ARG, "no transfer from this level");
+    if (nv != c->params.nv[level]) mg::raise(MG_ERR_NV, "nv does not match the parameters");
+    const size_t n = level_vec_complex(c, level, nullptr);
+    if (c->injected.size() < MG_MAX_LEVELS) c->injected.assign(MG_MAX_LEVELS, std::vector<double>());
+    std::vector<double>& h = c->injected[level];
+    h.resize(2 * n * nv);
+    if (where == MG_HOST) {
+      std::memcpy(h.data(), V, sizeof(double) * h.size());
+    } else {
+      MG_CUDA(cudaMemcpy(h.data(), V, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+    }
+    c->mg.reset();
+    return MG_OK;
+  });
+}
+
+int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    check_where(where);
+    if (!V) mg::raise(MG_ERR_ARG, "null vectors");
+    if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    const size_t bytes = sizeof(double) * 2 * level_vec_complex(c, level, nullptr) * nv;
+    Staged st;
+    stage_out_alloc(st, V, bytes, where);
+    mg::mg_get_vectors(c, level, st.ptr, nv);
+    stage_out_finish(c, st, V, bytes, where);
+    return MG_OK;
+  });
+}
+
+int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where, mg_solve_info* info) {
+  return guarded([&]() {
+    const auto t0 = std::chrono::steady_clock::now();
+    mg::Ctx* c = as_ctx(ctx);
+    check_where(where);
+    if (!psi || !eta || nrhs < 1 || !(tol > 0)) mg::raise(MG_ERR_ARG, "bad solve arguments");
+    if (mode != MG_MODE_MG && mode != MG_MODE_EO_GCR) mg::raise(MG_ERR_ARG, "bad mode");
+    if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
+    if (mode == MG_MODE_MG && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    mg_solve_info local;
+    std::memset(&local, 0, sizeof(local));
+    local.true_residual = 0.0;
+    mg::mg_reset_counters(c);
+    const long long launches0 = c->dslash_launches;
+    const size_t per = sizeof(double) * 24 * c->V;
+    Staged si, so;
+    stage_in(c, si, eta, per * nrhs, where);
+    stage_out_alloc(so, psi, per * nrhs, where);
+    int status = MG_OK;
+    for (int r = 0; r < nrhs; r++) {
+      const int st = mg::solve_fine(c, so.ptr + (size_t)r * 24 * c->V, si.ptr + (size_t)r * 24 * c->V, tol, mode, &local);
+      if (st != MG_OK) status = st;
+    }
+    stage_out_finish(c, so, psi, per * nrhs, where);
+    mg::mg_read_counters(c, local.coarse_iterations);
+    local.dslash_launches = c->dslash_launches - launches0;
+    local.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = local;
+    return status;
+  });
+}
+
+int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, int prec, int where) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    check_where(where);
+    if (!out || !in || nrhs < 1) mg::raise(MG_ERR_ARG, "bad apply arguments");
+    if (prec != MG_FP64 && prec != MG_FP32) mg::raise(MG_ERR_ARG, "bad precision");
+    if (op < MG_OP_D || op > MG_OP_P) mg::raise(MG_ERR_ARG, "bad operator");
+    if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
+    if (level < 0 || level >= c->params.levels) mg::raise(MG_ERR_ARG, "level out of range");
+    if ((level > 0 || op == MG_OP_R || op == MG_OP_P) && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    int ndof_in, ndof_out;
+    const int lin = op == MG_OP_P ? level + 1 : level;
+    const int lout = op == MG_OP_R ? level + 1 : level;
+    if ((op == MG_OP_R || op == MG_OP_P) && level + 1 >= c->params.levels) mg::raise(MG_ERR_ARG, "no transfer");
+    const size_t nin = level_vec_complex(c, lin, &ndof_in), nout = level_vec_complex(c, lout, &ndof_out);
+    Staged si, so;
+    stage_in(c, si, in, sizeof(double) * 2 * nin * nrhs, where);
+    stage_out_alloc(so, out, sizeof(double) * 2 * nout * nrhs, where);
+    for (int r = 0; r < nrhs; r++) {
+      const double* ip = si.ptr + (size_t)r * 2 * nin;
+      double* op_ = so.ptr + (size_t)r * 2 * nout;
+      if (level > 0 || op == MG_OP_R || op == MG_OP_P) {
+        mg::mg_apply_level(c, op, level, op_, ip);
+        continue;
+      }
+      const bool f32 = prec == MG_FP32;
+      const size_t es = f32 ? sizeof(float) : sizeof(double);
+      const size_t half = 24 * c->Vh;  // reals per half vector
+      mg::DBuf ib(es * 2 * half), ob(es * 2 * half);
+      MG_CUDA(cudaMemsetAsync(ob.get(), 0, es * 2 * half, c->stream));
+      char* ie = ib.as<char>();
+      char* io = ie + es * half;
+      char* oe = ob.as<char>();
+      char* oo = oe + es * half;
+      mg::pack_spinor(c->g, ip, ie, io, f32, c->stream);
+      auto run = [&](auto* tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        mg::FineOps<T> F(c);
+        T *ie_ = (T*)ie, *io_ = (T*)io, *oe_ = (T*)oe, *oo_ = (T*)oo;
+        switch (op) {
+          case MG_OP_D: F.D(oe_, oo_, ie_, io_); break;
+          case MG_OP_DP: F.Dp(oe_, oo_, ie_, io_); break;
+          case MG_OP_DR: F.Dr(oe_, ie_); break;
+          case MG_OP_BR: F.br(oe_, ie_, io_); break;
+          case MG_OP_M: F.M(oe_, oo_, ie_, io_, false); break;
+          case MG_OP_MINV: F.M(oe_, oo_, ie_, io_, true); break;
+          case MG_OP_HOP: F.H(oe_, oo_, ie_, io_); break;
+          default: mg::raise(MG_ERR_ARG, "bad operator");
+        }
+      };
+      if (f32)
+        run((float*)nullptr);
+      else
+        run((double*)nullptr);
+      mg::unpack_spinor(c->g, oe, oo, f32, op_, c->stream);
+      c->sync();
+    }
+    stage_out_finish(c, so, out, sizeof(double) * 2 * nout * nrhs, where);
+    return MG_OK;
+  });
+}
+
+int mg_level_info(void* ctx, int level, int dims_out[4], int* ndof_out) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!dims_out || !ndof_out) mg::raise(MG_ERR_ARG, "null output");
+    if (level < 0 || level >= c->params.levels) mg::raise(MG_ERR_ARG, "level out of range");
+    int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
+    int ndof = 12;
+    for (int l = 0; l < level; l++) {
+      for (int m = 0; m < 4; m++) d[m] /= c->params.block[l][m];
+      ndof = 2 * c->params.nv[l];
+    }
+    for (int m = 0; m < 4; m++) dims_out[m] = d[m];
+    *ndof_out = ndof;
+    return MG_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,766 @@
+// Coarse-level kernels of the adaptive multigrid (sm_103a).
+//
+//  * restriction R = P^dag and prolongation P with the chirality split of
+//    the null vectors (section "Red-black preconditioning": P is built from
+//    the low modes of D_p, split into the two chiralities inside each block;
+//    R = P^dag gamma_5 gives the same coarse correction as R = P^dag for a
+//    chirality-split P, so R = P^dag is applied)
+//  * Galerkin coarse links D_hat = R D_p P ("Red-black preconditioning"):
+//    one P column at a time, the eight directional hops of M^{-1} p are
+//    projected onto the receiving block's P, hops across a block face into
+//    Y_d and all others into X
+//  * the coarse stencil D_hat v = X v + sum_d Y_d v(. + d) with the same
+//    epilogues as the fine dslash, which give the coarse even-odd operators
+//    (the coarse system is solved by its reduced even-odd form)
+//  * FP64 batched Gauss-Jordan for X^{-1}
+//  * block Gram-Schmidt (FP64 accumulation) and coarse-vector packing
+//
+// Coarse operators look like a staggered operator with Nc = 2 Nv colours
+// ("Implementation"); a CTA owns one coarse site, its warps own rows of the
+// 2Nv x 8*2Nv link block, and the neighbour vectors are staged in shared
+// memory so each link row is read once, coalesced.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "coarse.h"
+#include "philox.cuh"
+
+namespace mg {
+
+namespace {
+constexpr int kBS = 256;
+
+__device__ __forceinline__ cx<float> fget(const FineAccess& fa, const float* base, int idx, int c) {
+  if (fa.wilson) {
+    const int par = idx >= fa.Vh;
+    const int cb = idx - par * fa.Vh;
+    return SpinorIO<float>::get(base + (size_t)par * 24 * fa.Vh, fa.Vh, cb, c);
+  }
+  const float2 v = reinterpret_cast<const float2*>(base)[(size_t)idx * fa.ndof + c];
+  return mkc(v.x, v.y);
+}
+
+__device__ __forceinline__ void fput(const FineAccess& fa, float* base, int idx, int c, cx<float> z) {
+  if (fa.wilson) {
+    const int par = idx >= fa.Vh;
+    const int cb = idx - par * fa.Vh;
+    SpinorIO<float>::put(base + (size_t)par * 24 * fa.Vh, fa.Vh, cb, c, z);
+    return;
+  }
+  reinterpret_cast<float2*>(base)[(size_t)idx * fa.ndof + c] = make_float2(z.re, z.im);
+}
+
+// element e of a stored complex array in format ST
+template <int ST>
+__device__ __forceinline__ cx<float> sget(const void* p, size_t e) {
+  if (ST == STORE_F32) {
+    const float2 v = reinterpret_cast<const float2*>(p)[e];
+    return mkc(v.x, v.y);
+  } else if (ST == STORE_F16) {
+    const float2 v = __half22float2(reinterpret_cast<const __half2*>(p)[e]);
+    return mkc(v.x, v.y);
+  } else {
+    const float2 v = __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(p)[e]);
+    return mkc(v.x, v.y);
+  }
+}
+
+template <int ST>
+__device__ __forceinline__ void sput(void* p, size_t e, cx<float> z) {
+  if (ST == STORE_F32) {
+    reinterpret_cast<float2*>(p)[e] = make_float2(z.re, z.im);
+  } else if (ST == STORE_F16) {
+    reinterpret_cast<__half2*>(p)[e] = __floats2half2_rn(z.re, z.im);
+  } else {
+    reinterpret_cast<__nv_bfloat162*>(p)[e] = __floats2bfloat162_rn(z.re, z.im);
+  }
+}
+
+struct TArgs {
+  int nv, ndof, nb, fine_half;
+  int b[4], cd[4];
+  FineAccess fa;
+  const int* blockmap;
+  const void* P;
+  const float* Ps;
+};
+
+TArgs targs(const TransferOp& T) {
+  TArgs a;
+  a.nv = T.nv;
+  a.ndof = T.fine_ndof;
+  a.nb = T.nb;
+  a.fine_half = T.fine_half;
+  for (int m = 0; m < 4; m++) {
+    a.b[m] = T.block[m];
+    a.cd[m] = T.cdims[m];
+  }
+  a.fa = T.fa;
+  a.blockmap = T.blockmap.as<int>();
+  a.P = T.P.get();
+  a.Ps = T.Pscale.as<float>();
+  return a;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+}  // namespace
+
+// --------------------------------------------------------------------------- restriction
+template <int ST>
+__global__ void k_restrict(TArgs a, float* __restrict__ out, const float* __restrict__ v, int even_only) {
+  extern __shared__ double sred[];  // [G][nv][2][2]
+  const int cc = blockIdx.x;
+  const int nv = a.nv, G = blockDim.x / nv;
+  const int k = threadIdx.x % nv, g = threadIdx.x / nv;
+  const int hd = a.ndof / 2;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  if (g < G) {
+    const float s0 = a.Ps[cc * 2], s1 = a.Ps[cc * 2 + 1];
+    for (int i = g; i < a.nb; i += G) {
+      const int idx = a.blockmap[cc * a.nb + i];
+      if (even_only && idx >= a.fine_half) continue;
+      const size_t base = (size_t)(cc * a.nb + i) * a.ndof;
+#pragma unroll
+      for (int ch = 0; ch < 2; ch++) {
+        const float sc = ch ? s1 : s0;
+        for (int c = ch * hd; c < (ch + 1) * hd; c++) {
+          const cx<float> x = fget(a.fa, v, idx, c);
+          const cx<float> p = sget<ST>(a.P, (base + c) * nv + k);
+          acc[ch][0] += (double)(sc * (p.re * x.re + p.im * x.im));
+          acc[ch][1] += (double)(sc * (p.re * x.im - p.im * x.re));
+        }
+      }
+    }
+    double* me = sred + ((size_t)g * nv + k) * 4;
+    me[0] = acc[0][0];
+    me[1] = acc[0][1];
+    me[2] = acc[1][0];
+    me[3] = acc[1][1];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x) {
+    const int ch = t / nv, kk = t % nv;
+    double re = 0, im = 0;
+    for (int q = 0; q < G; q++) {
+      re += sred[((size_t)q * nv + kk) * 4 + 2 * ch];
+      im += sred[((size_t)q * nv + kk) * 4 + 2 * ch + 1];
+    }
+    reinterpret_cast<float2*>(out)[(size_t)cc * 2 * nv + t] = make_float2((float)re, (float)im);
+  }
+}
+
+void restrict_vec(const TransferOp& T, float* out_c, const float* v, bool even_only, cudaStream_t s) {
+  TArgs a = targs(T);
+  const int G = kBS / T.nv;
+  const size_t sm = sizeof(double) * 4 * (size_t)G * T.nv;
+  switch (T.store) {
+    case STORE_F32: k_restrict<STORE_F32><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
+    case STORE_F16: k_restrict<STORE_F16><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
+    default: k_restrict<STORE_BF16><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
+  }
+  MG_LAUNCH();
+}
+
+// --------------------------------------------------------------------------- prolongation
+template <int ST>
+__global__ void k_prolong(TArgs a, float* __restrict__ v, const float* __restrict__ in_c, int even_only) {
+  extern __shared__ float2 svc[];  // [2 nv]
+  const int cc = blockIdx.x;
+  const int nv = a.nv, hd = a.ndof / 2;
+  for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x)
+    svc[t] = reinterpret_cast<const float2*>(in_c)[(size_t)cc * 2 * nv + t];
+  __syncthreads();
+  const float s0 = a.Ps[cc * 2], s1 = a.Ps[cc * 2 + 1];
+  for (int t = threadIdx.x; t < a.nb * a.ndof; t += blockDim.x) {
+    const int i = t / a.ndof, c = t % a.ndof;
+    const int idx = a.blockmap[cc * a.nb + i];
+    if (even_only && idx >= a.fine_half) continue;
+    const int ch = c >= hd;
+    const float2* vc = svc + ch * nv;
+    const size_t base = ((size_t)(cc * a.nb + i) * a.ndof + c) * nv;
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < nv; k++) {
+      const cx<float> p = sget<ST>(a.P, base + k);
+      re += p.re * vc[k].x - p.im * vc[k].y;
+      im += p.re * vc[k].y + p.im * vc[k].x;
+    }
+    const float sc = ch ? s1 : s0;
+    fput(a.fa, v, idx, c, mkc(sc * re, sc * im));
+  }
+}
+
+void prolong_vec(const TransferOp& T, float* v, const float* in_c, bool even_only, cudaStream_t s) {
+  TArgs a = targs(T);
+  const size_t sm = sizeof(float2) * 2 * T.nv;
+  switch (T.store) {
+    case STORE_F32: k_prolong<STORE_F32><<<T.ncoarse, kBS, sm, s>>>(a, v, in_c, even_only); break;
+    case STORE_F16: k_prolong<STORE_F16><<<T.ncoarse, kBS, sm, s>>>(a, v, in_c, even_only); break;
+    default: k_prolong<STORE_BF16><<<T.ncoarse, kBS, sm, s>>>(a, v, in_c, even_only); break;
+  }
+  MG_LAUNCH();
+}
+
+// --------------------------------------------------------------------------- column extraction
+template <int ST>
+__global__ void k_extract_column(TArgs a, float* p, int chir, int k) {
+  const size_t total = (size_t)a.nb * a.ndof;
+  const int cc = blockIdx.x;
+  const int hd = a.ndof / 2;
+  for (size_t t = threadIdx.x; t < total; t += blockDim.x) {
+    const int i = (int)(t / a.ndof), c = (int)(t % a.ndof);
+    const int idx = a.blockmap[cc * a.nb + i];
+    cx<float> z = mkc(0.f, 0.f);
+    if ((c >= hd) == (chir == 1)) {
+      z = sget<ST>(a.P, ((size_t)(cc * a.nb + i) * a.ndof + c) * a.nv + k);
+      const float sc = a.Ps[cc * 2 + chir];
+      z = mkc(sc * z.re, sc * z.im);
+    }
+    fput(a.fa, p, idx, c, z);
+  }
+}
+
+void extract_column(const TransferOp& T, float* p, int chir, int k, cudaStream_t s) {
+  TArgs a = targs(T);
+  switch (T.store) {
+    case STORE_F32: k_extract_column<STORE_F32><<<T.ncoarse, kBS, 0, s>>>(a, p, chir, k); break;
+    case STORE_F16: k_extract_column<STORE_F16><<<T.ncoarse, kBS, 0, s>>>(a, p, chir, k); break;
+    default: k_extract_column<STORE_BF16><<<T.ncoarse, kBS, 0, s>>>(a, p, chir, k); break;
+  }
+  MG_LAUNCH();
+}
+
+// --------------------------------------------------------------------------- Galerkin column
+struct W9 {
+  const float* p[9];
+};
+
+template <int ST>
+__global__ void k_restrict9(TArgs a, W9 W, float2* __restrict__ Y, float2* __restrict__ X, int col) {
+  extern __shared__ double sred[];  // [G][nv][2][2]
+  const int cc = blockIdx.x;
+  const int nv = a.nv, G = blockDim.x / nv, nc = 2 * nv;
+  const int k = threadIdx.x % nv, g = threadIdx.x / nv;
+  const int hd = a.ndof / 2;
+  double acc[9][2][2];
+#pragma unroll
+  for (int t = 0; t < 9; t++)
+#pragma unroll
+    for (int ch = 0; ch < 2; ch++) acc[t][ch][0] = acc[t][ch][1] = 0.0;
+  if (g < G) {
+    for (int i = g; i < a.nb; i += G) {
+      const int idx = a.blockmap[cc * a.nb + i];
+      int l[4];
+      l[0] = i % a.b[0];
+      l[1] = (i / a.b[0]) % a.b[1];
+      l[2] = (i / (a.b[0] * a.b[1])) % a.b[2];
+      l[3] = i / (a.b[0] * a.b[1] * a.b[2]);
+      bool face[8];
+#pragma unroll
+      for (int d = 0; d < 8; d++) {
+        const int mu = d & 3;
+        face[d] = a.cd[mu] > 1 && (d < 4 ? l[mu] == a.b[mu] - 1 : l[mu] == 0);
+      }
+      const size_t base = (size_t)(cc * a.nb + i) * a.ndof;
+#pragma unroll
+      for (int ch = 0; ch < 2; ch++) {
+        const float sc = a.Ps[cc * 2 + ch];
+        for (int c = ch * hd; c < (ch + 1) * hd; c++) {
+          cx<float> p = sget<ST>(a.P, (base + c) * nv + k);
+          p = mkc(sc * p.re, sc * p.im);
+#pragma unroll
+          for (int d = 0; d < 9; d++) {
+            const cx<float> w = fget(a.fa, W.p[d], idx, c);
+            const double re = (double)p.re * w.re + (double)p.im * w.im;
+            const double im = (double)p.re * w.im - (double)p.im * w.re;
+            if (d < 8 && face[d < 8 ? d : 0]) {
+              acc[d][ch][0] += re;
+              acc[d][ch][1] += im;
+            } else {
+              acc[8][ch][0] += re;
+              acc[8][ch][1] += im;
+            }
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 9; t++) {
+    __syncthreads();
+    if (g < G) {
+      double* me = sred + ((size_t)g * nv + k) * 4;
+      me[0] = acc[t][0][0];
+      me[1] = acc[t][0][1];
+      me[2] = acc[t][1][0];
+      me[3] = acc[t][1][1];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const int ch = q / nv, kk = q % nv;
+      double re = 0, im = 0;
+      for (int gg = 0; gg < G; gg++) {
+        re += sred[((size_t)gg * nv + kk) * 4 + 2 * ch];
+        im += sred[((size_t)gg * nv + kk) * 4 + 2 * ch + 1];
+      }
+      const int row = q;
+      if (t < 8)
+        Y[(((size_t)cc * nc + row) * 8 + t) * nc + col] = make_float2((float)re, (float)im);
+      else
+        X[((size_t)cc * nc + row) * nc + col] = make_float2((float)re, (float)im);
+    }
+  }
+}
+
+void restrict9(const TransferOp& T, CoarseOp& C, const float* const W[9], int col, cudaStream_t s) {
+  TArgs a = targs(T);
+  W9 w;
+  for (int d = 0; d < 9; d++) w.p[d] = W[d];
+  const int G = kBS / T.nv;
+  const size_t sm = sizeof(double) * 4 * (size_t)G * T.nv;
+  float2* Y = C.Y.as<float2>();
+  float2* X = C.X.as<float2>();
+  switch (T.store) {
+    case STORE_F32: k_restrict9<STORE_F32><<<T.ncoarse, kBS, sm, s>>>(a, w, Y, X, col); break;
+    case STORE_F16: k_restrict9<STORE_F16><<<T.ncoarse, kBS, sm, s>>>(a, w, Y, X, col); break;
+    default: k_restrict9<STORE_BF16><<<T.ncoarse, kBS, sm, s>>>(a, w, Y, X, col); break;
+  }
+  MG_LAUNCH();
+}
+
+// --------------------------------------------------------------------------- coarse stencil
+struct HopArgs {
+  int nc, s0, dirmask;
+  const int* nbr;
+  const float2* Y;
+  const float* Ys;
+  const float2* C;  // X or Xinv
+  float2* out;
+  const float2* in;
+  const float2* x;
+  float a;
+};
+
+template <int EPI>
+__global__ void __launch_bounds__(128) k_coarse_hop(HopArgs h) {
+  extern __shared__ float2 sm[];  // vin[8 nc], t[nc], vx[nc]
+  const int nc = h.nc;
+  const int s = h.s0 + blockIdx.x;
+  float2* vin = sm;
+  float2* tv = sm + 8 * nc;
+  float2* vx = tv + nc;
+  for (int t = threadIdx.x; t < 8 * nc; t += blockDim.x) {
+    const int d = t / nc, j = t % nc;
+    float2 v = make_float2(0.f, 0.f);
+    if ((h.dirmask >> d) & 1) {
+      const float sc = h.Ys[(size_t)s * 8 + d];
+      v = h.in[(size_t)h.nbr[(size_t)s * 8 + d] * nc + j];
+      v.x *= sc;
+      v.y *= sc;
+    }
+    vin[t] = v;
+  }
+  if (EPI == EPI_CX_PAY || EPI == EPI_XPAY || EPI == EPI_C_XPAY)
+    for (int t = threadIdx.x; t < nc; t += blockDim.x) vx[t] = h.x[(size_t)s * nc + t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = w; i < nc; i += nw) {
+    const float2* row = h.Y + ((size_t)s * nc + i) * 8 * nc;
+    float re = 0.f, im = 0.f;
+    for (int q = lane; q < 8 * nc; q += 32) {
+      const float2 y = row[q], v = vin[q];
+      re += y.x * v.x - y.y * v.y;
+      im += y.x * v.y + y.y * v.x;
+    }
+    re = warp_sumf(re);
+    im = warp_sumf(im);
+    if (lane == 0) {
+      if (EPI == EPI_H) {
+        h.out[(size_t)s * nc + i] = make_float2(re, im);
+      } else if (EPI == EPI_XPAY) {
+        h.out[(size_t)s * nc + i] = make_float2(vx[i].x + h.a * re, vx[i].y + h.a * im);
+      } else if (EPI == EPI_CH || EPI == EPI_CX_PAY) {
+        tv[i] = make_float2(re, im);
+      } else {  // EPI_C_XPAY
+        tv[i] = make_float2(vx[i].x + h.a * re, vx[i].y + h.a * im);
+      }
+    }
+  }
+  if (EPI == EPI_H || EPI == EPI_XPAY) return;
+  __syncthreads();
+  const float2* src = (EPI == EPI_CX_PAY) ? vx : tv;
+  for (int i = w; i < nc; i += nw) {
+    const float2* row = h.C + ((size_t)s * nc + i) * nc;
+    float re = 0.f, im = 0.f;
+    for (int q = lane; q < nc; q += 32) {
+      const float2 y = row[q], v = src[q];
+      re += y.x * v.x - y.y * v.y;
+      im += y.x * v.y + y.y * v.x;
+    }
+    re = warp_sumf(re);
+    im = warp_sumf(im);
+    if (lane == 0) {
+      if (EPI == EPI_CX_PAY)
+        h.out[(size_t)s * nc + i] = make_float2(re + h.a * tv[i].x, im + h.a * tv[i].y);
+      else
+        h.out[(size_t)s * nc + i] = make_float2(re, im);
+    }
+  }
+}
+
+void coarse_hop(const LevelGeom& G, const CoarseOp& C, Epilogue epi, bool use_inv, int s0, int s1, float* out,
+                const float* in, const float* x, float a, int dirmask, cudaStream_t s) {
+  if (s1 <= s0) return;
+  HopArgs h;
+  h.nc = C.nc;
+  h.s0 = s0;
+  h.dirmask = dirmask;
+  h.nbr = G.d_nbr.as<int>();
+  h.Y = C.Y.as<float2>();
+  h.Ys = C.Yscale.as<float>();
+  h.C = use_inv ? C.Xinv.as<float2>() : C.X.as<float2>();
+  h.out = (float2*)out;
+  h.in = (const float2*)in;
+  h.x = (const float2*)x;
+  h.a = a;
+  const size_t sm = sizeof(float2) * 10 * (size_t)C.nc;
+  const int nb = s1 - s0;
+  switch (epi) {
+    case EPI_H: k_coarse_hop<EPI_H><<<nb, 128, sm, s>>>(h); break;
+    case EPI_CH: k_coarse_hop<EPI_CH><<<nb, 128, sm, s>>>(h); break;
+    case EPI_XPAY: k_coarse_hop<EPI_XPAY><<<nb, 128, sm, s>>>(h); break;
+    case EPI_CX_PAY: k_coarse_hop<EPI_CX_PAY><<<nb, 128, sm, s>>>(h); break;
+    case EPI_C_XPAY: k_coarse_hop<EPI_C_XPAY><<<nb, 128, sm, s>>>(h); break;
+  }
+  MG_LAUNCH();
+}
+
+__global__ void __launch_bounds__(128) k_site_mul(int nc, int s0, const float2* __restrict__ C, float2* out,
+                                                   const float2* __restrict__ in) {
+  extern __shared__ float2 sv[];
+  const int s = s0 + blockIdx.x;
+  for (int t = threadIdx.x; t < nc; t += blockDim.x) sv[t] = in[(size_t)s * nc + t];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = w; i < nc; i += nw) {
+    const float2* row = C + ((size_t)s * nc + i) * nc;
+    float re = 0.f, im = 0.f;
+    for (int q = lane; q < nc; q += 32) {
+      const float2 y = row[q], v = sv[q];
+      re += y.x * v.x - y.y * v.y;
+      im += y.x * v.y + y.y * v.x;
+    }
+    re = warp_sumf(re);
+    im = warp_sumf(im);
+    if (lane == 0) out[(size_t)s * nc + i] = make_float2(re, im);
+  }
+}
+
+void coarse_site_mul(const LevelGeom& G, const CoarseOp& C, bool use_inv, int s0, int s1, float* out, const float* in,
+                     cudaStream_t s) {
+  (void)G;
+  if (s1 <= s0) return;
+  const float2* M = use_inv ? C.Xinv.as<float2>() : C.X.as<float2>();
+  k_site_mul<<<s1 - s0, 128, sizeof(float2) * C.nc, s>>>(C.nc, s0, M, (float2*)out, (const float2*)in);
+  MG_LAUNCH();
+}
+
+// --------------------------------------------------------------------------- coarse inverse
+__global__ void k_coarse_invert(int nc, const float2* __restrict__ X, float2* Xinv, int* flags) {
+  extern __shared__ double2 A[];  // [nc][2 nc]
+  __shared__ double2 fac[128];
+  __shared__ int piv_s;
+  __shared__ double amax_s;
+  const int s = blockIdx.x;
+  const int w2 = 2 * nc;
+  for (int t = threadIdx.x; t < nc * w2; t += blockDim.x) {
+    const int i = t / w2, j = t % w2;
+    double2 v;
+    if (j < nc) {
+      const float2 x = X[((size_t)s * nc + i) * nc + j];
+      v = make_double2(x.x, x.y);
+    } else {
+      v = make_double2(i == j - nc ? 1.0 : 0.0, 0.0);
+    }
+    A[t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int i = 0; i < nc; i++)
+      for (int j = 0; j < nc; j++) m = fmax(m, fabs(A[i * w2 + j].x) + fabs(A[i * w2 + j].y));
+    amax_s = m;
+  }
+  __syncthreads();
+  for (int col = 0; col < nc; col++) {
+    if (threadIdx.x < 32) {
+      double best = -1.0;
+      int bi = col;
+      for (int r = col + threadIdx.x; r < nc; r += 32) {
+        const double2 v = A[r * w2 + col];
+        const double m = v.x * v.x + v.y * v.y;
+        if (m > best) { best = m; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (threadIdx.x == 0) {
+        piv_s = bi;
+        if (!(sqrt(best) > 1e-12 * amax_s)) atomicExch(&flags[FLAG_SINGULAR], 1);
+      }
+    }
+    __syncthreads();
+    const int piv = piv_s;
+    if (piv != col)
+      for (int j = threadIdx.x; j < w2; j += blockDim.x) {
+        const double2 t = A[col * w2 + j];
+        A[col * w2 + j] = A[piv * w2 + j];
+        A[piv * w2 + j] = t;
+      }
+    __syncthreads();
+    double2 p = A[col * w2 + col];
+    double den = p.x * p.x + p.y * p.y;
+    if (den == 0) den = 1;
+    const double2 pinv = make_double2(p.x / den, -p.y / den);
+    __syncthreads();
+    for (int j = threadIdx.x; j < w2; j += blockDim.x) {
+      const double2 a = A[col * w2 + j];
+      A[col * w2 + j] = make_double2(pinv.x * a.x - pinv.y * a.y, pinv.x * a.y + pinv.y * a.x);
+    }
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) fac[r] = A[r * w2 + col];
+    __syncthreads();
+    for (int t = threadIdx.x; t < nc * w2; t += blockDim.x) {
+      const int r = t / w2, j = t % w2;
+      if (r == col) continue;
+      const double2 f = fac[r], a = A[col * w2 + j];
+      A[t].x -= f.x * a.x - f.y * a.y;
+      A[t].y -= f.x * a.y + f.y * a.x;
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < nc * nc; t += blockDim.x) {
+    const int i = t / nc, j = t % nc;
+    const double2 v = A[i * w2 + nc + j];
+    Xinv[((size_t)s * nc + i) * nc + j] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+void coarse_invert(const LevelGeom& G, CoarseOp& C, int* flags, cudaStream_t s) {
+  const size_t sm = sizeof(double2) * 2 * (size_t)C.nc * C.nc;
+  MG_CUDA(cudaFuncSetAttribute(k_coarse_invert, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_coarse_invert<<<G.nsites, 256, sm, s>>>(C.nc, C.X.as<float2>(), C.Xinv.as<float2>(), flags);
+  MG_LAUNCH();
+}
+
+// --------------------------------------------------------------------------- Philox / packing
+__global__ void k_philox_coarse(int nsites, int ndof, const int* lex_of, uint64_t seed, int level, int k, float2* out) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)nsites * ndof) return;
+  const int s = (int)(t / ndof), d = (int)(t % ndof);
+  const cx<double> z = philox_gauss(seed, level, k, lex_of[s], d);
+  out[t] = make_float2((float)z.re, (float)z.im);
+}
+
+void philox_coarse_vector(const LevelGeom& G, uint64_t seed, int level, int k, float* out, cudaStream_t s) {
+  const size_t n = G.vec_complex();
+  k_philox_coarse<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G.nsites, G.ndof, G.d_lex_of.as<int>(), seed, level, k,
+                                                              (float2*)out);
+  MG_LAUNCH();
+}
+
+__global__ void k_pack_coarse(int nsites, int ndof, const int* lex_of, const double2* abi, float2* v) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)nsites * ndof) return;
+  const int s = (int)(t / ndof), d = (int)(t % ndof);
+  const double2 z = abi[(size_t)lex_of[s] * ndof + d];
+  v[t] = make_float2((float)z.x, (float)z.y);
+}
+
+__global__ void k_unpack_coarse(int nsites, int ndof, const int* lex_of, const float2* v, double2* abi) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)nsites * ndof) return;
+  const int s = (int)(t / ndof), d = (int)(t % ndof);
+  const float2 z = v[t];
+  abi[(size_t)lex_of[s] * ndof + d] = make_double2(z.x, z.y);
+}
+
+void pack_coarse(const LevelGeom& G, const double* abi, float* v, cudaStream_t s) {
+  const size_t n = G.vec_complex();
+  k_pack_coarse<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G.nsites, G.ndof, G.d_lex_of.as<int>(), (const double2*)abi,
+                                                            (float2*)v);
+  MG_LAUNCH();
+}
+
+void unpack_coarse(const LevelGeom& G, const float* v, double* abi, cudaStream_t s) {
+  const size_t n = G.vec_complex();
+  k_unpack_coarse<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(G.nsites, G.ndof, G.d_lex_of.as<int>(), (const float2*)v,
+                                                              (double2*)abi);
+  MG_LAUNCH();
+}
+
+// --------------------------------------------------------------------------- block Gram-Schmidt
+struct GSArgs {
+  TArgs a;
+  const float* V;       // nv level vectors, vector k at V + k * vstride
+  size_t vstride;       // floats between consecutive vectors
+  double2* Q;           // [ncoarse][2][nv][L]
+  int L;                // nb * ndof / 2
+};
+
+__global__ void k_gs_gather(GSArgs g) {
+  const int cc = blockIdx.x;
+  const int nv = g.a.nv, hd = g.a.ndof / 2, L = g.L;
+  const size_t per = (size_t)2 * nv * L;
+  for (size_t t = threadIdx.x; t < per; t += blockDim.x) {
+    const int ch = (int)(t / ((size_t)nv * L));
+    const int k = (int)((t / L) % nv);
+    const int l = (int)(t % L);
+    const int i = l / hd, c = ch * hd + l % hd;
+    const int idx = g.a.blockmap[cc * g.a.nb + i];
+    const cx<float> z = fget(g.a.fa, g.V + (size_t)k * g.vstride, idx, c);
+    g.Q[(size_t)cc * per + t] = make_double2(z.re, z.im);
+  }
+}
+
+// one CTA per (coarse site, chirality): modified Gram-Schmidt, every vector
+// projected twice, FP64 accumulation; breakdown if the norm after projection
+// drops below 1e-10 of the norm before
+__global__ void k_block_gs(GSArgs g, int* flags) {
+  __shared__ double red[2][32];
+  const int blk = blockIdx.x;  // cc * 2 + ch
+  const int nv = g.a.nv, L = g.L;
+  double2* Q = g.Q + (size_t)blk * nv * L;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  auto block_sum2 = [&](double x, double y, double& ox, double& oy) {
+    x = warp_sum(x);
+    y = warp_sum(y);
+    __syncthreads();
+    if (lane == 0) {
+      red[0][wid] = x;
+      red[1][wid] = y;
+    }
+    __syncthreads();
+    double sx = 0, sy = 0;
+    for (int q = 0; q < nw; q++) {
+      sx += red[0][q];
+      sy += red[1][q];
+    }
+    ox = sx;
+    oy = sy;
+  };
+  for (int k = 0; k < nv; k++) {
+    double2* w = Q + (size_t)k * L;
+    double n0 = 0, dummy;
+    {
+      double a = 0;
+      for (int l = threadIdx.x; l < L; l += blockDim.x) a += w[l].x * w[l].x + w[l].y * w[l].y;
+      block_sum2(a, 0.0, n0, dummy);
+    }
+    for (int pass = 0; pass < 2; pass++)
+      for (int j = 0; j < k; j++) {
+        const double2* q = Q + (size_t)j * L;
+        double re = 0, im = 0;
+        for (int l = threadIdx.x; l < L; l += blockDim.x) {
+          re += q[l].x * w[l].x + q[l].y * w[l].y;
+          im += q[l].x * w[l].y - q[l].y * w[l].x;
+        }
+        double dre, dim;
+        block_sum2(re, im, dre, dim);
+        for (int l = threadIdx.x; l < L; l += blockDim.x) {
+          w[l].x -= dre * q[l].x - dim * q[l].y;
+          w[l].y -= dre * q[l].y + dim * q[l].x;
+        }
+        __syncthreads();
+      }
+    double n1 = 0;
+    {
+      double a = 0;
+      for (int l = threadIdx.x; l < L; l += blockDim.x) a += w[l].x * w[l].x + w[l].y * w[l].y;
+      block_sum2(a, 0.0, n1, dummy);
+    }
+    if (threadIdx.x == 0 && (!(n0 > 0) || !(sqrt(n1) >= 1e-10 * sqrt(n0)))) atomicExch(&flags[FLAG_GS_BREAKDOWN], 1);
+    const double f = n1 > 0 ? 1.0 / sqrt(n1) : 0.0;
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+      w[l].x *= f;
+      w[l].y *= f;
+    }
+    __syncthreads();
+  }
+}
+
+// scale per (coarse site, chirality): 1 for FP32 storage, else the largest
+// |Re|, |Im| of the tile so that the stored values lie in [-1, 1]
+template <int ST>
+__global__ void k_gs_scatter(GSArgs g, void* P, float* Ps) {
+  __shared__ float smax[2][32];
+  __shared__ float scale_s[2];
+  const int cc = blockIdx.x;
+  const int nv = g.a.nv, hd = g.a.ndof / 2, L = g.L;
+  const size_t per = (size_t)2 * nv * L;
+  const double2* Qc = g.Q + (size_t)cc * per;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float m[2] = {0.f, 0.f};
+  if (ST != STORE_F32)
+    for (size_t t = threadIdx.x; t < per; t += blockDim.x) {
+      const int ch = (int)(t / ((size_t)nv * L));
+      const double2 z = Qc[t];
+      m[ch] = fmaxf(m[ch], fmaxf(fabsf((float)z.x), fabsf((float)z.y)));
+    }
+  for (int ch = 0; ch < 2; ch++) {
+    float v = m[ch];
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) smax[ch][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    float v = 0.f;
+    for (int q = 0; q < nw; q++) v = fmaxf(v, smax[threadIdx.x][q]);
+    scale_s[threadIdx.x] = (ST == STORE_F32 || v == 0.f) ? 1.f : v;
+    Ps[cc * 2 + threadIdx.x] = scale_s[threadIdx.x];
+  }
+  __syncthreads();
+  for (size_t t = threadIdx.x; t < per; t += blockDim.x) {
+    const int ch = (int)(t / ((size_t)nv * L));
+    const int k = (int)((t / L) % nv);
+    const int l = (int)(t % L);
+    const int i = l / hd, c = ch * hd + l % hd;
+    const double2 z = Qc[t];
+    const float inv = 1.f / scale_s[ch];
+    sput<ST>(P, ((size_t)(cc * g.a.nb + i) * g.a.ndof + c) * nv + k, mkc((float)z.x * inv, (float)z.y * inv));
+  }
+}
+
+void block_orthonormalize(TransferOp& T, const float* const* V, DBuf& scratch, int* flags, cudaStream_t s) {
+  GSArgs g;
+  g.a = targs(T);
+  g.V = V[0];
+  g.vstride = (T.nv > 1) ? (size_t)(V[1] - V[0]) : 0;
+  for (int k = 2; k < T.nv; k++)
+    if ((size_t)(V[k] - V[0]) != k * g.vstride) raise(MG_ERR_ARG, "null vectors must be equally spaced");
+  g.L = T.nb * T.fine_ndof / 2;
+  const size_t need = sizeof(double2) * (size_t)T.ncoarse * 2 * T.nv * g.L;
+  if (scratch.bytes() < need) scratch.alloc(need);
+  g.Q = scratch.as<double2>();
+  k_gs_gather<<<T.ncoarse, kBS, 0, s>>>(g);
+  MG_LAUNCH();
+  k_block_gs<<<T.ncoarse * 2, kBS, 0, s>>>(g, flags);
+  MG_LAUNCH();
+  switch (T.store) {
+    case STORE_F32: k_gs_scatter<STORE_F32><<<T.ncoarse, kBS, 0, s>>>(g, T.P.get(), T.Pscale.as<float>()); break;
+    case STORE_F16: k_gs_scatter<STORE_F16><<<T.ncoarse, kBS, 0, s>>>(g, T.P.get(), T.Pscale.as<float>()); break;
+    default: k_gs_scatter<STORE_BF16><<<T.ncoarse, kBS, 0, s>>>(g, T.P.get(), T.Pscale.as<float>()); break;
+  }
+  MG_LAUNCH();
+}
+
+}  // namespace mg

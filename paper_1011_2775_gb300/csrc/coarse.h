@@ -1,0 +1,103 @@
+// Multigrid data structures and the launchers of coarse.cu.
+//
+// A level is a lattice with `ndof` complex components per site.  The fine
+// level (Wilson, ndof = 12) stores vectors in the chunked even-odd layout of
+// common.cuh; coarse levels store [site][ndof] complex FP32 with sites in
+// even-odd order when every extent is even (lexicographic otherwise).  A
+// site's "storage index" is parity * half + checkerboard index (even-odd
+// levels) or its lexicographic index.
+//
+// Transfer l -> l+1 (prolongation P, restriction R = P^dag; sections
+// "Adaptive multigrid" and "Red-black preconditioning"): P is stored per
+// coarse site c and block-local fine site i as P[c][i][dof][k], k < Nv; the
+// column of entry (c, i, dof, k) is coarse dof chir(dof) * Nv + k with
+// chir(dof) = dof / (ndof/2) (the chirality split of the null vectors).
+// Coarse links (Galerkin operator): Y[c][row][d][col] for the 8 hops
+// d (d < 4: from c + mu, d >= 4: from c - mu) and X[c][row][col], Xinv.
+#pragma once
+#include <vector>
+
+#include "internal.h"
+
+namespace mg {
+
+// Storage format of prolongators / coarse links
+enum Store { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
+
+struct LevelGeom {
+  int L[4] = {0, 0, 0, 0};
+  int nsites = 0;
+  bool eo = false;     // even-odd ordering / preconditioning available
+  int half = 0;        // nsites / 2 when eo
+  int ndof = 0;
+  bool wilson = false; // fine level (chunked layout)
+  int Vh = 0;          // fine level: half volume (chunk stride)
+  std::vector<int> lex_of;  // storage -> lexicographic
+  std::vector<int> store_of;  // lexicographic -> storage
+  DBuf d_nbr;          // coarse levels: int[nsites][8] neighbour storage indices
+  DBuf d_lex_of;       // int[nsites]
+  void init(const int dims[4], int ndof_, bool wilson_);
+  int coord_to_store(const int c[4]) const;
+  size_t vec_complex() const { return (size_t)nsites * ndof; }
+};
+
+struct FineAccess {
+  int wilson;
+  int Vh;
+  int ndof;
+};
+
+struct TransferOp {
+  int block[4] = {1, 1, 1, 1};
+  int cdims[4] = {1, 1, 1, 1};
+  int nv = 0, fine_ndof = 0, nb = 0, ncoarse = 0;
+  int fine_half = 0;       // storage index < fine_half <=> even site (fine level even-odd)
+  int store = STORE_F32;
+  FineAccess fa{};
+  DBuf blockmap;           // int[ncoarse][nb] fine storage index
+  DBuf P;                  // [ncoarse][nb][fine_ndof][nv] in `store` format
+  DBuf Pscale;             // float[ncoarse][2]: per (block, chirality) scale (1 for FP32)
+};
+
+struct CoarseOp {
+  int nc = 0;
+  int store = STORE_F32;
+  DBuf Y;                  // [site][nc][8][nc] in `store` format
+  DBuf Yscale;             // float[site][8]: per (site, direction) scale
+  DBuf X, Xinv;            // [site][nc][nc] complex FP32
+};
+
+// ---- transfer kernels (coarse.cu)
+// out_c (coarse full vector) = R v; even_only: v's odd sites are taken as zero
+void restrict_vec(const TransferOp& T, float* out_c, const float* v, bool even_only, cudaStream_t s);
+// v = P in_c; even_only: only even sites of v are written
+void prolong_vec(const TransferOp& T, float* v, const float* in_c, bool even_only, cudaStream_t s);
+// p = column (chir, k) of P as a whole-lattice vector of the fine level
+void extract_column(const TransferOp& T, float* p, int chir, int k, cudaStream_t s);
+// Galerkin accumulation of one column: W[0..7] directional hops of u = M^{-1} p,
+// W[8] the identity-slot vector; writes column `col` of Y (faces) and X.
+void restrict9(const TransferOp& T, CoarseOp& C, const float* const W[9], int col, cudaStream_t s);
+
+// ---- coarse stencil kernels
+// out[s] = epi(sum_{d in mask} Y_d(s) in[nbr_d(s)]) for storage sites
+// s in [s0, s1); epilogues as the fine dslash (EPI_*), C = X or Xinv.
+void coarse_hop(const LevelGeom& G, const CoarseOp& C, Epilogue epi, bool use_inv, int s0, int s1, float* out,
+                const float* in, const float* x, float a, int dirmask, cudaStream_t s);
+// out[s] = C(s) in[s] (+ a x[s] if x) for s in [s0, s1)
+void coarse_site_mul(const LevelGeom& G, const CoarseOp& C, bool use_inv, int s0, int s1, float* out, const float* in,
+                     cudaStream_t s);
+// Xinv = X^{-1} per site (FP64 Gauss-Jordan); sets FLAG_SINGULAR on a tiny pivot
+void coarse_invert(const LevelGeom& G, CoarseOp& C, int* flags, cudaStream_t s);
+
+// ---- setup kernels
+// Philox start vector on a coarse level (AoS)
+void philox_coarse_vector(const LevelGeom& G, uint64_t seed, int level, int k, float* out, cudaStream_t s);
+// chirality split + block Gram-Schmidt of nv vectors V[k] (level vectors)
+// into T.P (and T.Pscale); sets FLAG_GS_BREAKDOWN on breakdown
+void block_orthonormalize(TransferOp& T, const float* const* V, DBuf& scratch, int* flags, cudaStream_t s);
+
+// ---- ABI packing of coarse vectors ([lex][ndof] complex128 <-> storage FP32)
+void pack_coarse(const LevelGeom& G, const double* abi, float* v, cudaStream_t s);
+void unpack_coarse(const LevelGeom& G, const float* v, double* abi, cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,279 @@
+// Host-side internals of libmgclover: the context, device workspace, error
+// handling and the kernel launchers each translation unit provides.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <functional>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "mgclover.h"
+
+namespace mg {
+
+// --------------------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string what;
+};
+
+[[noreturn]] void raise(int code, const std::string& what);
+void cuda_check(cudaError_t e, const char* expr, const char* file, int line);
+#define MG_CUDA(expr) ::mg::cuda_check((expr), #expr, __FILE__, __LINE__)
+// checks the last launch error (launch-configuration errors only; no sync)
+#define MG_LAUNCH() ::mg::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+
+// --------------------------------------------------------------------------- device memory
+// Owning device allocation (cudaMalloc / cudaFree).
+class DBuf {
+ public:
+  DBuf() = default;
+  explicit DBuf(size_t bytes) { alloc(bytes); }
+  ~DBuf() { release(); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : p_(o.p_), bytes_(o.bytes_) { o.p_ = nullptr; o.bytes_ = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); p_ = o.p_; bytes_ = o.bytes_; o.p_ = nullptr; o.bytes_ = 0; }
+    return *this;
+  }
+  void alloc(size_t bytes);
+  void release();
+  template <typename T>
+  T* as() const { return static_cast<T*>(p_); }
+  void* get() const { return p_; }
+  size_t bytes() const { return bytes_; }
+
+ private:
+  void* p_ = nullptr;
+  size_t bytes_ = 0;
+};
+
+// --------------------------------------------------------------------------- workspace
+// Reduction scratch, device scalars and error flags shared by all kernels of
+// one context.  Reductions are deterministic: fixed grid, per-block FP64
+// partials, then an ordered sum by the last block to finish.
+struct Workspace {
+  static constexpr int kMaxBlocks = 608;       // 4 x 152 SMs
+  static constexpr int kMaxResults = 136;      // doubles per reduction
+  static constexpr int kScalars = 16384;       // device scalar pool (doubles)
+  DBuf partials;                               // [kMaxBlocks][kMaxResults]
+  DBuf counter;                                // unsigned, self-resetting
+  DBuf scalars;                                // doubles
+  DBuf flags;                                  // int[16]
+  double* host = nullptr;                      // pinned mirror of the first scalars
+  void init();
+  ~Workspace();
+};
+
+enum Flag { FLAG_SINGULAR = 0, FLAG_GS_BREAKDOWN = 1, FLAG_NAN = 2, FLAG_COUNT = 16 };
+
+// --------------------------------------------------------------------------- fine level
+// dslash epilogues: out = f(H in), H the hopping term including its -1/2
+enum Epilogue { EPI_H = 0, EPI_CH = 1, EPI_XPAY = 2, EPI_CX_PAY = 3, EPI_C_XPAY = 4 };
+//  EPI_H:      out = H in
+//  EPI_CH:     out = C (H in)
+//  EPI_XPAY:   out = x + a H in
+//  EPI_CX_PAY: out = C x + a H in
+//  EPI_C_XPAY: out = C (x + a H in)
+
+void pack_spinor(const Geom& g, const double* abi, void* even, void* odd, bool fp32, cudaStream_t s);
+void unpack_spinor(const Geom& g, const void* even, const void* odd, bool fp32, double* abi, cudaStream_t s);
+void pack_gauge(const Geom& g, const double* abi, double* g64, float* g32, cudaStream_t s);
+void build_clover(const Geom& g, const double* g64, double csw, double m0, double* A64, double* Ainv64,
+                  float* A32, float* Ainv32, int* flags, cudaStream_t s);
+template <typename T>
+void clover_apply(const Geom& g, T* out, const T* in, const T* clov, cudaStream_t s);
+template <typename T>
+void dslash(const Geom& g, Epilogue epi, int parity, T* out, const T* in, const T* gauge, const T* clov,
+            const T* x, double a, int dirmask, cudaStream_t s);
+// the 8 directional terms H_d in (without summation), written to out[d]
+// (whole-lattice FP32 vectors, [even half][odd half] each)
+void hop_directions(const Geom& g, float* const out[8], const float* in_even, const float* in_odd,
+                    const float* gauge, cudaStream_t s);
+// Philox4x32-10 Gaussian start vector (see the generator's definition in coarse.cu)
+void philox_fine_vector(const Geom& g, uint64_t seed, int level, int k, float* even, float* odd, cudaStream_t s);
+
+// --------------------------------------------------------------------------- BLAS
+// Vectors are flat arrays of n complex numbers of precision T.
+template <typename T>
+void blas_zero(T* x, size_t n, cudaStream_t s);
+template <typename TI, typename TO>
+void blas_convert(TO* y, const TI* x, size_t n, cudaStream_t s);
+// y = a x + b y  (real a, b)
+template <typename T>
+void blas_axpby(double a, const T* x, double b, T* y, size_t n, cudaStream_t s);
+// ||x||^2 -> d_out[0] (device)
+template <typename T>
+void blas_norm2(const T* x, size_t n, double* d_out, Workspace& ws, cudaStream_t s);
+// <x, y> -> d_out[0..1] (device)
+template <typename T>
+void blas_cdot(const T* x, const T* y, size_t n, double* d_out, Workspace& ws, cudaStream_t s);
+// d_out[2j..2j+1] = <V_j, w>, j < k (k <= 64)
+template <typename T>
+void blas_multidot(const T* const* V, int k, const T* w, size_t n, double* d_out, Workspace& ws, cudaStream_t s);
+// w -= sum_j beta_j V_j (beta device complex, k may be 0), then
+// d_out = {||w||^2, Re<w,r>, Im<w,r>}
+template <typename T>
+void blas_orth_update(T* w, const T* const* V, const double* d_beta, int k, const T* r, size_t n, double* d_out,
+                      Workspace& ws, cudaStream_t s);
+// gamma = sqrt(d_in[0]); alpha = (d_in[1] + i d_in[2]) / gamma; w /= gamma;
+// r -= alpha w; stores alpha (2 doubles), gamma; d_rnorm2 = ||r||^2
+template <typename T>
+void blas_r_update(T* w, T* r, size_t n, const double* d_in, double* d_alpha, double* d_gamma, double* d_rnorm2,
+                   Workspace& ws, cudaStream_t s);
+// x += scale * sum_j c_j Z_j (c device complex)
+template <typename T, typename TZ>
+void blas_lincomb(T* x, const TZ* const* Z, const double* d_c, int k, double scale, size_t n, cudaStream_t s);
+// GCR back substitution: c_j = (alpha_j - sum_{l>j} beta_{j,l} c_l) / gamma_j,
+// beta column-major with leading dimension ld: beta[(j + ld*l)*2 + {re,im}]
+void gcr_backsub(const double* d_beta, int ld, const double* d_alpha, const double* d_gamma, int k, double* d_c,
+                 cudaStream_t s);
+// minimal-residual step: alpha = <w,r>/<w,w> from d_in = {<w,w>, Re<w,r>, Im<w,r>};
+// e += alpha r; r -= alpha w
+template <typename T>
+void blas_mr_update(T* e, T* r, const T* w, const double* d_in, size_t n, cudaStream_t s);
+// x *= 1/sqrt(d_norm2[0])
+template <typename T>
+void blas_normalize(T* x, const double* d_norm2, size_t n, cudaStream_t s);
+// {<w,w>, Re<w,r>, Im<w,r>} -> d_out
+template <typename T>
+void blas_dot2(const T* w, const T* r, size_t n, double* d_out, Workspace& ws, cudaStream_t s);
+
+// --------------------------------------------------------------------------- context
+struct Level;     // multigrid level (coarse.cu / multigrid.cu)
+struct Hierarchy;
+
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  Geom g{};
+  int dims[4] = {0, 0, 0, 0};
+  size_t V = 0, Vh = 0;
+  Workspace ws;
+
+  // fields (internal layouts, see common.cuh)
+  DBuf gauge64, gauge32;                 // [2][4][9][Vh] complex
+  DBuf clov64, clovinv64;                // [2][72 Vh] doubles
+  DBuf clov32, clovinv32;                // [2][72 Vh] floats
+  bool have_gauge = false, have_clover = false;
+  double csw = 0, m0 = 0;
+
+  mg_params params{};
+  bool have_params = false;
+  std::shared_ptr<Hierarchy> mg;         // null until mg_setup (shared_ptr: Hierarchy is incomplete here)
+  std::vector<std::vector<double>> injected;  // per transfer: injected raw null vectors (host, complex128)
+  std::vector<int> injected_nv;
+
+  // host I/O staging
+  DBuf stage_in, stage_out;              // complex128 whole-lattice staging
+  long long dslash_launches = 0;
+  std::shared_ptr<void> solve_work;      // solve buffers (solver.cu), kept between calls
+
+  const double* A64(int p) const { return clov64.as<double>() + (size_t)p * 72 * Vh; }
+  const double* Ainv64(int p) const { return clovinv64.as<double>() + (size_t)p * 72 * Vh; }
+  const float* A32(int p) const { return clov32.as<float>() + (size_t)p * 72 * Vh; }
+  const float* Ainv32(int p) const { return clovinv32.as<float>() + (size_t)p * 72 * Vh; }
+  template <typename T>
+  const T* gauge() const;
+  template <typename T>
+  const T* A(int p) const;
+  template <typename T>
+  const T* Ainv(int p) const;
+
+  void sync();
+  double read_scalar(const double* d);            // sync + copy one double
+  void read_scalars(const double* d, double* h, int n);
+  int read_flag(int which, bool clear);
+};
+
+template <>
+inline const double* Ctx::gauge<double>() const { return gauge64.as<double>(); }
+template <>
+inline const float* Ctx::gauge<float>() const { return gauge32.as<float>(); }
+template <>
+inline const double* Ctx::A<double>(int p) const { return A64(p); }
+template <>
+inline const float* Ctx::A<float>(int p) const { return A32(p); }
+template <>
+inline const double* Ctx::Ainv<double>(int p) const { return Ainv64(p); }
+template <>
+inline const float* Ctx::Ainv<float>(int p) const { return Ainv32(p); }
+
+// --------------------------------------------------------------------------- fine operators
+// Even-odd operators of the fine level in precision T on half-lattice vectors
+// (12 Vh complex).  Temporaries are owned by the object.
+template <typename T>
+struct FineOps {
+  Ctx* c;
+  DBuf t1, t2;
+  explicit FineOps(Ctx* ctx);
+  size_t half_n() const { return 12 * c->Vh; }
+  // D_r y = y - H_eo A_o^{-1} H_oe A_e^{-1} y
+  void Dr(T* out_e, const T* in_e);
+  // b_r = b_e - H_eo A_o^{-1} b_o
+  void br(T* out_e, const T* b_e, const T* b_o);
+  // x_e = A_e^{-1} y_e, x_o = A_o^{-1}(b_o - H_oe x_e)
+  void reconstruct(T* x_e, T* x_o, const T* y_e, const T* b_o);
+  // full-lattice D, D_p, H, M, M^{-1}
+  void D(T* oe, T* oo, const T* ie, const T* io);
+  void Dp(T* oe, T* oo, const T* ie, const T* io);
+  void H(T* oe, T* oo, const T* ie, const T* io);
+  void M(T* oe, T* oo, const T* ie, const T* io, bool inverse);
+};
+
+// --------------------------------------------------------------------------- GCR
+// Flexible GCR(m) with deferred solution update (see solver.cu).
+template <typename T, typename TZ>
+class GCR {
+ public:
+  using Op = std::function<void(T* out, const T* in)>;
+  using Pre = std::function<void(TZ* z, const T* r)>;
+  struct Result {
+    int iterations = 0;
+    int restarts = 0;
+    double rnorm = 0;
+    bool converged = false;
+  };
+  GCR(Ctx* c, size_t n, int m);
+  // Solves A x = b.  x0_zero: start from x = 0 (x is overwritten), else from x.
+  // Checks ||r|| <= tol_abs after every iteration when check is true (one
+  // host sync per iteration); with check false it runs exactly maxit
+  // iterations without restarts and without host syncs.
+  Result solve(const Op& A, const Pre* M, T* x, const T* b, bool x0_zero, double tol_abs, int maxit, bool check);
+  T* residual() { return r_.as<T>(); }
+
+ private:
+  Ctx* c_;
+  size_t n_;
+  int m_;
+  std::vector<DBuf> W_, Z_;
+  DBuf r_, tmp_;
+  DBuf scal_;
+  double* s_;  // device scalars: beta[m*m*2], alpha[m*2], gamma[m], c[m*2], misc
+};
+
+// MR smoothing: e = MR_nu(A, r) from e = 0 (r is consumed as scratch)
+template <typename T>
+void mr_smooth(Ctx* c, const std::function<void(T*, const T*)>& A, T* e, T* r, T* w, size_t n, int nu,
+               double* d_scr);
+
+// --------------------------------------------------------------------------- solve drivers (solver.cu)
+int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int mode, mg_solve_info* info);
+
+// --------------------------------------------------------------------------- multigrid (multigrid.cu)
+void mg_build(Ctx* c, mg_setup_info* info);
+void mg_destroy_hierarchy(Ctx* c);
+// preconditioner of the fine D_r in FP32 (z_e, r_e half vectors)
+void mg_precondition(Ctx* c, float* z_e, const float* r_e);
+void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in_abi);
+void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv);
+void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof);
+void mg_reset_counters(Ctx* c);
+void mg_read_counters(Ctx* c, long long* coarse_iters);
+
+}  // namespace mg

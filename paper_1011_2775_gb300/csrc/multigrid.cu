@@ -1,0 +1,587 @@
+// Host driver of the adaptive multigrid preconditioner.
+//
+// Setup (section "Setup procedure"): for every transfer l, Nv near-null
+// vectors of level l's D_p by inverse iteration -- repeated GCR relaxations
+// on a random (Philox) vector, kept globally orthogonal to the vectors
+// already found, stopped when the Rayleigh quotient ||D_p v||^2 settles --
+// then the chirality split and block Gram-Schmidt into P_l, the Galerkin
+// coarse links R D_p P and their site inverses.
+//
+// Solve (section "Implementation"): the truly adaptive recursive cycle.  The
+// level-l cycle restricts (r_e, 0), solves the next level's reduced
+// even-odd system with GCR to a relative residual tol_coarse -- itself
+// preconditioned by the next cycle, down to an unpreconditioned GCR on the
+// coarsest lattice (without even-odd if an extent is odd) -- prolongs, keeps
+// the even part and post-smooths with minimal-residual steps on D_r.  For
+// D_p = [[1, X], [Y, 1]] the solution of D_p u = (r_e, 0) has
+// u_e = D_r^{-1} r_e, which is why a coarse space of D_p serves D_r.
+// The whole preconditioner runs in FP32.
+#include <chrono>
+#include <cmath>
+
+#include "coarse.h"
+
+namespace mg {
+
+// --------------------------------------------------------------------------- geometry
+void LevelGeom::init(const int dims[4], int ndof_, bool wilson_) {
+  nsites = 1;
+  eo = true;
+  for (int m = 0; m < 4; m++) {
+    L[m] = dims[m];
+    nsites *= dims[m];
+    if (dims[m] % 2) eo = false;
+  }
+  ndof = ndof_;
+  wilson = wilson_;
+  half = eo ? nsites / 2 : 0;
+  Vh = nsites / 2;
+  lex_of.assign(nsites, 0);
+  store_of.assign(nsites, 0);
+  for (int lex = 0; lex < nsites; lex++) {
+    int c[4], r = lex;
+    for (int m = 0; m < 4; m++) {
+      c[m] = r % L[m];
+      r /= L[m];
+    }
+    const int s = coord_to_store(c);
+    store_of[lex] = s;
+    lex_of[s] = lex;
+  }
+  if (!wilson) {
+    std::vector<int> nbr((size_t)nsites * 8);
+    for (int s = 0; s < nsites; s++) {
+      int c[4], r = lex_of[s];
+      for (int m = 0; m < 4; m++) {
+        c[m] = r % L[m];
+        r /= L[m];
+      }
+      for (int d = 0; d < 8; d++) {
+        int n[4] = {c[0], c[1], c[2], c[3]};
+        const int mu = d & 3;
+        n[mu] = (c[mu] + (d < 4 ? 1 : -1) + L[mu]) % L[mu];
+        nbr[(size_t)s * 8 + d] = coord_to_store(n);
+      }
+    }
+    d_nbr.alloc(sizeof(int) * nbr.size());
+    MG_CUDA(cudaMemcpy(d_nbr.get(), nbr.data(), sizeof(int) * nbr.size(), cudaMemcpyHostToDevice));
+    d_lex_of.alloc(sizeof(int) * nsites);
+    MG_CUDA(cudaMemcpy(d_lex_of.get(), lex_of.data(), sizeof(int) * nsites, cudaMemcpyHostToDevice));
+  }
+}
+
+int LevelGeom::coord_to_store(const int c[4]) const {
+  const int lex = c[0] + L[0] * (c[1] + L[1] * (c[2] + L[2] * c[3]));
+  if (wilson || eo) {
+    const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+    return par * (nsites / 2) + lex / 2;
+  }
+  return lex;
+}
+
+// --------------------------------------------------------------------------- hierarchy
+struct LevelWork {
+  DBuf tA, tB;             // coarse: full-vector temporaries of the even-odd operators
+  DBuf br, y;              // coarse: reduced rhs / solution
+  std::unique_ptr<GCR<float, float>> gcr;
+  DBuf rc, ec;             // next level's rhs / solution (this level's cycle)
+  DBuf res, w, e, z0;      // this level's half vectors for smoothing
+};
+
+struct Hierarchy {
+  int L = 0;
+  std::vector<LevelGeom> geo;
+  std::vector<CoarseOp> cop;
+  std::vector<TransferOp> tr;
+  std::vector<DBuf> nullvecs;
+  std::vector<LevelWork> work;
+  std::unique_ptr<FineOps<float>> F32;
+  std::vector<long long> iters;
+  DBuf gs_scratch;
+};
+
+namespace {
+
+size_t half_n(const Hierarchy& H, int l) {
+  const LevelGeom& G = H.geo[l];
+  return (size_t)(l == 0 ? G.Vh : G.half) * G.ndof;
+}
+size_t full_n(const Hierarchy& H, int l) { return H.geo[l].vec_complex(); }
+
+// ----- level operators (FP32); vectors are full-vector base pointers, even sites first
+void Dr_level(Ctx* c, Hierarchy& H, int l, float* out, const float* in) {
+  if (l == 0) {
+    H.F32->Dr(out, in);
+    return;
+  }
+  const LevelGeom& G = H.geo[l];
+  const CoarseOp& C = H.cop[l];
+  LevelWork& W = H.work[l];
+  float* tA = W.tA.as<float>();
+  float* tB = W.tB.as<float>();
+  coarse_site_mul(G, C, true, 0, G.half, tA, in, c->stream);                                    // X_e^{-1} y_e
+  coarse_hop(G, C, EPI_CH, true, G.half, G.nsites, tB, tA, nullptr, 0.f, 0xff, c->stream);      // X_o^{-1} Y_oe .
+  coarse_hop(G, C, EPI_XPAY, false, 0, G.half, out, tB, in, -1.f, 0xff, c->stream);            // y_e - Y_eo .
+}
+
+void br_level(Ctx* c, Hierarchy& H, int l, float* br, const float* b) {
+  const LevelGeom& G = H.geo[l];
+  const CoarseOp& C = H.cop[l];
+  float* tB = H.work[l].tB.as<float>();
+  coarse_site_mul(G, C, true, G.half, G.nsites, tB, b, c->stream);
+  coarse_hop(G, C, EPI_XPAY, false, 0, G.half, br, tB, b, -1.f, 0xff, c->stream);
+}
+
+void recon_level(Ctx* c, Hierarchy& H, int l, float* x, const float* y, const float* b) {
+  const LevelGeom& G = H.geo[l];
+  const CoarseOp& C = H.cop[l];
+  coarse_site_mul(G, C, true, 0, G.half, x, y, c->stream);
+  coarse_hop(G, C, EPI_C_XPAY, true, G.half, G.nsites, x, x, b, -1.f, 0xff, c->stream);
+}
+
+void Dfull_level(Ctx* c, Hierarchy& H, int l, float* out, const float* in) {
+  if (l == 0) {
+    H.F32->D(out, out + 24 * c->Vh, in, in + 24 * c->Vh);
+    return;
+  }
+  const LevelGeom& G = H.geo[l];
+  coarse_hop(G, H.cop[l], EPI_CX_PAY, false, 0, G.nsites, out, in, in, 1.f, 0xff, c->stream);
+}
+
+void Dp_level(Ctx* c, Hierarchy& H, int l, float* out, const float* in) {
+  if (l == 0) {
+    H.F32->Dp(out, out + 24 * c->Vh, in, in + 24 * c->Vh);
+    return;
+  }
+  const LevelGeom& G = H.geo[l];
+  float* tA = H.work[l].tA.as<float>();
+  coarse_site_mul(G, H.cop[l], true, 0, G.nsites, tA, in, c->stream);
+  coarse_hop(G, H.cop[l], EPI_XPAY, false, 0, G.nsites, out, tA, in, 1.f, 0xff, c->stream);
+}
+
+void Minv_level(Ctx* c, Hierarchy& H, int l, float* out, const float* in, bool inverse) {
+  if (l == 0) {
+    H.F32->M(out, out + 24 * c->Vh, in, in + 24 * c->Vh, inverse);
+    return;
+  }
+  const LevelGeom& G = H.geo[l];
+  coarse_site_mul(G, H.cop[l], inverse, 0, G.nsites, out, in, c->stream);
+}
+
+void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b);
+
+// ----- the cycle: z_e ~ D_r^{-1} r_e on level l
+void cycle(Ctx* c, Hierarchy& H, int l, float* z, const float* r) {
+  const mg_params& p = c->params;
+  LevelWork& W = H.work[l];
+  const TransferOp& T = H.tr[l];
+  const size_t n = half_n(H, l);
+  cudaStream_t s = c->stream;
+  double* scr = c->ws.scalars.as<double>() + 64 + 8 * l;
+  auto Dr = [&](float* o, const float* i) { Dr_level(c, H, l, o, i); };
+  float* res = W.res.as<float>();
+  float* w = W.w.as<float>();
+  float* e = W.e.as<float>();
+  const float* rin = r;
+  if (p.nu_pre > 0) {
+    blas_convert<float, float>(res, r, n, s);
+    mr_smooth<float>(c, Dr, z, res, w, n, p.nu_pre, scr);  // z = MR(r)
+    Dr(w, z);
+    blas_convert<float, float>(res, r, n, s);
+    blas_axpby<float>(-1.0, w, 1.0, res, n, s);
+    rin = res;
+  }
+  restrict_vec(T, W.rc.as<float>(), rin, true, s);
+  coarse_solve(c, H, l + 1, W.ec.as<float>(), W.rc.as<float>());
+  if (p.nu_pre > 0) {
+    float* z0 = W.z0.as<float>();
+    prolong_vec(T, z0, W.ec.as<float>(), true, s);
+    blas_axpby<float>(1.0, z0, 1.0, z, n, s);
+  } else {
+    prolong_vec(T, z, W.ec.as<float>(), true, s);
+  }
+  if (p.nu_post > 0) {
+    Dr(w, z);
+    blas_convert<float, float>(res, r, n, s);
+    blas_axpby<float>(-1.0, w, 1.0, res, n, s);
+    mr_smooth<float>(c, Dr, e, res, w, n, p.nu_post, scr);
+    blas_axpby<float>(1.0, e, 1.0, z, n, s);
+  }
+}
+
+void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
+  const mg_params& p = c->params;
+  const LevelGeom& G = H.geo[l];
+  LevelWork& W = H.work[l];
+  cudaStream_t s = c->stream;
+  double* scr = c->ws.scalars.as<double>() + 32 + l;
+  blas_norm2<float>(b, full_n(H, l), scr, c->ws, s);
+  const double bn = std::sqrt(c->read_scalar(scr));
+  if (bn == 0.0) {
+    blas_zero<float>(x, full_n(H, l), s);
+    return;
+  }
+  const double tol = p.tol_coarse * bn;
+  const bool has_next = l + 1 < H.L;
+  if (G.eo) {
+    float* br = W.br.as<float>();
+    float* y = W.y.as<float>();
+    br_level(c, H, l, br, b);
+    auto A = [&](float* o, const float* i) { Dr_level(c, H, l, o, i); };
+    GCR<float, float>::Pre pre = [&](float* z, const float* r) { cycle(c, H, l, z, r); };
+    auto res = W.gcr->solve(A, has_next ? &pre : nullptr, y, br, true, tol, p.maxit_coarse, true);
+    H.iters[l] += res.iterations;
+    recon_level(c, H, l, x, y, b);
+  } else {
+    auto A = [&](float* o, const float* i) { Dfull_level(c, H, l, o, i); };
+    auto res = W.gcr->solve(A, nullptr, x, b, true, tol, p.maxit_coarse, true);
+    H.iters[l] += res.iterations;
+  }
+}
+
+// ----- setup
+void fill_start_vector(Ctx* c, Hierarchy& H, int l, int k, float* v) {
+  const uint64_t seed = c->params.seed;
+  if (l == 0)
+    philox_fine_vector(c->g, seed, l, k, v, v + 24 * c->Vh, c->stream);
+  else
+    philox_coarse_vector(H.geo[l], seed, l, k, v, c->stream);
+}
+
+void find_null_vectors(Ctx* c, Hierarchy& H, int l, mg_setup_info* info) {
+  const mg_params& p = c->params;
+  const int nv = p.nv[l];
+  const size_t n = full_n(H, l);
+  cudaStream_t s = c->stream;
+  float* base = H.nullvecs[l].as<float>();
+  std::vector<const float*> found(nv);
+  for (int k = 0; k < nv; k++) found[k] = base + (size_t)k * 2 * n;
+  if (l < (int)c->injected.size() && !c->injected[l].empty()) {
+    DBuf stage(sizeof(double) * 2 * n);
+    for (int k = 0; k < nv; k++) {
+      MG_CUDA(cudaMemcpyAsync(stage.get(), c->injected[l].data() + (size_t)k * 2 * n, sizeof(double) * 2 * n,
+                              cudaMemcpyHostToDevice, s));
+      float* v = base + (size_t)k * 2 * n;
+      if (l == 0)
+        pack_spinor(c->g, stage.as<double>(), v, v + 24 * c->Vh, true, s);
+      else
+        pack_coarse(H.geo[l], stage.as<double>(), v, s);
+    }
+    c->sync();
+    if (info) info->vectors[l] = nv;
+    return;
+  }
+  const int inner = p.setup_inner > 0 ? p.setup_inner : 8;
+  GCR<float, float> gcr(c, n, inner);
+  DBuf vb(sizeof(float) * 2 * n), wb(sizeof(float) * 2 * n);
+  float* v = vb.as<float>();
+  float* w = wb.as<float>();
+  double* scr = c->ws.scalars.as<double>() + 256;
+  auto Dp = [&](float* o, const float* i) { Dp_level(c, H, l, o, i); };
+  int passes = 0;
+  double rq = 0;
+  for (int k = 0; k < nv; k++) {
+    float* x = base + (size_t)k * 2 * n;
+    fill_start_vector(c, H, l, k, v);
+    double rq_prev = -1;
+    for (int it = 0; it < p.setup_iters; it++) {
+      gcr.solve(Dp, nullptr, x, v, true, 0.0, inner, false);
+      for (int rep = 0; rep < 2 && k > 0; rep++) {
+        blas_multidot<float>(found.data(), k, x, n, scr, c->ws, s);
+        blas_lincomb<float, float>(x, found.data(), scr, k, -1.0, n, s);
+      }
+      blas_norm2<float>(x, n, scr + 200, c->ws, s);
+      blas_normalize<float>(x, scr + 200, n, s);
+      Dp(w, x);
+      blas_norm2<float>(w, n, scr + 201, c->ws, s);
+      rq = c->read_scalar(scr + 201);
+      if (!std::isfinite(rq)) raise(MG_ERR_NAN, "non-finite Rayleigh quotient in setup");
+      passes++;
+      blas_convert<float, float>(v, x, n, s);
+      if (rq_prev >= 0 && std::fabs(rq - rq_prev) < p.setup_rq_tol * rq) break;
+      rq_prev = rq;
+    }
+  }
+  if (info) {
+    info->vectors[l] = nv;
+    info->passes[l] = passes;
+    info->rq_last[l] = rq;
+  }
+}
+
+void build_coarse_links(Ctx* c, Hierarchy& H, int l) {
+  const mg_params& p = c->params;
+  TransferOp& T = H.tr[l];
+  CoarseOp& C = H.cop[l + 1];
+  const LevelGeom& Gc = H.geo[l + 1];
+  const int nv = T.nv, nc = 2 * nv;
+  const size_t n = full_n(H, l);
+  cudaStream_t s = c->stream;
+  C.nc = nc;
+  C.store = STORE_F32;
+  C.Y.alloc(sizeof(float2) * (size_t)Gc.nsites * nc * 8 * nc);
+  C.X.alloc(sizeof(float2) * (size_t)Gc.nsites * nc * nc);
+  C.Xinv.alloc(sizeof(float2) * (size_t)Gc.nsites * nc * nc);
+  C.Yscale.alloc(sizeof(float) * (size_t)Gc.nsites * 8);
+  {
+    std::vector<float> ones((size_t)Gc.nsites * 8, 1.f);
+    MG_CUDA(cudaMemcpyAsync(C.Yscale.get(), ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice, s));
+    c->sync();
+  }
+  DBuf pb(sizeof(float) * 2 * n), ub(sizeof(float) * 2 * n), mb(sizeof(float) * 2 * n);
+  std::vector<DBuf> Wb(8);
+  for (auto& b : Wb) b.alloc(sizeof(float) * 2 * n);
+  float* pv = pb.as<float>();
+  float* u = ub.as<float>();
+  float* mp = mb.as<float>();
+  float* Wp[8];
+  for (int d = 0; d < 8; d++) Wp[d] = Wb[d].as<float>();
+  const bool galerkin_dp = p.coarse_op != MG_COARSE_D;
+  for (int ch = 0; ch < 2; ch++)
+    for (int k = 0; k < nv; k++) {
+      extract_column(T, pv, ch, k, s);
+      const float* slot8 = pv;
+      const float* hop_in = pv;
+      if (galerkin_dp) {
+        Minv_level(c, H, l, u, pv, true);
+        hop_in = u;
+      } else {
+        Minv_level(c, H, l, mp, pv, false);
+        slot8 = mp;
+      }
+      if (l == 0) {
+        hop_directions(c->g, Wp, hop_in, hop_in + 24 * c->Vh, c->gauge<float>(), s);
+      } else {
+        const LevelGeom& G = H.geo[l];
+        for (int d = 0; d < 8; d++)
+          coarse_hop(G, H.cop[l], EPI_H, false, 0, G.nsites, Wp[d], hop_in, nullptr, 0.f, 1 << d, s);
+      }
+      const float* W9[9] = {Wp[0], Wp[1], Wp[2], Wp[3], Wp[4], Wp[5], Wp[6], Wp[7], slot8};
+      restrict9(T, C, W9, ch * nv + k, s);
+    }
+  coarse_invert(Gc, C, c->ws.flags.as<int>(), s);
+  if (c->read_flag(FLAG_SINGULAR, true)) raise(MG_ERR_SINGULAR_CLOVER, "singular coarse diagonal block");
+}
+
+void alloc_work(Ctx* c, Hierarchy& H) {
+  const mg_params& p = c->params;
+  for (int l = 0; l < H.L; l++) {
+    LevelWork& W = H.work[l];
+    const size_t nh = half_n(H, l), nf = full_n(H, l);
+    if (l >= 1) {
+      W.tA.alloc(sizeof(float) * 2 * nf);
+      W.tB.alloc(sizeof(float) * 2 * nf);
+      MG_CUDA(cudaMemset(W.tA.get(), 0, sizeof(float) * 2 * nf));
+      MG_CUDA(cudaMemset(W.tB.get(), 0, sizeof(float) * 2 * nf));
+      const int restart = p.restart_coarse > 0 ? p.restart_coarse : 32;
+      if (H.geo[l].eo) {
+        W.br.alloc(sizeof(float) * 2 * nh);
+        W.y.alloc(sizeof(float) * 2 * nh);
+        W.gcr.reset(new GCR<float, float>(c, nh, restart));
+      } else {
+        W.gcr.reset(new GCR<float, float>(c, nf, restart));
+      }
+    }
+    if (l + 1 < H.L) {
+      const size_t nfc = full_n(H, l + 1);
+      W.rc.alloc(sizeof(float) * 2 * nfc);
+      W.ec.alloc(sizeof(float) * 2 * nfc);
+      const size_t vec = l == 0 ? 2 * nh : 2 * nf;  // fine: half vectors; coarse: full-vector base
+      W.res.alloc(sizeof(float) * vec);
+      W.w.alloc(sizeof(float) * vec);
+      W.e.alloc(sizeof(float) * vec);
+      W.z0.alloc(sizeof(float) * vec);
+      MG_CUDA(cudaMemset(W.res.get(), 0, sizeof(float) * vec));
+      MG_CUDA(cudaMemset(W.w.get(), 0, sizeof(float) * vec));
+      MG_CUDA(cudaMemset(W.e.get(), 0, sizeof(float) * vec));
+      MG_CUDA(cudaMemset(W.z0.get(), 0, sizeof(float) * vec));
+    }
+  }
+}
+
+}  // namespace
+
+// --------------------------------------------------------------------------- entry points
+void mg_destroy_hierarchy(Ctx* c) { c->mg.reset(); }
+
+void mg_build(Ctx* c, mg_setup_info* info) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const mg_params& p = c->params;
+  c->mg.reset();
+  std::unique_ptr<Hierarchy> H(new Hierarchy());
+  H->L = p.levels;
+  H->geo.resize(p.levels);
+  H->cop.resize(p.levels);
+  H->tr.resize(p.levels > 1 ? p.levels - 1 : 0);
+  H->nullvecs.resize(p.levels > 1 ? p.levels - 1 : 0);
+  H->work.resize(p.levels);
+  H->iters.assign(p.levels, 0);
+  H->F32.reset(new FineOps<float>(c));
+  H->geo[0].init(c->dims, 12, true);
+  for (int l = 0; l + 1 < p.levels; l++) {
+    int cd[4];
+    for (int m = 0; m < 4; m++) cd[m] = H->geo[l].L[m] / p.block[l][m];
+    H->geo[l + 1].init(cd, 2 * p.nv[l], false);
+  }
+  alloc_work(c, *H);
+  for (int l = 0; l + 1 < p.levels; l++) {
+    const LevelGeom& G = H->geo[l];
+    const LevelGeom& Gc = H->geo[l + 1];
+    TransferOp& T = H->tr[l];
+    T.nv = p.nv[l];
+    T.fine_ndof = G.ndof;
+    T.nb = 1;
+    for (int m = 0; m < 4; m++) {
+      T.block[m] = p.block[l][m];
+      T.cdims[m] = Gc.L[m];
+      T.nb *= p.block[l][m];
+    }
+    T.ncoarse = Gc.nsites;
+    T.fine_half = l == 0 ? G.Vh : (G.eo ? G.half : G.nsites);
+    T.store = (p.storage == MG_STORE_FP16) ? STORE_F16 : (p.storage == MG_STORE_BF16 ? STORE_BF16 : STORE_F32);
+    T.fa.wilson = l == 0;
+    T.fa.Vh = G.Vh;
+    T.fa.ndof = G.ndof;
+    // block map: coarse storage index -> fine storage indices of its block (bx fastest)
+    std::vector<int> bm((size_t)T.ncoarse * T.nb);
+    for (int cs = 0; cs < Gc.nsites; cs++) {
+      int cc[4], r = Gc.lex_of[cs];
+      for (int m = 0; m < 4; m++) {
+        cc[m] = r % Gc.L[m];
+        r /= Gc.L[m];
+      }
+      for (int i = 0; i < T.nb; i++) {
+        int lc[4], q = i;
+        for (int m = 0; m < 4; m++) {
+          lc[m] = q % T.block[m];
+          q /= T.block[m];
+        }
+        int fc[4];
+        for (int m = 0; m < 4; m++) fc[m] = cc[m] * T.block[m] + lc[m];
+        bm[(size_t)cs * T.nb + i] = G.coord_to_store(fc);
+      }
+    }
+    T.blockmap.alloc(sizeof(int) * bm.size());
+    MG_CUDA(cudaMemcpy(T.blockmap.get(), bm.data(), sizeof(int) * bm.size(), cudaMemcpyHostToDevice));
+    const size_t esz = T.store == STORE_F32 ? sizeof(float2) : 4;
+    T.P.alloc(esz * (size_t)T.ncoarse * T.nb * T.fine_ndof * T.nv);
+    T.Pscale.alloc(sizeof(float) * 2 * (size_t)T.ncoarse);
+    H->nullvecs[l].alloc(sizeof(float) * 2 * full_n(*H, l) * T.nv);
+    MG_CUDA(cudaMemset(H->nullvecs[l].get(), 0, sizeof(float) * 2 * full_n(*H, l) * T.nv));
+
+    find_null_vectors(c, *H, l, info);
+    std::vector<const float*> V(T.nv);
+    for (int k = 0; k < T.nv; k++) V[k] = H->nullvecs[l].as<float>() + (size_t)k * 2 * full_n(*H, l);
+    block_orthonormalize(T, V.data(), H->gs_scratch, c->ws.flags.as<int>(), c->stream);
+    if (c->read_flag(FLAG_GS_BREAKDOWN, true)) raise(MG_ERR_GS_BREAKDOWN, "block Gram-Schmidt breakdown");
+    build_coarse_links(c, *H, l);
+    if (info) info->coarse_sites[l] = Gc.nsites;
+  }
+  H->gs_scratch.release();
+  c->sync();
+  c->mg = std::move(H);
+  if (info) info->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void mg_precondition(Ctx* c, float* z_e, const float* r_e) {
+  if (!c->mg) raise(MG_ERR_STATE, "multigrid not set up");
+  cycle(c, *c->mg, 0, z_e, r_e);
+}
+
+void mg_reset_counters(Ctx* c) {
+  if (c->mg) c->mg->iters.assign(c->mg->L, 0);
+}
+
+void mg_read_counters(Ctx* c, long long* coarse_iters) {
+  for (int l = 0; l < MG_MAX_LEVELS; l++) coarse_iters[l] = 0;
+  if (!c->mg) return;
+  for (int l = 0; l < c->mg->L && l < MG_MAX_LEVELS; l++) coarse_iters[l] = c->mg->iters[l];
+}
+
+void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof) {
+  if (level == 0) {
+    for (int m = 0; m < 4; m++) dims[m] = c->dims[m];
+    *ndof = 12;
+    return;
+  }
+  if (!c->mg || level >= c->mg->L) raise(MG_ERR_STATE, "level not set up");
+  for (int m = 0; m < 4; m++) dims[m] = c->mg->geo[level].L[m];
+  *ndof = c->mg->geo[level].ndof;
+}
+
+void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv) {
+  if (!c->mg || level + 1 >= c->mg->L) raise(MG_ERR_STATE, "transfer not set up");
+  Hierarchy& H = *c->mg;
+  if (nv != H.tr[level].nv) raise(MG_ERR_NV, "nv does not match the setup");
+  const size_t n = full_n(H, level);
+  for (int k = 0; k < nv; k++) {
+    const float* v = H.nullvecs[level].as<float>() + (size_t)k * 2 * n;
+    if (level == 0)
+      unpack_spinor(c->g, v, v + 24 * c->Vh, true, V_abi + (size_t)k * 2 * n, c->stream);
+    else
+      unpack_coarse(H.geo[level], v, V_abi + (size_t)k * 2 * n, c->stream);
+  }
+  c->sync();
+}
+
+// Apply `op` on a coarse level (level >= 1), or R / P from any level.
+void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in_abi) {
+  if (!c->mg) raise(MG_ERR_STATE, "multigrid not set up");
+  Hierarchy& H = *c->mg;
+  cudaStream_t s = c->stream;
+  auto pack = [&](int l, const double* abi, float* v) {
+    if (l == 0)
+      pack_spinor(c->g, abi, v, v + 24 * c->Vh, true, s);
+    else
+      pack_coarse(H.geo[l], abi, v, s);
+  };
+  auto unpack = [&](int l, const float* v, double* abi) {
+    if (l == 0)
+      unpack_spinor(c->g, v, v + 24 * c->Vh, true, abi, s);
+    else
+      unpack_coarse(H.geo[l], v, abi, s);
+  };
+  if (op == MG_OP_R || op == MG_OP_P) {
+    if (level < 0 || level + 1 >= H.L) raise(MG_ERR_ARG, "no transfer from this level");
+    DBuf fb(sizeof(float) * 2 * full_n(H, level)), cb(sizeof(float) * 2 * full_n(H, level + 1));
+    if (op == MG_OP_R) {
+      pack(level, in_abi, fb.as<float>());
+      restrict_vec(H.tr[level], cb.as<float>(), fb.as<float>(), false, s);
+      unpack(level + 1, cb.as<float>(), out_abi);
+    } else {
+      pack(level + 1, in_abi, cb.as<float>());
+      prolong_vec(H.tr[level], fb.as<float>(), cb.as<float>(), false, s);
+      unpack(level, fb.as<float>(), out_abi);
+    }
+    c->sync();
+    return;
+  }
+  if (level < 1 || level >= H.L) raise(MG_ERR_ARG, "coarse level out of range");
+  const LevelGeom& G = H.geo[level];
+  const size_t n = full_n(H, level);
+  DBuf ib(sizeof(float) * 2 * n), ob(sizeof(float) * 2 * n);
+  float* in = ib.as<float>();
+  float* out = ob.as<float>();
+  pack(level, in_abi, in);
+  MG_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * 2 * n, s));
+  switch (op) {
+    case MG_OP_D: Dfull_level(c, H, level, out, in); break;
+    case MG_OP_DP: Dp_level(c, H, level, out, in); break;
+    case MG_OP_M: Minv_level(c, H, level, out, in, false); break;
+    case MG_OP_MINV: Minv_level(c, H, level, out, in, true); break;
+    case MG_OP_HOP: coarse_hop(G, H.cop[level], EPI_H, false, 0, G.nsites, out, in, nullptr, 0.f, 0xff, s); break;
+    case MG_OP_DR:
+      if (!G.eo) raise(MG_ERR_DIMS, "level has an odd extent");
+      Dr_level(c, H, level, out, in);
+      break;
+    case MG_OP_BR:
+      if (!G.eo) raise(MG_ERR_DIMS, "level has an odd extent");
+      br_level(c, H, level, out, in);
+      break;
+    default: raise(MG_ERR_ARG, "unknown operator");
+  }
+  unpack(level, out, out_abi);
+  c->sync();
+}
+
+}  // namespace mg

@@ -1,0 +1,95 @@
+"""Convenience wrapper over the C ABI: one ``Solver`` per lattice.
+
+Marshalling only (see ``binding``): gauge fields, sources and solutions are
+complex128 numpy arrays (host) or torch CUDA tensors (device), in the ABI
+layouts; every operation runs in libmgclover.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import binding as B
+
+
+class Solver:
+    """``[D(U) + m] psi = eta`` on one lattice ``dims = (Lx, Ly, Lz, Lt)``."""
+
+    def __init__(self, dims, device: int = 0, stream: int | None = None):
+        self.dims = tuple(int(d) for d in dims)
+        self.ctx = B.mg_create(self.dims, device, stream)
+        self.params = B.mg_default_params()
+
+    # -- lifecycle
+    def close(self):
+        if self.ctx is not None:
+            B.mg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- configuration
+    def load_gauge(self, U):
+        B.mg_load_gauge(self.ctx, U)
+
+    def set_clover(self, csw: float, m0: float):
+        B.mg_set_clover(self.ctx, csw, m0)
+
+    def set_params(self, levels=None, blocks=None, nv=None, **kw):
+        p = self.params
+        if levels is not None:
+            p.levels = int(levels)
+        if blocks is not None:
+            for l, b in enumerate(blocks):
+                for m in range(4):
+                    p.block[l][m] = int(b[m])
+        if nv is not None:
+            for l, n in enumerate(nv):
+                p.nv[l] = int(n)
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise AttributeError(f"mg_params has no field {k}")
+            setattr(p, k, v)
+        B.mg_set_params(self.ctx, p)
+
+    def set_null_vectors(self, level: int, V):
+        B.mg_set_null_vectors(self.ctx, level, V, V.shape[0])
+
+    def get_null_vectors(self, level: int):
+        dims, ndof = self.level_info(level)
+        out = np.zeros((self.params.nv[level], dims[3], dims[2], dims[1], dims[0], ndof), dtype=np.complex128)
+        B.mg_get_null_vectors(self.ctx, level, out, out.shape[0])
+        return out
+
+    def setup(self):
+        return B.mg_setup(self.ctx)
+
+    def level_info(self, level: int):
+        return B.mg_level_info(self.ctx, level)
+
+    # -- work
+    def solve(self, eta, tol: float = 1e-10, mode: int = B.MG_MODE_MG, out=None, allow_not_converged=False):
+        """Solve for eta of shape ``(Lt, Lz, Ly, Lx, 4, 3)`` or ``(nrhs, ...)``."""
+        nrhs = 1 if eta.ndim == 6 else eta.shape[0]
+        if out is None:
+            out = eta.new_zeros(eta.shape) if not isinstance(eta, np.ndarray) else np.zeros_like(eta)
+        st, info = B.mg_solve(self.ctx, out, eta, nrhs, tol, mode, allow_not_converged)
+        return out, info
+
+    def apply(self, op: int, x, level: int = 0, prec: int = B.MG_FP64, out_shape=None):
+        if out_shape is None:
+            out = x.new_zeros(x.shape) if not isinstance(x, np.ndarray) else np.zeros_like(x)
+        else:
+            out = np.zeros(out_shape, dtype=np.complex128) if isinstance(x, np.ndarray) else x.new_zeros(out_shape)
+        nrhs = 1
+        B.mg_apply(self.ctx, op, level, out, x, nrhs, prec)
+        return out

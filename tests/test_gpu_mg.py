@@ -1,0 +1,202 @@
+"""GPU parity of the multigrid pieces and the solvers, through the C ABI.
+
+* Transfer and coarse operators by injection: the same Philox null vectors go
+  to the oracle and (via mg_set_null_vectors) to the GPU; R, P and the
+  coarse D_hat, D_hat_p, D_hat_r, X, X^{-1}, hop are compared (FP32 pipeline:
+  relative error <= 1e-5), for 2 and 3 levels.
+* Setup without injection: P^dag P = I and gamma_5 P = P gamma_5c hold.
+* Solves: EO-GCR and MG-GCR reach ||eta - D psi|| / ||eta|| <= 1e-10 with D
+  the oracle's FP64 operator applied to the returned psi.
+* Failure paths return their status codes.
+"""
+import numpy as np
+import pytest
+
+from gpu_common import TOL32, lib_built, rel
+from oracle.dirac import WilsonClover, norm2
+from oracle.multigrid import MGParams, Multigrid
+from oracle.philox import gaussian_vector
+from paper_1011_2775_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(dims, U, csw, m0):
+    lib_built()
+    from paper_1011_2775_gb300.solver import Solver
+    S = Solver(dims)
+    S.load_gauge(U)
+    S.set_clover(csw, m0)
+    return S
+
+
+def _vectors(seed, level, nv, shape, ndof):
+    return [gaussian_vector(seed, level, k, shape, ndof) for k in range(nv)]
+
+
+def _true_residual(W, psi, eta):
+    r = eta.reshape(W.shape + (12,)) - W.D(psi.reshape(W.shape + (12,)))
+    return np.sqrt(norm2(r) / norm2(eta))
+
+
+@pytest.fixture(scope="module")
+def injected3():
+    """3 levels on 8^4: blocks 2^4 (Nv = 8) then 2^4 (Nv = 6), vectors injected."""
+    dims = (8, 8, 8, 8)
+    U = I.make_gauge(dims, 0.3, 1, 0.5, 3001)
+    W = WilsonClover(U, 1.0, -0.2)
+    V0 = _vectors(77, 0, 8, W.shape, 12)
+    V1 = _vectors(78, 1, 6, (4, 4, 4, 4), 16)
+    prm = MGParams(blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 6])
+    mg = Multigrid(W, prm, null_vectors=[V0, V1])
+    S = _solver(dims, U, 1.0, -0.2)
+    S.set_params(levels=3, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 6])
+    S.set_null_vectors(0, np.ascontiguousarray(np.stack(V0)))
+    S.set_null_vectors(1, np.ascontiguousarray(np.stack(V1)))
+    S.setup()
+    yield dims, W, mg, S
+    S.close()
+
+
+def test_level_info(injected3):
+    dims, W, mg, S = injected3
+    assert S.level_info(1) == ((4, 4, 4, 4), 16)
+    assert S.level_info(2) == ((2, 2, 2, 2), 12)
+
+
+@pytest.mark.parametrize("level", [0, 1])
+def test_restrict_prolong_parity(injected3, level):
+    from paper_1011_2775_gb300 import binding as B
+    dims, W, mg, S = injected3
+    T = mg.transfers[level]
+    fine = mg.levels[level]
+    rng = np.random.default_rng(level)
+    v = rng.standard_normal(fine.shape + (fine.ndof,)) + 1j * rng.standard_normal(fine.shape + (fine.ndof,))
+    vc = rng.standard_normal(T.cshape + (2 * T.nv,)) + 1j * rng.standard_normal(T.cshape + (2 * T.nv,))
+    got_r = S.apply(B.MG_OP_R, np.ascontiguousarray(v), level=level, out_shape=vc.shape)
+    assert rel(got_r, T.restrict(v)) <= TOL32
+    got_p = S.apply(B.MG_OP_P, np.ascontiguousarray(vc), level=level, out_shape=v.shape)
+    assert rel(got_p, T.prolong(vc)) <= TOL32
+
+
+@pytest.mark.parametrize("level", [1, 2])
+@pytest.mark.parametrize("op", ["D", "DP", "DR", "BR", "M", "MINV", "HOP"])
+def test_coarse_operator_parity(injected3, level, op):
+    from paper_1011_2775_gb300 import binding as B
+    dims, W, mg, S = injected3
+    C = mg.levels[level]
+    rng = np.random.default_rng(10 + level)
+    v = rng.standard_normal(C.shape + (C.ndof,)) + 1j * rng.standard_normal(C.shape + (C.ndof,))
+    ref = {"D": C.D, "DP": C.Dp, "DR": lambda x: C.Dr(x * C.even), "BR": C.b_r, "M": C.M, "MINV": C.Minv,
+           "HOP": C.hop}[op](v)
+    got = S.apply(getattr(B, "MG_OP_" + op), np.ascontiguousarray(v), level=level)
+    assert rel(got, ref) <= TOL32
+
+
+def test_setup_P_orthonormal_and_chiral():
+    """Setup without injection: R P = I on coarse vectors (P^dag P = I) and
+    gamma_5 P = P gamma_5c."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (8, 8, 8, 8)
+    U = I.make_gauge(dims, 0.25, 2, 0.5, 4001)
+    S = _solver(dims, U, 1.0, -0.25)
+    S.set_params(levels=2, blocks=[(4, 4, 4, 4)], nv=[12], setup_iters=6)
+    info = S.setup()
+    assert info.vectors[0] == 12 and info.coarse_sites[0] == 16 and info.passes[0] >= 12
+    rng = np.random.default_rng(0)
+    cs = (2, 2, 2, 2, 24)
+    vc = rng.standard_normal(cs) + 1j * rng.standard_normal(cs)
+    pv = S.apply(B.MG_OP_P, vc, level=0, out_shape=(8, 8, 8, 8, 4, 3))
+    assert rel(S.apply(B.MG_OP_R, pv, level=0, out_shape=cs), vc) <= TOL32
+    g5c = np.concatenate([np.ones(12), -np.ones(12)])
+    pg = S.apply(B.MG_OP_P, np.ascontiguousarray(vc * g5c), level=0, out_shape=pv.shape)
+    g5 = np.array([1, 1, -1, -1])[:, None]
+    assert rel(pg, pv * g5) <= TOL32
+    # the vectors are globally orthonormal (setup keeps them orthogonal)
+    V = S.get_null_vectors(0).reshape(12, -1)
+    G = V.conj() @ V.T
+    assert np.abs(G - np.eye(12)).max() < 1e-4
+    S.close()
+
+
+@pytest.mark.parametrize("mode", ["eo", "mg2", "mg3"])
+def test_solve_true_residual(mode):
+    from paper_1011_2775_gb300 import binding as B
+    dims = (8, 8, 8, 16)
+    U = I.make_gauge(dims, 0.25, 3, 0.5, 5001)
+    W = WilsonClover(U, 1.0, -0.3)
+    S = _solver(dims, U, 1.0, -0.3)
+    if mode == "mg2":
+        S.set_params(levels=2, blocks=[(4, 4, 4, 4)], nv=[12])
+        S.setup()
+    elif mode == "mg3":
+        S.set_params(levels=3, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 8])
+        S.setup()
+    eta = I.gaussian_source(dims, 5002)
+    psi, info = S.solve(eta, 1e-10, B.MG_MODE_EO_GCR if mode == "eo" else B.MG_MODE_MG)
+    assert info.true_residual <= 1e-10
+    assert _true_residual(W, psi, eta) <= 1e-10
+    if mode != "eo":
+        assert info.coarse_iterations[1] > 0
+    S.close()
+
+
+def test_config1_mg_matches_oracle_solution():
+    """Config 1 (4^4, 2^4 blocks, Nv = 8): GPU and oracle MG-GCR solutions agree
+    within the conditioning of the 1e-10 residual."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (4, 4, 4, 4)
+    U = I.make_gauge(dims, 0.3, 0, 0.5, 1001)
+    W = WilsonClover(U, 1.0, -0.1)
+    S = _solver(dims, U, 1.0, -0.1)
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[8], seed=1003)
+    S.setup()
+    eta = I.gaussian_source(dims, 1002)
+    psi, info = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    x, oinfo = Multigrid(W, MGParams(blocks=[(2, 2, 2, 2)], nv=[8], seed=1003)).solve(eta.reshape(W.shape + (12,)))
+    assert _true_residual(W, psi, eta) <= 1e-10 and oinfo.true_residual <= 1e-10
+    assert np.linalg.norm(psi.ravel() - x.ravel()) / np.linalg.norm(x) < 1e-7
+    S.close()
+
+
+def test_error_paths():
+    from paper_1011_2775_gb300 import binding as B
+    dims = (4, 4, 4, 4)
+    lib_built()
+    from paper_1011_2775_gb300.solver import Solver
+    S = Solver(dims)
+    eta = I.gaussian_source(dims, 1)
+    with pytest.raises(B.MGError) as e:
+        S.set_clover(1.0, 0.0)
+    assert e.value.status == B.MG_ERR_STATE
+    S.load_gauge(I.unit_gauge(dims))
+    with pytest.raises(B.MGError) as e:
+        S.set_clover(1.0, -4.0)            # A = 0: singular clover
+    assert e.value.status == B.MG_ERR_SINGULAR_CLOVER
+    S.set_clover(1.0, 0.1)
+    with pytest.raises(B.MGError) as e:
+        S.solve(eta, 1e-10, B.MG_MODE_MG)  # no setup
+    assert e.value.status == B.MG_ERR_STATE
+    with pytest.raises(B.MGError) as e:
+        S.set_params(levels=2, blocks=[(3, 2, 2, 2)], nv=[4])
+    assert e.value.status == B.MG_ERR_DIMS
+    with pytest.raises(B.MGError) as e:
+        S.set_params(levels=2, blocks=[(1, 1, 1, 2)], nv=[13])  # a block's chiral subspace has dim 12
+    assert e.value.status == B.MG_ERR_NV
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[4])
+    V = np.stack([gaussian_vector(3, 0, k, (4, 4, 4, 4), 12) for k in range(4)])
+    V[3] = 2.0 * V[1] - 0.5 * V[0]        # locally dependent
+    S.set_null_vectors(0, np.ascontiguousarray(V))
+    with pytest.raises(B.MGError) as e:
+        S.setup()
+    assert e.value.status == B.MG_ERR_GS_BREAKDOWN
+    bad = eta.copy()
+    bad[0, 0, 0, 0, 0, 0] = np.nan
+    with pytest.raises(B.MGError) as e:
+        S.solve(bad, 1e-10, B.MG_MODE_EO_GCR)
+    assert e.value.status == B.MG_ERR_NAN
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[4], maxit_fine=3)
+    psi = np.zeros_like(eta)
+    st, info = B.mg_solve(S.ctx, psi, eta, 1, 1e-12, B.MG_MODE_EO_GCR, allow_not_converged=True)
+    assert st == B.MG_ERR_NOT_CONVERGED and info.outer_iterations <= 3 and np.isfinite(info.true_residual)
+    S.close()
