@@ -85,7 +85,10 @@ enum mg_op {
   MG_OP_MINV = 5,       /* M^{-1}                                                          */
   MG_OP_HOP = 6,        /* hopping term H alone                                            */
   MG_OP_R = 7,          /* restriction R = P^dag: level l vector -> level l+1 vector       */
-  MG_OP_P = 8           /* prolongation P: level l+1 vector -> level l vector              */
+  MG_OP_P = 8,          /* prolongation P: level l+1 vector -> level l vector              */
+  MG_OP_CYCLE = 9       /* one multigrid cycle K_l (the preconditioner of D_r on level l): */
+                        /* reads the even sites of `in`, writes z_e ~ D_r^{-1} r_e to the  */
+                        /* even sites of `out` and zeros its odd sites (FP32 arithmetic)   */
 };
 
 enum mg_prec { MG_FP64 = 0, MG_FP32 = 1 };

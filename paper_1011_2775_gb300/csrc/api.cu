@@ -337,10 +337,11 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
     check_where(where);
     if (!out || !in || nrhs < 1) mg::raise(MG_ERR_ARG, "bad apply arguments");
     if (prec != MG_FP64 && prec != MG_FP32) mg::raise(MG_ERR_ARG, "bad precision");
-    if (op < MG_OP_D || op > MG_OP_P) mg::raise(MG_ERR_ARG, "bad operator");
+    if (op < MG_OP_D || op > MG_OP_CYCLE) mg::raise(MG_ERR_ARG, "bad operator");
     if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
     if (level < 0 || level >= c->params.levels) mg::raise(MG_ERR_ARG, "level out of range");
-    if ((level > 0 || op == MG_OP_R || op == MG_OP_P) && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    if ((level > 0 || op == MG_OP_R || op == MG_OP_P || op == MG_OP_CYCLE) && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    if (op == MG_OP_CYCLE && level + 1 >= c->params.levels) mg::raise(MG_ERR_ARG, "no coarser level to cycle to");
     int ndof_in, ndof_out;
     const int lin = op == MG_OP_P ? level + 1 : level;
     const int lout = op == MG_OP_R ? level + 1 : level;
@@ -352,7 +353,7 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
     for (int r = 0; r < nrhs; r++) {
       const double* ip = si.ptr + (size_t)r * 2 * nin;
       double* op_ = so.ptr + (size_t)r * 2 * nout;
-      if (level > 0 || op == MG_OP_R || op == MG_OP_P) {
+      if (level > 0 || op == MG_OP_R || op == MG_OP_P || op == MG_OP_CYCLE) {
         mg::mg_apply_level(c, op, level, op_, ip);
         continue;
       }

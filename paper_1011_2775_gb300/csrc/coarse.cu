@@ -634,7 +634,11 @@ __global__ void k_gs_gather(GSArgs g) {
 
 // one CTA per (coarse site, chirality): modified Gram-Schmidt, every vector
 // projected twice, FP64 accumulation; breakdown if the norm after projection
-// drops below 1e-10 of the norm before
+// drops below kGSBreakdown of the norm before.  The vectors arrive in FP32,
+// so dependence is only resolvable to about 1e-7: the threshold is 1e-6
+// (the FP64 oracle uses 1e-10 on FP64 vectors).
+constexpr double kGSBreakdown = 1e-6;
+
 __global__ void k_block_gs(GSArgs g, int* flags) {
   __shared__ double red[2][32];
   const int blk = blockIdx.x;  // cc * 2 + ch
@@ -688,7 +692,7 @@ __global__ void k_block_gs(GSArgs g, int* flags) {
       for (int l = threadIdx.x; l < L; l += blockDim.x) a += w[l].x * w[l].x + w[l].y * w[l].y;
       block_sum2(a, 0.0, n1, dummy);
     }
-    if (threadIdx.x == 0 && (!(n0 > 0) || !(sqrt(n1) >= 1e-10 * sqrt(n0)))) atomicExch(&flags[FLAG_GS_BREAKDOWN], 1);
+    if (threadIdx.x == 0 && (!(n0 > 0) || !(sqrt(n1) >= kGSBreakdown * sqrt(n0)))) atomicExch(&flags[FLAG_GS_BREAKDOWN], 1);
     const double f = n1 > 0 ? 1.0 / sqrt(n1) : 0.0;
     for (int l = threadIdx.x; l < L; l += blockDim.x) {
       w[l].x *= f;

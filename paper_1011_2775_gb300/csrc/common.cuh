@@ -4,9 +4,10 @@
 // Internal layouts (chosen for coalesced, vectorised access on sm_103a; the
 // C ABI exchanges complex128 in lexicographic order and pack/unpack kernels
 // convert):
-//  * fine spinor, one parity: structure-of-chunks.  FP32: float4[6][Vh]
-//    (24 reals/site), FP64: double2[12][Vh].  Real index within a site is
-//    2*(3*spin + colour) + {0: re, 1: im}.  A whole-lattice fine vector is
+//  * fine spinor, one parity: structure-of-chunks, 6 chunks of two complex
+//    numbers per site -- FP32: float4[6][Vh], FP64: (2 x double2)[6][Vh] --
+//    so both precisions order the complex numbers identically.  Complex
+//    index within a site is 3*spin + colour.  A whole-lattice fine vector is
 //    [even half][odd half].
 //  * gauge, per (parity p, direction mu): complex[9][Vh], entry a*3+b of
 //    U_mu(x) for the site x of parity p with checkerboard index i.
@@ -129,30 +130,37 @@ struct SpinorIO<float> {
   }
 };
 
+// FP64 uses the same complex ordering as FP32 -- 6 chunks of two complex
+// numbers (32 bytes) per site -- so that element-wise precision conversion
+// of whole vectors (the mixed-precision GCR) keeps every component in place.
 template <>
 struct SpinorIO<double> {
-  // 12 double2 chunks per site
   static __device__ __forceinline__ void load(const double* base, int Vh, int i, cx<double> s[12]) {
     const double2* p = reinterpret_cast<const double2*>(base);
 #pragma unroll
-    for (int q = 0; q < 12; q++) {
-      double2 v = p[(size_t)q * Vh + i];
-      s[q] = mkc(v.x, v.y);
+    for (int q = 0; q < 6; q++) {
+      const double2 a = p[((size_t)q * Vh + i) * 2];
+      const double2 b = p[((size_t)q * Vh + i) * 2 + 1];
+      s[2 * q] = mkc(a.x, a.y);
+      s[2 * q + 1] = mkc(b.x, b.y);
     }
   }
   static __device__ __forceinline__ void store(double* base, int Vh, int i, const cx<double> s[12]) {
     double2* p = reinterpret_cast<double2*>(base);
 #pragma unroll
-    for (int q = 0; q < 12; q++) p[(size_t)q * Vh + i] = make_double2(s[q].re, s[q].im);
+    for (int q = 0; q < 6; q++) {
+      p[((size_t)q * Vh + i) * 2] = make_double2(s[2 * q].re, s[2 * q].im);
+      p[((size_t)q * Vh + i) * 2 + 1] = make_double2(s[2 * q + 1].re, s[2 * q + 1].im);
+    }
   }
   static __device__ __forceinline__ cx<double> get(const double* base, int Vh, int i, int c) {
     const double2* p = reinterpret_cast<const double2*>(base);
-    double2 v = p[(size_t)c * Vh + i];
+    double2 v = p[((size_t)(c >> 1) * Vh + i) * 2 + (c & 1)];
     return mkc(v.x, v.y);
   }
   static __device__ __forceinline__ void put(double* base, int Vh, int i, int c, cx<double> z) {
     double2* p = reinterpret_cast<double2*>(base);
-    p[(size_t)c * Vh + i] = make_double2(z.re, z.im);
+    p[((size_t)(c >> 1) * Vh + i) * 2 + (c & 1)] = make_double2(z.re, z.im);
   }
 };
 

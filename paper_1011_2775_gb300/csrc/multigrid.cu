@@ -556,6 +556,24 @@ void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in
     c->sync();
     return;
   }
+  if (op == MG_OP_CYCLE) {
+    if (level + 1 >= H.L) raise(MG_ERR_ARG, "no coarser level");
+    const size_t n = full_n(H, level);
+    DBuf ib(sizeof(float) * 2 * n), ob(sizeof(float) * 2 * n);
+    MG_CUDA(cudaMemsetAsync(ib.get(), 0, sizeof(float) * 2 * n, s));
+    MG_CUDA(cudaMemsetAsync(ob.get(), 0, sizeof(float) * 2 * n, s));
+    pack(level, in_abi, ib.as<float>());
+    if (level > 0) {  // even sites only: zero the odd half of the input
+      const LevelGeom& G = H.geo[level];
+      if (!G.eo) raise(MG_ERR_DIMS, "level has an odd extent");
+      MG_CUDA(cudaMemsetAsync(ib.as<float>() + 2 * (size_t)G.half * G.ndof, 0,
+                              sizeof(float) * 2 * (size_t)(G.nsites - G.half) * G.ndof, s));
+    }
+    cycle(c, H, level, ob.as<float>(), ib.as<float>());
+    unpack(level, ob.as<float>(), out_abi);
+    c->sync();
+    return;
+  }
   if (level < 1 || level >= H.L) raise(MG_ERR_ARG, "coarse level out of range");
   const LevelGeom& G = H.geo[level];
   const size_t n = full_n(H, level);

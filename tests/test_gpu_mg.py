@@ -123,9 +123,10 @@ def test_setup_P_orthonormal_and_chiral():
 def test_solve_true_residual(mode):
     from paper_1011_2775_gb300 import binding as B
     dims = (8, 8, 8, 16)
-    U = I.make_gauge(dims, 0.25, 3, 0.5, 5001)
-    W = WilsonClover(U, 1.0, -0.3)
-    S = _solver(dims, U, 1.0, -0.3)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 5001)
+    W = WilsonClover(U, 1.0, -0.6)
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(maxit_fine=5000)
     if mode == "mg2":
         S.set_params(levels=2, blocks=[(4, 4, 4, 4)], nv=[12])
         S.setup()
@@ -185,7 +186,7 @@ def test_error_paths():
     assert e.value.status == B.MG_ERR_NV
     S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[4])
     V = np.stack([gaussian_vector(3, 0, k, (4, 4, 4, 4), 12) for k in range(4)])
-    V[3] = 2.0 * V[1] - 0.5 * V[0]        # locally dependent
+    V[3] = 2.0 * V[1] - 0.5 * V[0]        # locally dependent (to FP32 rounding)
     S.set_null_vectors(0, np.ascontiguousarray(V))
     with pytest.raises(B.MGError) as e:
         S.setup()
@@ -199,4 +200,52 @@ def test_error_paths():
     psi = np.zeros_like(eta)
     st, info = B.mg_solve(S.ctx, psi, eta, 1, 1e-12, B.MG_MODE_EO_GCR, allow_not_converged=True)
     assert st == B.MG_ERR_NOT_CONVERGED and info.outer_iterations <= 3 and np.isfinite(info.true_residual)
+    S.close()
+
+
+@pytest.fixture(scope="module")
+def qcdlike():
+    """QCD-like field (plaquette ~0.7): 8^4, eps = 1.0 + 5 APE steps, m0 = -0.6;
+    2 levels with 2^4 blocks and Nv = 8 injected Philox vectors."""
+    dims = (8, 8, 8, 8)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 2001)
+    W = WilsonClover(U, 1.0, -0.6)
+    V0 = _vectors(91, 0, 8, W.shape, 12)
+    return dims, U, W, V0
+
+
+@pytest.mark.parametrize("nu", [0, 2])
+def test_cycle_parity(qcdlike, nu):
+    """One application of the preconditioner K (restrict, near-exact coarse
+    solve, prolong, nu MR steps) matches the oracle's cycle."""
+    from paper_1011_2775_gb300 import binding as B
+    dims, U, W, V0 = qcdlike
+    prm = dict(tol_coarse=1e-6, maxit_coarse=400, restart_coarse=64, nu_post=nu)
+    mg = Multigrid(W, MGParams(blocks=[(2, 2, 2, 2)], nv=[8], **prm), null_vectors=[V0])
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[8], **prm)
+    S.set_null_vectors(0, np.ascontiguousarray(np.stack(V0)))
+    S.setup()
+    r = I.gaussian_source(dims, 7)
+    got = S.apply(B.MG_OP_CYCLE, r, level=0)
+    ref = mg.cycle(0, r.reshape(W.shape + (12,)) * W.even).reshape(r.shape)
+    assert rel(got, ref) <= 1e-4
+    S.close()
+
+
+def test_mg_iterations_match_oracle(qcdlike):
+    """With the same injected null vectors the GPU MG-GCR needs about as many
+    outer iterations as the oracle's (FP32 preconditioner vs FP64)."""
+    from paper_1011_2775_gb300 import binding as B
+    dims, U, W, V0 = qcdlike
+    mg = Multigrid(W, MGParams(blocks=[(2, 2, 2, 2)], nv=[8]), null_vectors=[V0])
+    eta = I.gaussian_source(dims, 8)
+    _, oinfo = mg.solve(eta.reshape(W.shape + (12,)), 1e-10)
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[8])
+    S.set_null_vectors(0, np.ascontiguousarray(np.stack(V0)))
+    S.setup()
+    psi, info = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _true_residual(W, psi, eta) <= 1e-10
+    assert abs(info.outer_iterations - oinfo.outer_iterations) <= max(3, 0.2 * oinfo.outer_iterations)
     S.close()
