@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark: MG-GCR solve time to 1e-10 vs plain FP64 EO-GCR on GB300, and the
+fine dslash as a fraction of HBM peak.
+
+Workload (one step = one MG-GCR solve of one right-hand side to a true
+relative residual of 1e-10, setup excluded and timed separately): the
+16^3x32 Wilson-clover lattice with links exp(i eps H), eps = 0.25, H
+Gaussian traceless Hermitian, 5 APE steps (alpha = 0.5), csw = 1.0, at the
+lightest mass of the sweep, m0 = -0.35; 2-level multigrid with 4^4 blocks
+and Nv = 24 null vectors; FP32 preconditioner, FP64 outer GCR.
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own
+replica of the workload on its own GPU (no data-path collective); timings
+are the max over ranks.  ``--impl reference`` times the FP64 CPU oracle on
+the host cores instead (a bounded sample of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MG-GCR solve time to 1e-10 vs plain EO-GCR on GB300; dslash % HBM peak"
+DIMS = (16, 16, 16, 32)
+EPS, APE, ALPHA, CSW = 0.25, 5, 0.5, 1.0
+MASSES = (-0.2, -0.3, -0.35)
+GAUGE_SEED, SOURCE_SEED, NULLVEC_SEED = 2001, 2002, 2003
+MG = dict(levels=2, blocks=[(4, 4, 4, 4)], nv=[24])
+TOL = 1e-10
+HBM_DIMS = (32, 32, 32, 64)          # 1.1 GB per FP32 fused-dslash launch: far beyond the 129 MB L2
+L2_FLUSH_BYTES = 512 << 20
+CPU_SAMPLE_DR = 5                    # oracle D_r applications in one CPU sample
+
+
+def workload_name(m0):
+    return (f"wilson-clover {DIMS[0]}^3x{DIMS[3]}, eps={EPS}+{APE} APE(alpha={ALPHA}), csw={CSW}, m0={m0}, "
+            f"2-level MG 4^4 blocks Nv=24, tol 1e-10")
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- distributed plumbing
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group(backend="gloo")  # barrier and timing reductions only
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+def cpu_sample(m0: float, n_dr: int) -> dict:
+    """Times n_dr applications of the oracle's FP64 D_r on this workload, in a
+    single-threaded subprocess (run as ``python bench.py --cpu-sample``)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(m0), str(n_dr)],
+                         capture_output=True, text=True, env=env, timeout=900)
+    for line in out.stdout.splitlines()[::-1]:
+        if line.startswith("{"):
+            return json.loads(line)
+    raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
+
+
+def cpu_sample_main(m0: float, n_dr: int):
+    from oracle.dirac import WilsonClover
+    from paper_1011_2775_gb300 import inputs as I
+    U = I.make_gauge(DIMS, EPS, APE, ALPHA, GAUGE_SEED)
+    W = WilsonClover(U, CSW, m0)
+    y = I.gaussian_source(DIMS, SOURCE_SEED).reshape(W.shape + (12,)) * W.even
+    W.Dr(y)  # warm
+    t0 = time.perf_counter()
+    for _ in range(n_dr):
+        y = W.Dr(y)
+        y = y / max(1.0, float(abs(y).max()))
+    dt = time.perf_counter() - t0
+    print(json.dumps({"seconds": dt, "n_dr": n_dr, "ms_per_dr": 1e3 * dt / n_dr}))
+
+
+def profile_main(args):
+    import numpy as np
+    import torch
+    from paper_1011_2775_gb300 import binding as B
+    from paper_1011_2775_gb300 import build as build_mod
+    from paper_1011_2775_gb300 import inputs as I
+    from paper_1011_2775_gb300.solver import Solver
+
+    build_mod.build()
+    U = I.make_gauge(DIMS, EPS, APE, ALPHA, GAUGE_SEED)
+    if args.profile == "solve":
+        eta = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED)).cuda()
+        psi = torch.zeros_like(eta)
+        S = Solver(DIMS)
+        S.load_gauge(U)
+        S.set_clover(CSW, args.mass)
+        S.set_params(seed=NULLVEC_SEED, maxit_fine=2000, **MG)
+        S.setup()
+        for _ in range(args.warmup):
+            S.solve(eta, TOL, B.MG_MODE_MG, out=psi)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            _, info = S.solve(eta, TOL, B.MG_MODE_MG, out=psi)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile": "solve", "steps": args.steps, "kernel_launches": info.kernel_launches,
+                          "outer_iterations": info.outer_iterations, "true_residual": info.true_residual}))
+        S.close()
+    else:
+        reps = [h // d for h, d in zip(HBM_DIMS, DIMS)]
+        H = Solver(HBM_DIMS)
+        H.load_gauge(np.tile(U, (reps[3], reps[2], reps[1], reps[0], 1, 1, 1)))
+        H.set_clover(CSW, args.mass)
+        B.mg_benchmark_kernel(H.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, warmup=args.warmup, iters=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        ms, by = B.mg_benchmark_kernel(H.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, warmup=0, iters=args.steps)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile": "dslash", "launches": args.steps, "bytes_per_launch": by}))
+        H.close()
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_gpu(args, dist: Dist) -> dict:
+    import numpy as np
+    import torch
+    from paper_1011_2775_gb300 import binding as B
+    from paper_1011_2775_gb300 import build as build_mod
+    from paper_1011_2775_gb300 import inputs as I
+    from paper_1011_2775_gb300.solver import Solver
+
+    build_mod.build()
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    m0 = args.mass
+    U = I.make_gauge(DIMS, EPS, APE, ALPHA, GAUGE_SEED)
+    eta = I.gaussian_source(DIMS, SOURCE_SEED)
+    stream = torch.cuda.current_stream(dev)
+    S = Solver(DIMS, device=dev, stream=stream.cuda_stream)
+    S.load_gauge(U)
+    S.set_clover(CSW, m0)
+    S.set_params(seed=NULLVEC_SEED, maxit_fine=2000, **MG)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sinfo = S.setup()
+    setup_ms = 1e3 * (time.perf_counter() - t0)
+
+    eta_d = torch.from_numpy(eta).to(f"cuda:{dev}")
+    psi_d = torch.zeros_like(eta_d)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    for _ in range(args.warmup):
+        S.solve(eta_d, TOL, B.MG_MODE_MG, out=psi_d)
+    torch.cuda.synchronize()
+
+    # timed region: K solves, inputs resident in HBM, L2 flushed before each
+    clocks = Clocks(dev)
+    dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times, infos, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, info = S.solve(eta_d, TOL, B.MG_MODE_MG, out=psi_d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        infos.append(info)
+        launches += info.kernel_launches
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms = dist.max(sum(times) / len(times))
+    last = infos[-1]
+    assert last.true_residual <= TOL, f"true residual {last.true_residual}"
+
+    # end to end through the C ABI with host buffers (H2D of eta, D2H of psi inside)
+    psi_h = np.zeros_like(eta)
+    e2e_times = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, einfo = S.solve(eta, TOL, B.MG_MODE_MG, out=psi_h)
+        e2e_times.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms = dist.max(statistics.median(e2e_times))
+    nbytes = eta.nbytes
+
+    # plain FP64 even-odd GCR on the same system (bounded)
+    eo = None
+    if not args.no_eo:
+        S.set_params(seed=NULLVEC_SEED, maxit_fine=args.eo_maxit, **MG)
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, ei = B.mg_solve(S.ctx, psi_d, eta_d, 1, TOL, B.MG_MODE_EO_GCR, allow_not_converged=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        eo = {"ms": e0.elapsed_time(e1), "iterations": ei.outer_iterations, "true_residual": ei.true_residual,
+              "converged": st == B.MG_OK, "restart": 16, "iteration_cap": args.eo_maxit}
+    S.close()
+
+    # the fine dslash on a lattice far beyond L2 (HBM-resident)
+    reps = [h // d for h, d in zip(HBM_DIMS, DIMS)]
+    U_big = np.tile(U, (reps[3], reps[2], reps[1], reps[0], 1, 1, 1))  # periodic copy: valid SU(3) field
+    H = Solver(HBM_DIMS, device=dev, stream=stream.cuda_stream)
+    H.load_gauge(U_big)
+    H.set_clover(CSW, m0)
+    del U_big
+    kern = {}
+    for name, code, prec in [("dslash_clover_fp32", B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32),
+                             ("dslash_xpay_fp32", B.MG_KERNEL_DSLASH_XPAY, B.MG_FP32),
+                             ("dr_fp32", B.MG_KERNEL_DR, B.MG_FP32),
+                             ("dslash_clover_fp64", B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP64)]:
+        ms_k, by = B.mg_benchmark_kernel(H.ctx, code, prec, warmup=10, iters=50)
+        kern[name] = {"ms": ms_k, "bytes": by, "gbs": by / ms_k / 1e6}
+    H.close()
+    return dict(ms=ms, times=times, info=last, setup_ms=setup_ms, sinfo=sinfo, e2e_ms=e2e_ms, nbytes=nbytes,
+                eo=eo, kern=kern, clocks=clk, launches=launches // max(1, args.steps))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["mg", "reference"], default="mg")
+    ap.add_argument("--mass", type=float, default=MASSES[-1])
+    ap.add_argument("--no-eo", action="store_true", help="skip the plain EO-GCR comparison")
+    ap.add_argument("--eo-maxit", type=int, default=20000)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--profile", choices=["solve", "dslash"],
+                    help="for ncu --profile-from-start off: bracket `steps` solves (after setup and warm-up), or "
+                         "`steps` launches of the HBM-size FP32 fused dslash, with cudaProfilerStart/Stop; "
+                         "nothing else is run")
+    ap.add_argument("--cpu-sample", nargs=2, help=argparse.SUPPRESS)
+    args = ap.parse_args()
+    if args.cpu_sample:
+        cpu_sample_main(float(args.cpu_sample[0]), int(args.cpu_sample[1]))
+        return
+    if args.profile:
+        profile_main(args)
+        return
+    args.warmup = max(args.warmup, 0)
+    dist = Dist()
+    hbm_peak, peak_kind = load_peaks()
+
+    if args.impl == "reference":
+        if dist.rank != 0:
+            dist.close()
+            return
+        samples = []
+        for i in range(args.warmup + args.steps):
+            s = cpu_sample(args.mass, CPU_SAMPLE_DR)
+            if i >= args.warmup:
+                samples.append(s)
+        ms_dr = statistics.median(s["ms_per_dr"] for s in samples)
+        value = ms_dr * REFERENCE_DR_PER_SOLVE
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_name(args.mass)},
+                "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                                 "sample": f"{CPU_SAMPLE_DR} oracle D_r applications per step, projected to a solve "
+                                           f"by {REFERENCE_DR_PER_SOLVE} fine D_r applications (coarse work excluded)"},
+                "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        dist.close()
+        return
+
+    r = run_gpu(args, dist)
+    info = r["info"]
+    dr_per_solve = info.dslash_launches / 2.0
+    k = r["kern"]["dslash_clover_fp32"]
+    roof = {"kernel": "fused hop + clover-inverse dslash, FP32, 32^3x64 (HBM-resident)", "bound": "hbm",
+            "achieved": k["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": k["gbs"] / hbm_peak,
+            "traffic": None, "peak_kind": peak_kind, "bytes_per_launch": k["bytes"], "ms_per_launch": k["ms"]}
+    line = {"metric": METRIC, "value": r["ms"], "unit": "ms", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": workload_name(args.mass), "lattice": "16x16x16x32", "m0": args.mass,
+                       "mg": "2-level, 4^4 blocks, Nv=24, coarse tol 0.1, nu_post=4 MR",
+                       "precision": "FP64 outer GCR(16), FP32 preconditioner", "l2": "flushed before every solve",
+                       "parallelism": f"replicas x{dist.world}"},
+            "roofline": roof,
+            "e2e": {"value": r["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": r["nbytes"],
+                    "d2h_bytes_per_step": r["nbytes"]},
+            "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "solve": {"outer_iterations": info.outer_iterations, "coarse_iterations": info.coarse_iterations[1],
+                      "true_residual": info.true_residual, "fine_dr_applications": dr_per_solve,
+                      "step_ms": r["times"]},
+            "setup_ms": r["setup_ms"], "setup_passes": r["sinfo"].passes[0],
+            "eo_gcr": r["eo"], "kernels": r["kern"]}
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+        s = cpu_sample(args.mass, CPU_SAMPLE_DR)
+        line["cpu_baseline"] = {"value": s["ms_per_dr"] * dr_per_solve, "unit": "ms", "cores": 1, "kind": "oracle",
+                                "sample": f"{CPU_SAMPLE_DR} applications of the oracle's FP64 D_r on this workload "
+                                          f"({s['ms_per_dr']:.0f} ms each), projected by the {dr_per_solve:.0f} fine "
+                                          f"D_r applications of one MG solve; coarse work excluded"}
+    if dist.rank == 0:
+        print(json.dumps(line))
+    dist.close()
+
+
+# fine D_r applications of one MG-GCR solve of this workload (measured by the
+# GPU arm, solve.fine_dr_applications); used to project the reference arm's sample
+REFERENCE_DR_PER_SOLVE = 300
+
+if __name__ == "__main__":
+    main()

@@ -132,7 +132,16 @@ typedef struct {
   double true_residual;                     /* max over rhs of ||eta - D psi|| / ||eta||      */
   double solve_ms;                          /* wall time of the call                          */
   long long dslash_launches;                /* fine hopping-term launches in the call         */
+  long long kernel_launches;                /* all library kernel launches in the call        */
 } mg_solve_info;
+
+/* Kernels for mg_benchmark_kernel. */
+enum mg_kernel {
+  MG_KERNEL_DSLASH_CLOVER = 0,  /* fused hop + clover-inverse epilogue (t_o = A_o^{-1} H_oe s_e) */
+  MG_KERNEL_DSLASH_XPAY = 1,    /* fused hop + axpy epilogue (y_e - H_eo t_o)                    */
+  MG_KERNEL_DR = 2,             /* a whole D_r application (clover apply + the two kernels above) */
+  MG_KERNEL_COARSE_DR = 3       /* a whole coarse D_hat_r application on level 1 (needs setup)   */
+};
 
 /* Name of a status code (static string). */
 MG_API const char* mg_strerror(int status);
@@ -201,6 +210,21 @@ MG_API int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol,
  * need mg_setup.  Errors: MG_ERR_ARG, MG_ERR_STATE, MG_ERR_DIMS (MG_OP_DR or
  * MG_OP_BR on a level with an odd extent), MG_ERR_CUDA. */
 MG_API int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, int prec, int where);
+
+/* Time one hot kernel in isolation on the context's resident fields (needs
+ * gauge and clover; MG_KERNEL_COARSE_DR needs setup): `warmup` untimed
+ * launches, then `iters` back-to-back launches bracketed by CUDA events on
+ * the context stream.  Returns the average milliseconds per launch and the
+ * algorithmic bytes one launch must move (every input field read once and
+ * the output written once, as counted for the roofline):
+ *   DSLASH_CLOVER: Vh * (8 links * 18 + 24 spinor + 72 clover + 24 out) reals,
+ *   DSLASH_XPAY:   Vh * (8 * 18 + 24 + 24 x + 24 out) reals,
+ *   DR:            the sum of its three kernels,
+ *   COARSE_DR:     Vc/2 * (18 Nc^2 link/inverse entries + 7 Nc vector entries) complex.
+ * `prec` selects FP64 or FP32 for the fine kernels.  Errors: MG_ERR_ARG,
+ * MG_ERR_STATE, MG_ERR_CUDA. */
+MG_API int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int iters, double* avg_ms,
+                               double* bytes_per_launch);
 
 /* Lattice size of level `level` after setup (dims_out[4] = {Lx,Ly,Lz,Lt})
  * and its dof per site (12 on the fine level, 2*nv[level-1] on coarse ones). */

@@ -33,9 +33,11 @@ MG_STORE_FP32, MG_STORE_FP16, MG_STORE_BF16 = 0, 1, 2
 MG_MODE_MG, MG_MODE_EO_GCR = 0, 1
 MG_COARSE_DP, MG_COARSE_D = 0, 1
 
+MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_DR = range(4)
+
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_solve", "mg_apply", "mg_level_info"]
+            "mg_solve", "mg_apply", "mg_benchmark_kernel", "mg_level_info"]
 
 
 class mg_params(ctypes.Structure):
@@ -71,7 +73,8 @@ class mg_solve_info(ctypes.Structure):
                 ("coarse_iterations", ctypes.c_longlong * MG_MAX_LEVELS),
                 ("true_residual", ctypes.c_double),
                 ("solve_ms", ctypes.c_double),
-                ("dslash_launches", ctypes.c_longlong)]
+                ("dslash_launches", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong)]
 
 
 class MGError(RuntimeError):
@@ -108,6 +111,7 @@ def lib() -> ctypes.CDLL:
             "mg_get_null_vectors": [vp, ip, vp, ip, ip],
             "mg_solve": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
+            "mg_benchmark_kernel": [vp, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_level_info": [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)],
         }
         for name, args in sig.items():
@@ -216,6 +220,14 @@ def mg_apply(ctx, op: int, level: int, out, x, nrhs: int = 1, prec: int = MG_FP6
     if wo != wi:
         raise TypeError("in and out must both be host or both be device buffers")
     _check(lib().mg_apply(ctx, int(op), int(level), po, pi, int(nrhs), int(prec), wo), "mg_apply")
+
+
+def mg_benchmark_kernel(ctx, kernel: int, prec: int = MG_FP32, warmup: int = 5, iters: int = 50):
+    """Returns ``(avg_ms_per_launch, algorithmic_bytes_per_launch)``."""
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mg_benchmark_kernel(ctx, int(kernel), int(prec), int(warmup), int(iters), ctypes.byref(ms),
+                                     ctypes.byref(by)), "mg_benchmark_kernel")
+    return ms.value, by.value
 
 
 def mg_level_info(ctx, level: int):

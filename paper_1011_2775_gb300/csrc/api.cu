@@ -313,6 +313,7 @@ int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mo
     local.true_residual = 0.0;
     mg::mg_reset_counters(c);
     const long long launches0 = c->dslash_launches;
+    const long long kernels0 = mg::launches_so_far();
     const size_t per = sizeof(double) * 24 * c->V;
     Staged si, so;
     stage_in(c, si, eta, per * nrhs, where);
@@ -325,6 +326,7 @@ int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mo
     stage_out_finish(c, so, psi, per * nrhs, where);
     mg::mg_read_counters(c, local.coarse_iterations);
     local.dslash_launches = c->dslash_launches - launches0;
+    local.kernel_launches = mg::launches_so_far() - kernels0;
     local.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = local;
     return status;
@@ -390,6 +392,69 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
       c->sync();
     }
     stage_out_finish(c, so, out, sizeof(double) * 2 * nout * nrhs, where);
+    return MG_OK;
+  });
+}
+
+int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int iters, double* avg_ms,
+                        double* bytes_per_launch) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!avg_ms || !bytes_per_launch || iters < 1 || warmup < 0) mg::raise(MG_ERR_ARG, "bad benchmark arguments");
+    if (prec != MG_FP64 && prec != MG_FP32) mg::raise(MG_ERR_ARG, "bad precision");
+    if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
+    if (kernel == MG_KERNEL_COARSE_DR) {
+      mg::mg_benchmark_coarse(c, warmup, iters, avg_ms, bytes_per_launch);
+      return MG_OK;
+    }
+    if (kernel < MG_KERNEL_DSLASH_CLOVER || kernel > MG_KERNEL_DR) mg::raise(MG_ERR_ARG, "bad kernel");
+    const bool f32 = prec == MG_FP32;
+    const size_t half_reals = 24 * c->Vh;
+    mg::DBuf a32(sizeof(float) * 2 * half_reals);
+    mg::philox_fine_vector(c->g, 12345, 0, 0, a32.as<float>(), a32.as<float>() + half_reals, c->stream);
+    cudaEvent_t e0, e1;
+    MG_CUDA(cudaEventCreate(&e0));
+    MG_CUDA(cudaEventCreate(&e1));
+    double ms = 0, bytes = 0;
+    auto run = [&](auto* tag) {
+      using T = std::remove_pointer_t<decltype(tag)>;
+      mg::DBuf in(sizeof(T) * half_reals), x(sizeof(T) * half_reals), out(sizeof(T) * half_reals);
+      mg::blas_convert<float, T>(in.as<T>(), a32.as<float>(), half_reals / 2, c->stream);
+      mg::blas_convert<float, T>(x.as<T>(), a32.as<float>() + half_reals, half_reals / 2, c->stream);
+      mg::FineOps<T> F(c);
+      const mg::Geom& g = c->g;
+      auto launch = [&]() {
+        switch (kernel) {
+          case MG_KERNEL_DSLASH_CLOVER:
+            mg::dslash<T>(g, mg::EPI_CH, 1, out.as<T>(), in.as<T>(), c->gauge<T>(), c->Ainv<T>(1), nullptr, 0.0, 0xff,
+                          c->stream);
+            break;
+          case MG_KERNEL_DSLASH_XPAY:
+            mg::dslash<T>(g, mg::EPI_XPAY, 0, out.as<T>(), in.as<T>(), c->gauge<T>(), nullptr, x.as<T>(), -1.0, 0xff,
+                          c->stream);
+            break;
+          default: F.Dr(out.as<T>(), in.as<T>()); break;
+        }
+      };
+      for (int w = 0; w < warmup; w++) launch();
+      MG_CUDA(cudaEventRecord(e0, c->stream));
+      for (int it = 0; it < iters; it++) launch();
+      MG_CUDA(cudaEventRecord(e1, c->stream));
+      MG_CUDA(cudaEventSynchronize(e1));
+      float t = 0;
+      MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      ms = t / iters;
+      const double reals = kernel == MG_KERNEL_DSLASH_CLOVER ? 264.0 : (kernel == MG_KERNEL_DSLASH_XPAY ? 216.0 : 600.0);
+      bytes = reals * sizeof(T) * (double)c->Vh;
+    };
+    if (f32)
+      run((float*)nullptr);
+    else
+      run((double*)nullptr);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *avg_ms = ms;
+    *bytes_per_launch = bytes;
     return MG_OK;
   });
 }

@@ -23,9 +23,12 @@ struct Error {
 
 [[noreturn]] void raise(int code, const std::string& what);
 void cuda_check(cudaError_t e, const char* expr, const char* file, int line);
+// counts one kernel launch and checks its launch error (configuration errors
+// only; no sync)
+void launch_check(const char* file, int line);
+long long launches_so_far();
 #define MG_CUDA(expr) ::mg::cuda_check((expr), #expr, __FILE__, __LINE__)
-// checks the last launch error (launch-configuration errors only; no sync)
-#define MG_LAUNCH() ::mg::cuda_check(cudaGetLastError(), "kernel launch", __FILE__, __LINE__)
+#define MG_LAUNCH() ::mg::launch_check(__FILE__, __LINE__)
 
 // --------------------------------------------------------------------------- device memory
 // Owning device allocation (cudaMalloc / cudaFree).
@@ -274,6 +277,8 @@ void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in
 void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv);
 void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof);
 void mg_reset_counters(Ctx* c);
+// times `iters` applications of the level-1 coarse D_hat_r (see mg_benchmark_kernel)
+void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes);
 void mg_read_counters(Ctx* c, long long* coarse_iters);
 
 }  // namespace mg

@@ -488,6 +488,31 @@ void mg_precondition(Ctx* c, float* z_e, const float* r_e) {
   cycle(c, *c->mg, 0, z_e, r_e);
 }
 
+void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes) {
+  if (!c->mg || c->mg->L < 2) raise(MG_ERR_STATE, "multigrid not set up");
+  Hierarchy& H = *c->mg;
+  const LevelGeom& G = H.geo[1];
+  if (!G.eo) raise(MG_ERR_DIMS, "level 1 has an odd extent");
+  const size_t n = full_n(H, 1);
+  DBuf ib(sizeof(float) * 2 * n), ob(sizeof(float) * 2 * n);
+  philox_coarse_vector(G, 777, 1, 0, ib.as<float>(), c->stream);
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  for (int w = 0; w < warmup; w++) Dr_level(c, H, 1, ob.as<float>(), ib.as<float>());
+  MG_CUDA(cudaEventRecord(e0, c->stream));
+  for (int it = 0; it < iters; it++) Dr_level(c, H, 1, ob.as<float>(), ib.as<float>());
+  MG_CUDA(cudaEventRecord(e1, c->stream));
+  MG_CUDA(cudaEventSynchronize(e1));
+  float t = 0;
+  MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *avg_ms = t / iters;
+  const double nc = H.cop[1].nc;
+  *bytes = (double)G.half * (18.0 * nc * nc + 7.0 * nc) * sizeof(float2);
+}
+
 void mg_reset_counters(Ctx* c) {
   if (c->mg) c->mg->iters.assign(c->mg->L, 0);
 }

@@ -8,6 +8,7 @@
 // cycle (back substitution of the triangular system).  In exact arithmetic
 // this is the textbook flexible GCR; deferring the update lets the
 // preconditioned directions z_j stay in the preconditioner's precision.
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -25,6 +26,17 @@ void cuda_check(cudaError_t e, const char* expr, const char* file, int line) {
   if (e == cudaErrorMemoryAllocation) raise(MG_ERR_ALLOC, msg);
   raise(MG_ERR_CUDA, msg);
 }
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void launch_check(const char* file, int line) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cuda_check(cudaGetLastError(), "kernel launch", file, line);
+}
+
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 void DBuf::alloc(size_t bytes) {
   release();
