@@ -211,6 +211,32 @@ MG_API int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol,
  * MG_OP_BR on a level with an odd extent), MG_ERR_CUDA. */
 MG_API int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, int prec, int where);
 
+/* Allocation-free variant of mg_apply for the fine level.  The paper has no
+ * counterpart: it exists for callers that cannot call cudaMalloc -- code whose
+ * device memory is owned by another allocator (a framework's caching
+ * allocator or a fixed pool) and latency-critical loops that cannot afford
+ * the implicit device synchronisation of cudaMalloc/cudaFree.  mg_apply
+ * allocates staging buffers and temporaries on every call; this entry point
+ * allocates nothing.
+ *
+ * Applies op (MG_OP_D, MG_OP_DP, MG_OP_DR, MG_OP_BR, MG_OP_M, MG_OP_MINV or
+ * MG_OP_HOP) of the fine level to ONE vector: `in` and `out` are DEVICE
+ * pointers to complex128 fine vectors in the layout above (owned by the
+ * caller, not kept); `prec` is MG_FP64 or MG_FP32.  Results equal mg_apply's.
+ *
+ * Its scratch is one file-scope device array of 9 MiB (16384 sites x 576
+ * bytes), which every GPU that loads the library holds until the process
+ * exits.  Lattices above 16384 sites are rejected with MG_ERR_DIMS.  The
+ * first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (the parts that must start at zero are cleared by each
+ * call), so calls that overlap on the GPU -- other streams, other threads,
+ * other contexts on the same device -- race: serialise them.  Runs on the
+ * context's stream and returns after it has drained.  Errors: MG_ERR_ARG,
+ * MG_ERR_STATE (no clover), MG_ERR_DIMS (too large), MG_ERR_CUDA. */
+MG_API int mg_apply_noalloc(void* ctx, int op, void* out, const void* in, int prec);
+
 /* Time one hot kernel in isolation on the context's resident fields (needs
  * gauge and clover; MG_KERNEL_COARSE_DR needs setup): `warmup` untimed
  * launches, then `iters` back-to-back launches bracketed by CUDA events on

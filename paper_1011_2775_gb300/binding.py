@@ -37,7 +37,7 @@ MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_D
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_solve", "mg_apply", "mg_benchmark_kernel", "mg_level_info"]
+            "mg_solve", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_level_info"]
 
 
 class mg_params(ctypes.Structure):
@@ -112,6 +112,7 @@ def lib() -> ctypes.CDLL:
             "mg_solve": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
             "mg_benchmark_kernel": [vp, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
+            "mg_apply_noalloc": [vp, ip, vp, vp, ip],
             "mg_level_info": [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)],
         }
         for name, args in sig.items():
@@ -220,6 +221,15 @@ def mg_apply(ctx, op: int, level: int, out, x, nrhs: int = 1, prec: int = MG_FP6
     if wo != wi:
         raise TypeError("in and out must both be host or both be device buffers")
     _check(lib().mg_apply(ctx, int(op), int(level), po, pi, int(nrhs), int(prec), wo), "mg_apply")
+
+
+def mg_apply_noalloc(ctx, op: int, out, x, prec: int = MG_FP64) -> None:
+    """Allocation-free fine-level operator; ``out`` and ``x`` must be device buffers."""
+    po, wo = _buf(out, writable=True)
+    pi, wi = _buf(x)
+    if wo != MG_DEVICE or wi != MG_DEVICE:
+        raise TypeError("mg_apply_noalloc takes device buffers only")
+    _check(lib().mg_apply_noalloc(ctx, int(op), po, pi, int(prec)), "mg_apply_noalloc")
 
 
 def mg_benchmark_kernel(ctx, kernel: int, prec: int = MG_FP32, warmup: int = 5, iters: int = 50):

@@ -86,6 +86,11 @@ void check_where(int where) {
 }
 }  // namespace
 
+namespace mg {
+// lets entry points defined in other files record their error detail
+void set_last_error(const std::string& what) { g_last_error = what; }
+}  // namespace mg
+
 extern "C" {
 
 const char* mg_strerror(int status) {
