@@ -23,6 +23,7 @@
 #include <cuda_fp16.h>
 
 #include "coarse.h"
+#include "coarse_dev.cuh"
 #include "philox.cuh"
 
 namespace mg {
@@ -350,8 +351,8 @@ struct HopArgs {
 };
 
 template <int EPI>
-__global__ void __launch_bounds__(128) k_coarse_hop(HopArgs h) {
-  extern __shared__ float2 sm[];  // vin[8 nc], t[nc], vx[nc]
+__global__ void __launch_bounds__(256) k_coarse_hop(HopArgs h) {
+  extern __shared__ __align__(16) float2 sm[];  // vin[8 nc], t[nc], vx[nc]
   const int nc = h.nc;
   const int s = h.s0 + blockIdx.x;
   float2* vin = sm;
@@ -372,48 +373,36 @@ __global__ void __launch_bounds__(128) k_coarse_hop(HopArgs h) {
     for (int t = threadIdx.x; t < nc; t += blockDim.x) vx[t] = h.x[(size_t)s * nc + t];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = w; i < nc; i += nw) {
-    const float2* row = h.Y + ((size_t)s * nc + i) * 8 * nc;
-    float re = 0.f, im = 0.f;
-    for (int q = lane; q < 8 * nc; q += 32) {
-      const float2 y = row[q], v = vin[q];
-      re += y.x * v.x - y.y * v.y;
-      im += y.x * v.y + y.y * v.x;
-    }
-    re = warp_sumf(re);
-    im = warp_sumf(im);
-    if (lane == 0) {
-      if (EPI == EPI_H) {
-        h.out[(size_t)s * nc + i] = make_float2(re, im);
-      } else if (EPI == EPI_XPAY) {
-        h.out[(size_t)s * nc + i] = make_float2(vx[i].x + h.a * re, vx[i].y + h.a * im);
-      } else if (EPI == EPI_CH || EPI == EPI_CX_PAY) {
-        tv[i] = make_float2(re, im);
-      } else {  // EPI_C_XPAY
-        tv[i] = make_float2(vx[i].x + h.a * re, vx[i].y + h.a * im);
+  const int rpw = (nc + nw - 1) / nw;
+  float2 res[kGemvMaxRows];
+  warp_gemv(h.Y + (size_t)s * nc * 8 * nc, nc, 8 * nc, vin, w, rpw, lane, res);
+  if (lane == 0)
+#pragma unroll
+    for (int r = 0; r < kGemvMaxRows; r++) {
+      const int i = w * rpw + r;
+      if (r < rpw && i < nc) {
+        if (EPI == EPI_H) h.out[(size_t)s * nc + i] = res[r];
+        else if (EPI == EPI_XPAY)
+          h.out[(size_t)s * nc + i] = make_float2(vx[i].x + h.a * res[r].x, vx[i].y + h.a * res[r].y);
+        else if (EPI == EPI_CH || EPI == EPI_CX_PAY) tv[i] = res[r];
+        else tv[i] = make_float2(vx[i].x + h.a * res[r].x, vx[i].y + h.a * res[r].y);  // EPI_C_XPAY
       }
     }
-  }
   if (EPI == EPI_H || EPI == EPI_XPAY) return;
   __syncthreads();
   const float2* src = (EPI == EPI_CX_PAY) ? vx : tv;
-  for (int i = w; i < nc; i += nw) {
-    const float2* row = h.C + ((size_t)s * nc + i) * nc;
-    float re = 0.f, im = 0.f;
-    for (int q = lane; q < nc; q += 32) {
-      const float2 y = row[q], v = src[q];
-      re += y.x * v.x - y.y * v.y;
-      im += y.x * v.y + y.y * v.x;
+  warp_gemv(h.C + (size_t)s * nc * nc, nc, nc, src, w, rpw, lane, res);
+  if (lane == 0)
+#pragma unroll
+    for (int r = 0; r < kGemvMaxRows; r++) {
+      const int i = w * rpw + r;
+      if (r < rpw && i < nc) {
+        if (EPI == EPI_CX_PAY)
+          h.out[(size_t)s * nc + i] = make_float2(res[r].x + h.a * tv[i].x, res[r].y + h.a * tv[i].y);
+        else
+          h.out[(size_t)s * nc + i] = res[r];
+      }
     }
-    re = warp_sumf(re);
-    im = warp_sumf(im);
-    if (lane == 0) {
-      if (EPI == EPI_CX_PAY)
-        h.out[(size_t)s * nc + i] = make_float2(re + h.a * tv[i].x, im + h.a * tv[i].y);
-      else
-        h.out[(size_t)s * nc + i] = make_float2(re, im);
-    }
-  }
 }
 
 void coarse_hop(const LevelGeom& G, const CoarseOp& C, Epilogue epi, bool use_inv, int s0, int s1, float* out,
@@ -434,34 +423,31 @@ void coarse_hop(const LevelGeom& G, const CoarseOp& C, Epilogue epi, bool use_in
   const size_t sm = sizeof(float2) * 10 * (size_t)C.nc;
   const int nb = s1 - s0;
   switch (epi) {
-    case EPI_H: k_coarse_hop<EPI_H><<<nb, 128, sm, s>>>(h); break;
-    case EPI_CH: k_coarse_hop<EPI_CH><<<nb, 128, sm, s>>>(h); break;
-    case EPI_XPAY: k_coarse_hop<EPI_XPAY><<<nb, 128, sm, s>>>(h); break;
-    case EPI_CX_PAY: k_coarse_hop<EPI_CX_PAY><<<nb, 128, sm, s>>>(h); break;
-    case EPI_C_XPAY: k_coarse_hop<EPI_C_XPAY><<<nb, 128, sm, s>>>(h); break;
+    case EPI_H: k_coarse_hop<EPI_H><<<nb, 256, sm, s>>>(h); break;
+    case EPI_CH: k_coarse_hop<EPI_CH><<<nb, 256, sm, s>>>(h); break;
+    case EPI_XPAY: k_coarse_hop<EPI_XPAY><<<nb, 256, sm, s>>>(h); break;
+    case EPI_CX_PAY: k_coarse_hop<EPI_CX_PAY><<<nb, 256, sm, s>>>(h); break;
+    case EPI_C_XPAY: k_coarse_hop<EPI_C_XPAY><<<nb, 256, sm, s>>>(h); break;
   }
   MG_LAUNCH();
 }
 
-__global__ void __launch_bounds__(128) k_site_mul(int nc, int s0, const float2* __restrict__ C, float2* out,
+__global__ void __launch_bounds__(256) k_site_mul(int nc, int s0, const float2* __restrict__ C, float2* out,
                                                    const float2* __restrict__ in) {
-  extern __shared__ float2 sv[];
+  extern __shared__ __align__(16) float2 sv[];
   const int s = s0 + blockIdx.x;
   for (int t = threadIdx.x; t < nc; t += blockDim.x) sv[t] = in[(size_t)s * nc + t];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int i = w; i < nc; i += nw) {
-    const float2* row = C + ((size_t)s * nc + i) * nc;
-    float re = 0.f, im = 0.f;
-    for (int q = lane; q < nc; q += 32) {
-      const float2 y = row[q], v = sv[q];
-      re += y.x * v.x - y.y * v.y;
-      im += y.x * v.y + y.y * v.x;
+  const int rpw = (nc + nw - 1) / nw;
+  float2 res[kGemvMaxRows];
+  warp_gemv(C + (size_t)s * nc * nc, nc, nc, sv, w, rpw, lane, res);
+  if (lane == 0)
+#pragma unroll
+    for (int r = 0; r < kGemvMaxRows; r++) {
+      const int i = w * rpw + r;
+      if (r < rpw && i < nc) out[(size_t)s * nc + i] = res[r];
     }
-    re = warp_sumf(re);
-    im = warp_sumf(im);
-    if (lane == 0) out[(size_t)s * nc + i] = make_float2(re, im);
-  }
 }
 
 void coarse_site_mul(const LevelGeom& G, const CoarseOp& C, bool use_inv, int s0, int s1, float* out, const float* in,
@@ -469,7 +455,7 @@ void coarse_site_mul(const LevelGeom& G, const CoarseOp& C, bool use_inv, int s0
   (void)G;
   if (s1 <= s0) return;
   const float2* M = use_inv ? C.Xinv.as<float2>() : C.X.as<float2>();
-  k_site_mul<<<s1 - s0, 128, sizeof(float2) * C.nc, s>>>(C.nc, s0, M, (float2*)out, (const float2*)in);
+  k_site_mul<<<s1 - s0, 256, sizeof(float2) * C.nc, s>>>(C.nc, s0, M, (float2*)out, (const float2*)in);
   MG_LAUNCH();
 }
 

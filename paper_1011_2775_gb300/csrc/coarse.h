@@ -89,6 +89,18 @@ void coarse_site_mul(const LevelGeom& G, const CoarseOp& C, bool use_inv, int s0
 // Xinv = X^{-1} per site (FP64 Gauss-Jordan); sets FLAG_SINGULAR on a tiny pivot
 void coarse_invert(const LevelGeom& G, CoarseOp& C, int* flags, cudaStream_t s);
 
+// ---- the coarsest-level solve as one persistent cooperative kernel (coarse_gcr.cu)
+struct CoarseGCRBuffers {
+  int grid = 0;            // co-resident blocks of the cooperative launch
+  DBuf r, y, br, tA, tB, W, Z, partials, scal;
+  void init(const LevelGeom& G, int nc, int m);
+};
+// x = D_hat^{-1} b to ||b - D_hat x|| <= tol_rel ||b|| (or maxit iterations) by
+// GCR(m) on the reduced even-odd system (or on D_hat itself when the level has
+// an odd extent); adds the iterations run to *d_iters (device)
+void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuffers& B, int m, int maxit,
+                      double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s);
+
 // ---- setup kernels
 // Philox start vector on a coarse level (AoS)
 void philox_coarse_vector(const LevelGeom& G, uint64_t seed, int level, int k, float* out, cudaStream_t s);

@@ -84,6 +84,7 @@ struct LevelWork {
   DBuf tA, tB;             // coarse: full-vector temporaries of the even-odd operators
   DBuf br, y;              // coarse: reduced rhs / solution
   std::unique_ptr<GCR<float, float>> gcr;
+  CoarseGCRBuffers cg;     // coarsest level: buffers of the persistent solver
   DBuf rc, ec;             // next level's rhs / solution (this level's cycle)
   DBuf res, w, e, z0;      // this level's half vectors for smoothing
 };
@@ -97,6 +98,7 @@ struct Hierarchy {
   std::vector<LevelWork> work;
   std::unique_ptr<FineOps<float>> F32;
   std::vector<long long> iters;
+  DBuf d_iters;            // long long[MG_MAX_LEVELS]: iterations counted on the device
   DBuf gs_scratch;
 };
 
@@ -214,6 +216,13 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
   const LevelGeom& G = H.geo[l];
   LevelWork& W = H.work[l];
   cudaStream_t s = c->stream;
+  if (l + 1 == H.L) {
+    // coarsest level: one persistent kernel, no host round trip
+    const int restart = p.restart_coarse > 0 ? p.restart_coarse : 32;
+    coarse_gcr_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, b, x,
+                     H.d_iters.as<long long>() + l, c->ws.flags.as<int>(), s);
+    return;
+  }
   double* scr = c->ws.scalars.as<double>() + 32 + l;
   blas_norm2<float>(b, full_n(H, l), scr, c->ws, s);
   const double bn = std::sqrt(c->read_scalar(scr));
@@ -381,6 +390,7 @@ void alloc_work(Ctx* c, Hierarchy& H) {
       } else {
         W.gcr.reset(new GCR<float, float>(c, nf, restart));
       }
+      if (l + 1 == H.L) W.cg.init(H.geo[l], H.geo[l].ndof, restart);
     }
     if (l + 1 < H.L) {
       const size_t nfc = full_n(H, l + 1);
@@ -416,6 +426,8 @@ void mg_build(Ctx* c, mg_setup_info* info) {
   H->nullvecs.resize(p.levels > 1 ? p.levels - 1 : 0);
   H->work.resize(p.levels);
   H->iters.assign(p.levels, 0);
+  H->d_iters.alloc(sizeof(long long) * MG_MAX_LEVELS);
+  MG_CUDA(cudaMemset(H->d_iters.get(), 0, sizeof(long long) * MG_MAX_LEVELS));
   H->F32.reset(new FineOps<float>(c));
   H->geo[0].init(c->dims, 12, true);
   for (int l = 0; l + 1 < p.levels; l++) {
@@ -514,13 +526,19 @@ void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* 
 }
 
 void mg_reset_counters(Ctx* c) {
-  if (c->mg) c->mg->iters.assign(c->mg->L, 0);
+  if (!c->mg) return;
+  c->mg->iters.assign(c->mg->L, 0);
+  MG_CUDA(cudaMemsetAsync(c->mg->d_iters.get(), 0, sizeof(long long) * MG_MAX_LEVELS, c->stream));
 }
 
 void mg_read_counters(Ctx* c, long long* coarse_iters) {
   for (int l = 0; l < MG_MAX_LEVELS; l++) coarse_iters[l] = 0;
   if (!c->mg) return;
-  for (int l = 0; l < c->mg->L && l < MG_MAX_LEVELS; l++) coarse_iters[l] = c->mg->iters[l];
+  long long dev[MG_MAX_LEVELS];
+  MG_CUDA(cudaMemcpyAsync(dev, c->mg->d_iters.get(), sizeof(dev), cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+  for (int l = 0; l < c->mg->L && l < MG_MAX_LEVELS; l++) coarse_iters[l] = c->mg->iters[l] + dev[l];
+  if (c->read_flag(FLAG_NAN, true)) raise(MG_ERR_NAN, "non-finite residual in the coarse solve");
 }
 
 void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof) {
