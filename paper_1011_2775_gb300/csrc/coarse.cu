@@ -548,6 +548,85 @@ void coarse_invert(const LevelGeom& G, CoarseOp& C, int* flags, cudaStream_t s) 
   MG_LAUNCH();
 }
 
+// --------------------------------------------------------------------------- folded links
+// One CTA per (odd site o, direction d): A_d(o) = X^{-1}(o) Y_d(o) X^{-1}(o + d).
+__global__ void k_fold_eo(int nc, int half, const int* __restrict__ nbr, const float2* __restrict__ Y,
+                          const float* __restrict__ Ys, const float2* __restrict__ Xinv, float2* A) {
+  extern __shared__ __align__(16) float2 fs[];  // Xo, Yd, Xn, T: 4 nc^2
+  const int o = half + blockIdx.x, d = blockIdx.y;
+  const int n2 = nc * nc;
+  float2* Xo = fs;
+  float2* Yd = fs + n2;
+  float2* Xn = fs + 2 * n2;
+  float2* T = fs + 3 * n2;
+  const int nb = nbr[(size_t)o * 8 + d];
+  const float sc = Ys[(size_t)o * 8 + d];
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const int i = t / nc, j = t % nc;
+    Xo[t] = Xinv[(size_t)o * n2 + t];
+    const float2 y = Y[(((size_t)o * nc + i) * 8 + d) * nc + j];
+    Yd[t] = make_float2(sc * y.x, sc * y.y);
+    Xn[t] = Xinv[(size_t)nb * n2 + t];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {  // T = Yd Xn
+    const int i = t / nc, j = t % nc;
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < nc; k++) {
+      const float2 a = Yd[i * nc + k], b = Xn[k * nc + j];
+      re += a.x * b.x - a.y * b.y;
+      im += a.x * b.y + a.y * b.x;
+    }
+    T[t] = make_float2(re, im);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {  // A = Xo T
+    const int i = t / nc, j = t % nc;
+    float re = 0.f, im = 0.f;
+    for (int k = 0; k < nc; k++) {
+      const float2 a = Xo[i * nc + k], b = T[k * nc + j];
+      re += a.x * b.x - a.y * b.y;
+      im += a.x * b.y + a.y * b.x;
+    }
+    A[((((size_t)(o - half)) * nc + i) * 8 + d) * nc + j] = make_float2(re, im);
+  }
+}
+
+__global__ void k_cat_links(int nc, int nsites, const float2* __restrict__ Y, const float* __restrict__ Ys,
+                            const float2* __restrict__ X, float2* A) {
+  const size_t total = (size_t)nsites * nc * 9 * nc;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % nc);
+    const int d = (int)((t / nc) % 9);
+    const size_t row = t / ((size_t)9 * nc);  // s * nc + i
+    const size_t s = row / nc;
+    if (d < 8) {
+      const float2 y = Y[(row * 8 + d) * nc + j];
+      const float sc = Ys[s * 8 + d];
+      A[t] = make_float2(sc * y.x, sc * y.y);
+    } else {
+      A[t] = X[row * nc + j];
+    }
+  }
+}
+
+void coarse_fold_links(const LevelGeom& G, CoarseOp& C, cudaStream_t s) {
+  const int nc = C.nc;
+  if (G.eo) {
+    const int nodd = G.nsites - G.half;
+    C.A.alloc(sizeof(float2) * (size_t)nodd * nc * 8 * nc);
+    const size_t sm = sizeof(float2) * 4 * (size_t)nc * nc;
+    MG_CUDA(cudaFuncSetAttribute(k_fold_eo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    k_fold_eo<<<dim3(nodd, 8), 256, sm, s>>>(nc, G.half, G.d_nbr.as<int>(), C.Y.as<float2>(), C.Yscale.as<float>(),
+                                             C.Xinv.as<float2>(), C.A.as<float2>());
+  } else {
+    C.A.alloc(sizeof(float2) * (size_t)G.nsites * nc * 9 * nc);
+    k_cat_links<<<152 * 8, 256, 0, s>>>(nc, G.nsites, C.Y.as<float2>(), C.Yscale.as<float>(), C.X.as<float2>(),
+                                         C.A.as<float2>());
+  }
+  MG_LAUNCH();
+}
+
 // --------------------------------------------------------------------------- Philox / packing
 __global__ void k_philox_coarse(int nsites, int ndof, const int* lex_of, uint64_t seed, int level, int k, float2* out) {
   const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;

@@ -65,7 +65,15 @@ struct CoarseOp {
   DBuf Y;                  // [site][nc][8][nc] in `store` format
   DBuf Yscale;             // float[site][8]: per (site, direction) scale
   DBuf X, Xinv;            // [site][nc][nc] complex FP32
+  // Links with the site inverses folded in, for the persistent coarsest solve:
+  //  even-odd levels: A[o - half][nc][8][nc] = X_o^{-1} Y_d(o) X^{-1}(o + d) on odd
+  //  sites, so that (X_o^{-1} Y_oe X_e^{-1} y)(o) = sum_d A_d(o) y(o + d);
+  //  other levels: [site][nc][9][nc] = [Y_0 .. Y_7 | X], so D_hat v is one GEMV.
+  DBuf A;
 };
+
+// builds C.A from Y, X, Xinv (see CoarseOp)
+void coarse_fold_links(const LevelGeom& G, CoarseOp& C, cudaStream_t s);
 
 // ---- transfer kernels (coarse.cu)
 // out_c (coarse full vector) = R v; even_only: v's odd sites are taken as zero
@@ -92,6 +100,7 @@ void coarse_invert(const LevelGeom& G, CoarseOp& C, int* flags, cudaStream_t s);
 // ---- the coarsest-level solve as one persistent cooperative kernel (coarse_gcr.cu)
 struct CoarseGCRBuffers {
   int grid = 0;            // co-resident blocks of the cooperative launch
+  int nsplit = 1;          // work items per site in the stencil phases (row split)
   DBuf r, y, br, tA, tB, W, Z, partials, scal;
   void init(const LevelGeom& G, int nc, int m);
 };

@@ -18,12 +18,13 @@ __device__ __forceinline__ float gemv_wsum(float v) {
   return v;
 }
 
-// res[r] = sum_k M[row_r][k] * v[k] for the warp's rows row_r = w*rpw + r
-// (r < rpw, row_r < nrows).  M: global, row stride K complex (K even,
+// res[r] = sum_k M[row_r][k] * v[k] for the warp's rows row_r = row0 + w*rpw + r
+// (r < rpw, row_r < row1).  M: global, row stride K complex (K even,
 // 16-byte aligned rows); v: shared memory, K complex, 16-byte aligned.
 // After the call every lane holds the full sums.
-__device__ __forceinline__ void warp_gemv(const float2* __restrict__ M, int nrows, int K, const float2* v, int w,
-                                          int rpw, int lane, float2 res[kGemvMaxRows]) {
+__device__ __forceinline__ void warp_gemv_rows(const float2* __restrict__ M, int row0, int row1, int K,
+                                               const float2* v, int w, int rpw, int lane,
+                                               float2 res[kGemvMaxRows]) {
   const float4* M4 = reinterpret_cast<const float4*>(M);
   const float4* v4 = reinterpret_cast<const float4*>(v);
   const int K4 = K >> 1;
@@ -39,8 +40,8 @@ __device__ __forceinline__ void warp_gemv(const float2* __restrict__ M, int nrow
     for (int u = 0; u < kSteps; u++)
 #pragma unroll
       for (int r = 0; r < kGemvMaxRows; r++) {
-        const int i = w * rpw + r, q = q0 + 32 * u;
-        m[u][r] = (r < rpw && i < nrows && q < K4) ? M4[(size_t)i * K4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int i = row0 + w * rpw + r, q = q0 + 32 * u;
+        m[u][r] = (r < rpw && i < row1 && q < K4) ? M4[(size_t)i * K4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
     for (int u = 0; u < kSteps; u++) {
@@ -65,6 +66,11 @@ __device__ __forceinline__ void warp_gemv(const float2* __restrict__ M, int nrow
   for (int r = 0; r < kGemvMaxRows; r++) {
     if (r < rpw) res[r] = make_float2(gemv_wsum(re[r]), gemv_wsum(im[r]));
   }
+}
+
+__device__ __forceinline__ void warp_gemv(const float2* __restrict__ M, int nrows, int K, const float2* v, int w,
+                                          int rpw, int lane, float2 res[kGemvMaxRows]) {
+  warp_gemv_rows(M, 0, nrows, K, v, w, rpw, lane, res);
 }
 
 }  // namespace mg

@@ -42,13 +42,14 @@ constexpr int RC = RB + 3;                 // ||r||^2 (recurrence)
 constexpr int RD = RC + 1;                 // ||b||^2, true residual
 
 struct CGArgs {
-  int nc, half, nsites, m, maxit, eo;
+  int nc, half, nsites, m, maxit, eo, nsplit;
   double tol_rel;
   const int* nbr;
   const float2* Y;
   const float* Ys;
   const float2* X;
   const float2* Xinv;
+  const float2* A;   // folded links (CoarseOp::A)
   const float2* b;   // full right-hand side
   float2* x;         // full solution
   float2* r;         // residual (half when eo, else full)
@@ -200,16 +201,59 @@ __device__ void hop_phase(const CGArgs& a, int mode, int s0, int s1, float2* out
   }
 }
 
-// w = A v (A = D_r on even sites, or the full D_hat); three barriers (eo) or none
+// One GEMV per site with the site's rows split over a.nsplit work items, so
+// the blocks stay balanced when there are fewer sites than 2x blocks.
+// Links L: site s uses L + (s - lbase) * nc * nb * nc (row-major, nb blocks of
+// nc columns); its vector gathers the 8 neighbours (and, for nb == 9, the
+// site itself).  subtract: out = xs - L v, else out = L v.
+__device__ void hop_rows(const CGArgs& a, const float2* L, const float* scale, int lbase, int nb, bool subtract,
+                         int s0, int s1, float2* out, const float2* in, const float2* xs, float2* sm) {
+  const int nc = a.nc;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int per = (nc + a.nsplit - 1) / a.nsplit;
+  const int rpw = (per + nw - 1) / nw;
+  const int nitems = (s1 - s0) * a.nsplit;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int s = s0 + it / a.nsplit, part = it % a.nsplit;
+    const int row0 = part * per, row1 = row0 + per < nc ? row0 + per : nc;
+    for (int t = threadIdx.x; t < nb * nc; t += blockDim.x) {
+      const int d = t / nc, j = t % nc;
+      float2 x = d < 8 ? in[(size_t)a.nbr[(size_t)s * 8 + d] * nc + j] : in[(size_t)s * nc + j];
+      if (scale && d < 8) {
+        const float sc = scale[(size_t)s * 8 + d];
+        x = make_float2(sc * x.x, sc * x.y);
+      }
+      sm[t] = x;
+    }
+    __syncthreads();
+    float2 res[kGemvMaxRows];
+    warp_gemv_rows(L + (size_t)(s - lbase) * nc * nb * nc, row0, row1, nb * nc, sm, w, rpw, lane, res);
+    if (lane == 0)
+#pragma unroll
+      for (int r = 0; r < kGemvMaxRows; r++) {
+        const int i = row0 + w * rpw + r;
+        if (r < rpw && i < row1) {
+          if (subtract) {
+            const float2 x = xs[(size_t)s * nc + i];
+            out[(size_t)s * nc + i] = make_float2(x.x - res[r].x, x.y - res[r].y);
+          } else {
+            out[(size_t)s * nc + i] = res[r];
+          }
+        }
+      }
+    __syncthreads();
+  }
+}
+
+// w = A v with A = D_r on the even sites (folded links: two GEMV phases, one
+// barrier) or the full D_hat (one GEMV phase over [Y | X])
 __device__ void apply_A(const CGArgs& a, cg::grid_group& grid, float2* w, const float2* v, float2* sm) {
   if (a.eo) {
-    site_mul(a, a.Xinv, 0, a.half, a.tA, v, sm);                 // s_e = X_e^{-1} v_e
+    hop_rows(a, a.A, nullptr, a.half, 8, false, a.half, a.nsites, a.tB, v, nullptr, sm);  // X_o^-1 Y_oe X_e^-1 v_e
     grid.sync();
-    hop_phase(a, 1, a.half, a.nsites, a.tB, a.tA, a.tA, sm);      // t_o = X_o^{-1} Y_oe s_e
-    grid.sync();
-    hop_phase(a, 0, 0, a.half, w, a.tB, v, sm);                   // w_e = v_e - Y_eo t_o
+    hop_rows(a, a.Y, a.Ys, 0, 8, true, 0, a.half, w, a.tB, v, sm);                       // w_e = v_e - Y_eo t_o
   } else {
-    hop_phase(a, 3, 0, a.nsites, w, v, v, sm);                    // w = X v + Y v
+    hop_rows(a, a.A, nullptr, 0, 9, false, 0, a.nsites, w, v, nullptr, sm);              // w = [Y | X] v
   }
 }
 
@@ -250,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_gcr(CGArgs a) {
   if (a.eo) {
     site_mul(a, a.Xinv, a.half, a.nsites, a.tB, a.b, sm);        // t_o = X_o^{-1} b_o
     grid.sync();
-    hop_phase(a, 0, 0, a.half, a.br, a.tB, a.b, sm);             // b_r = b_e - Y_eo t_o
+    hop_rows(a, a.Y, a.Ys, 0, 8, true, 0, a.half, a.br, a.tB, a.b, sm);  // b_r = b_e - Y_eo t_o
     rhs = a.br;
   }
   grid.sync();
@@ -446,6 +490,9 @@ void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuff
   a.Ys = C.Yscale.as<float>();
   a.X = C.X.as<float2>();
   a.Xinv = C.Xinv.as<float2>();
+  a.A = C.A.as<float2>();
+  if (!a.A) raise(MG_ERR_STATE, "folded coarse links missing");
+  a.nsplit = B.nsplit;
   a.b = reinterpret_cast<const float2*>(b);
   a.x = reinterpret_cast<float2*>(x);
   a.r = B.r.as<float2>();
@@ -477,6 +524,10 @@ void CoarseGCRBuffers::init(const LevelGeom& G, int nc, int m) {
   const int target = G.eo ? G.half : G.nsites;
   grid = target < most ? target : most;
   if (grid < sms) grid = sms < most ? sms : most;
+  // One work item per site.  Splitting a site's rows over several items was
+  // measured slower on GB300: a block then walks its items one after another,
+  // each with its own gather and load latency.
+  nsplit = 1;
   r.alloc(sizeof(float2) * n);
   y.alloc(sizeof(float2) * n);
   br.alloc(sizeof(float2) * (G.eo ? n : 1));

@@ -370,6 +370,7 @@ void build_coarse_links(Ctx* c, Hierarchy& H, int l) {
     }
   coarse_invert(Gc, C, c->ws.flags.as<int>(), s);
   if (c->read_flag(FLAG_SINGULAR, true)) raise(MG_ERR_SINGULAR_CLOVER, "singular coarse diagonal block");
+  if (l + 2 == H.L) coarse_fold_links(Gc, C, s);  // the coarsest level runs the persistent solver
 }
 
 void alloc_work(Ctx* c, Hierarchy& H) {
