@@ -102,7 +102,7 @@ enum mg_coarse_op { MG_COARSE_DP = 0, MG_COARSE_D = 1 };
 typedef struct {
   int levels;                     /* total levels including the fine one (1..MG_MAX_LEVELS)      */
   int block[MG_MAX_LEVELS][4];    /* aggregation block {bx,by,bz,bt} of P_l                      */
-  int nv[MG_MAX_LEVELS];          /* null vectors of P_l (coarse dof per site = 2*nv[l])         */
+  int nv[MG_MAX_LEVELS];          /* null vectors of P_l, 1..32 (coarse dof per site = 2*nv[l])  */
   int setup_iters;                /* inverse-iteration passes per null vector (cap)              */
   int setup_inner;                /* GCR iterations on D_p per pass                              */
   double setup_rq_tol;            /* stop a vector when |dRQ| < setup_rq_tol * RQ                */

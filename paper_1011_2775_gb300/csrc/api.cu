@@ -240,7 +240,8 @@ int mg_set_params(void* ctx, const mg_params* p) {
         nb *= b;
       }
       const int nv = p->nv[l];
-      if (nv < 1 || nv > 40) mg::raise(MG_ERR_NV, "nv must be in [1, 40]");
+      // the coarse kernels hold at most 64 complex components per coarse site
+      if (nv < 1 || nv > 32) mg::raise(MG_ERR_NV, "nv must be in [1, 32]");
       if (nv > nb * ndof / 2) mg::raise(MG_ERR_NV, "nv exceeds the dimension of a block's chiral subspace");
       for (int m = 0; m < 4; m++) d[m] /= p->block[l][m];
       ndof = 2 * nv;

@@ -82,6 +82,13 @@ template <typename T>
 struct VecPtrs {
   const cx<T>* p[8];
 };
+
+// Per-thread accumulation type: a thread sums only its few grid-stride
+// elements, in the vectors' own precision (FP64 for FP64 vectors); the
+// cross-thread tree is always FP64.  On GB300 this keeps the FP32 reductions
+// off the (slow) FP64 pipe.
+template <typename T>
+using acc_t = typename std::conditional<sizeof(T) == 4, float, double>::type;
 }  // namespace
 
 // --------------------------------------------------------------------------- elementwise
@@ -123,12 +130,13 @@ void blas_axpby(double a, const T* x, double b, T* y, size_t n, cudaStream_t s) 
 // --------------------------------------------------------------------------- reductions
 template <typename T>
 __global__ void k_norm2(const cx<T>* __restrict__ x, size_t n, double* partials, unsigned* counter, double* out) {
-  double v[1] = {0.0};
+  acc_t<T> s = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     cx<T> a = x[i];
-    v[0] = fma((double)a.re, (double)a.re, v[0]);
-    v[0] = fma((double)a.im, (double)a.im, v[0]);
+    s = fma((acc_t<T>)a.re, (acc_t<T>)a.re, s);
+    s = fma((acc_t<T>)a.im, (acc_t<T>)a.im, s);
   }
+  double v[1] = {(double)s};
   grid_reduce<1>(v, partials, counter, out);
 }
 template <typename T>
@@ -140,14 +148,15 @@ void blas_norm2(const T* x, size_t n, double* d_out, Workspace& ws, cudaStream_t
 template <typename T>
 __global__ void k_cdot(const cx<T>* __restrict__ x, const cx<T>* __restrict__ y, size_t n, double* partials,
                        unsigned* counter, double* out) {
-  double v[2] = {0.0, 0.0};
+  acc_t<T> s0 = 0, s1 = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     cx<T> a = x[i], b = y[i];
-    v[0] = fma((double)a.re, (double)b.re, v[0]);
-    v[0] = fma((double)a.im, (double)b.im, v[0]);
-    v[1] = fma((double)a.re, (double)b.im, v[1]);
-    v[1] = fma(-(double)a.im, (double)b.re, v[1]);
+    s0 = fma((acc_t<T>)a.re, (acc_t<T>)b.re, s0);
+    s0 = fma((acc_t<T>)a.im, (acc_t<T>)b.im, s0);
+    s1 = fma((acc_t<T>)a.re, (acc_t<T>)b.im, s1);
+    s1 = fma(-(acc_t<T>)a.im, (acc_t<T>)b.re, s1);
   }
+  double v[2] = {(double)s0, (double)s1};
   grid_reduce<2>(v, partials, counter, out);
 }
 template <typename T>
@@ -160,16 +169,17 @@ void blas_cdot(const T* x, const T* y, size_t n, double* d_out, Workspace& ws, c
 template <typename T>
 __global__ void k_dot2(const cx<T>* __restrict__ w, const cx<T>* __restrict__ r, size_t n, double* partials,
                        unsigned* counter, double* out) {
-  double v[3] = {0.0, 0.0, 0.0};
+  acc_t<T> s0 = 0, s1 = 0, s2 = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     cx<T> a = w[i], b = r[i];
-    v[0] = fma((double)a.re, (double)a.re, v[0]);
-    v[0] = fma((double)a.im, (double)a.im, v[0]);
-    v[1] = fma((double)a.re, (double)b.re, v[1]);
-    v[1] = fma((double)a.im, (double)b.im, v[1]);
-    v[2] = fma((double)a.re, (double)b.im, v[2]);
-    v[2] = fma(-(double)a.im, (double)b.re, v[2]);
+    s0 = fma((acc_t<T>)a.re, (acc_t<T>)a.re, s0);
+    s0 = fma((acc_t<T>)a.im, (acc_t<T>)a.im, s0);
+    s1 = fma((acc_t<T>)a.re, (acc_t<T>)b.re, s1);
+    s1 = fma((acc_t<T>)a.im, (acc_t<T>)b.im, s1);
+    s2 = fma((acc_t<T>)a.re, (acc_t<T>)b.im, s2);
+    s2 = fma(-(acc_t<T>)a.im, (acc_t<T>)b.re, s2);
   }
+  double v[3] = {(double)s0, (double)s1, (double)s2};
   grid_reduce<3>(v, partials, counter, out);
 }
 template <typename T>
@@ -183,20 +193,23 @@ void blas_dot2(const T* w, const T* r, size_t n, double* d_out, Workspace& ws, c
 template <typename T, int K>
 __global__ void k_multidot(VecPtrs<T> V, const cx<T>* __restrict__ w, size_t n, double* partials, unsigned* counter,
                            double* out) {
-  double v[2 * K];
+  acc_t<T> s[2 * K];
 #pragma unroll
-  for (int r = 0; r < 2 * K; r++) v[r] = 0.0;
+  for (int r = 0; r < 2 * K; r++) s[r] = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     cx<T> b = w[i];
 #pragma unroll
     for (int j = 0; j < K; j++) {
       cx<T> a = V.p[j][i];
-      v[2 * j] = fma((double)a.re, (double)b.re, v[2 * j]);
-      v[2 * j] = fma((double)a.im, (double)b.im, v[2 * j]);
-      v[2 * j + 1] = fma((double)a.re, (double)b.im, v[2 * j + 1]);
-      v[2 * j + 1] = fma(-(double)a.im, (double)b.re, v[2 * j + 1]);
+      s[2 * j] = fma((acc_t<T>)a.re, (acc_t<T>)b.re, s[2 * j]);
+      s[2 * j] = fma((acc_t<T>)a.im, (acc_t<T>)b.im, s[2 * j]);
+      s[2 * j + 1] = fma((acc_t<T>)a.re, (acc_t<T>)b.im, s[2 * j + 1]);
+      s[2 * j + 1] = fma(-(acc_t<T>)a.im, (acc_t<T>)b.re, s[2 * j + 1]);
     }
   }
+  double v[2 * K];
+#pragma unroll
+  for (int r = 0; r < 2 * K; r++) v[r] = (double)s[r];
   grid_reduce<2 * K>(v, partials, counter, out);
 }
 
@@ -235,7 +248,7 @@ __global__ void k_orth_update(cx<T>* w, VecPtrs<T> V, const double* __restrict__
     br[j] = (T)beta[2 * j];
     bi[j] = (T)beta[2 * j + 1];
   }
-  double v[3] = {0.0, 0.0, 0.0};
+  acc_t<T> s0 = 0, s1 = 0, s2 = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     cx<T> a = w[i];
 #pragma unroll
@@ -247,14 +260,15 @@ __global__ void k_orth_update(cx<T>* w, VecPtrs<T> V, const double* __restrict__
     if (K > 0) w[i] = a;
     if (RED) {
       cx<T> b = r[i];
-      v[0] = fma((double)a.re, (double)a.re, v[0]);
-      v[0] = fma((double)a.im, (double)a.im, v[0]);
-      v[1] = fma((double)a.re, (double)b.re, v[1]);
-      v[1] = fma((double)a.im, (double)b.im, v[1]);
-      v[2] = fma((double)a.re, (double)b.im, v[2]);
-      v[2] = fma(-(double)a.im, (double)b.re, v[2]);
+      s0 = fma((acc_t<T>)a.re, (acc_t<T>)a.re, s0);
+      s0 = fma((acc_t<T>)a.im, (acc_t<T>)a.im, s0);
+      s1 = fma((acc_t<T>)a.re, (acc_t<T>)b.re, s1);
+      s1 = fma((acc_t<T>)a.im, (acc_t<T>)b.im, s1);
+      s2 = fma((acc_t<T>)a.re, (acc_t<T>)b.im, s2);
+      s2 = fma(-(acc_t<T>)a.im, (acc_t<T>)b.re, s2);
     }
   }
+  double v[3] = {(double)s0, (double)s1, (double)s2};
   if (RED) grid_reduce<3>(v, partials, counter, out);
 }
 
@@ -316,7 +330,7 @@ __global__ void k_r_update(cx<T>* w, cx<T>* r, size_t n, const double* __restric
     gamma_out[0] = gam;
   }
   const T ig = (T)(1.0 / gam), a_r = (T)ar, a_i = (T)ai;
-  double v[1] = {0.0};
+  acc_t<T> s = 0;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     cx<T> q = w[i];
     q.re *= ig;
@@ -326,9 +340,10 @@ __global__ void k_r_update(cx<T>* w, cx<T>* r, size_t n, const double* __restric
     b.re -= a_r * q.re - a_i * q.im;
     b.im -= a_r * q.im + a_i * q.re;
     r[i] = b;
-    v[0] = fma((double)b.re, (double)b.re, v[0]);
-    v[0] = fma((double)b.im, (double)b.im, v[0]);
+    s = fma((acc_t<T>)b.re, (acc_t<T>)b.re, s);
+    s = fma((acc_t<T>)b.im, (acc_t<T>)b.im, s);
   }
+  double v[1] = {(double)s};
   grid_reduce<1>(v, partials, counter, out);
 }
 

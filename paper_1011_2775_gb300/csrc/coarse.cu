@@ -116,53 +116,65 @@ __device__ __forceinline__ float warp_sumf(float v) {
 }  // namespace
 
 // --------------------------------------------------------------------------- restriction
+// One CTA per coarse site.  Warp w takes the block's fine sites w, w+8, ...;
+// lane k (and k+32 when Nv > 32) accumulates conj(P[i][c][k]) v[i][c] for the
+// two chiralities.  The site's components are read once by lanes 0..ndof-1
+// and broadcast with shuffles; P rows are read coalesced, several components
+// in flight at a time.  Per-warp sums are combined in FP64 at the end.
 template <int ST>
-__global__ void k_restrict(TArgs a, float* __restrict__ out, const float* __restrict__ v, int even_only) {
-  extern __shared__ double sred[];  // [G][nv][2][2]
+__global__ void __launch_bounds__(256) k_restrict(TArgs a, float* __restrict__ out, const float* __restrict__ v,
+                                                  int even_only) {
+  extern __shared__ float2 sacc[];  // [nwarps][2 nv]
   const int cc = blockIdx.x;
-  const int nv = a.nv, G = blockDim.x / nv;
-  const int k = threadIdx.x % nv, g = threadIdx.x / nv;
-  const int hd = a.ndof / 2;
-  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-  if (g < G) {
-    const float s0 = a.Ps[cc * 2], s1 = a.Ps[cc * 2 + 1];
-    for (int i = g; i < a.nb; i += G) {
-      const int idx = a.blockmap[cc * a.nb + i];
-      if (even_only && idx >= a.fine_half) continue;
-      const size_t base = (size_t)(cc * a.nb + i) * a.ndof;
+  const int nv = a.nv, hd = a.ndof / 2;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float acc[2][2][2] = {};  // [k-half][chirality][re, im]
+  for (int i = w; i < a.nb; i += nw) {
+    const int idx = a.blockmap[cc * a.nb + i];
+    if (even_only && idx >= a.fine_half) continue;
+    const cx<float> x0 = lane < a.ndof ? fget(a.fa, v, idx, lane) : mkc(0.f, 0.f);
+    const cx<float> x1 = lane + 32 < a.ndof ? fget(a.fa, v, idx, lane + 32) : mkc(0.f, 0.f);
+    const size_t base = (size_t)(cc * a.nb + i) * a.ndof;
+#pragma unroll 4
+    for (int c = 0; c < a.ndof; c++) {
+      const float xr = __shfl_sync(0xffffffffu, c < 32 ? x0.re : x1.re, c & 31);
+      const float xi = __shfl_sync(0xffffffffu, c < 32 ? x0.im : x1.im, c & 31);
+      const int ch = c >= hd;
 #pragma unroll
-      for (int ch = 0; ch < 2; ch++) {
-        const float sc = ch ? s1 : s0;
-        for (int c = ch * hd; c < (ch + 1) * hd; c++) {
-          const cx<float> x = fget(a.fa, v, idx, c);
+      for (int h = 0; h < 2; h++) {
+        const int k = lane + 32 * h;
+        if (k < nv) {
           const cx<float> p = sget<ST>(a.P, (base + c) * nv + k);
-          acc[ch][0] += (double)(sc * (p.re * x.re + p.im * x.im));
-          acc[ch][1] += (double)(sc * (p.re * x.im - p.im * x.re));
+          acc[h][ch][0] += p.re * xr + p.im * xi;
+          acc[h][ch][1] += p.re * xi - p.im * xr;
         }
       }
     }
-    double* me = sred + ((size_t)g * nv + k) * 4;
-    me[0] = acc[0][0];
-    me[1] = acc[0][1];
-    me[2] = acc[1][0];
-    me[3] = acc[1][1];
+  }
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const int k = lane + 32 * h;
+    if (k < nv) {
+      sacc[(size_t)w * 2 * nv + k] = make_float2(acc[h][0][0], acc[h][0][1]);
+      sacc[(size_t)w * 2 * nv + nv + k] = make_float2(acc[h][1][0], acc[h][1][1]);
+    }
   }
   __syncthreads();
+  const float s0 = a.Ps[cc * 2], s1 = a.Ps[cc * 2 + 1];
   for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x) {
-    const int ch = t / nv, kk = t % nv;
     double re = 0, im = 0;
-    for (int q = 0; q < G; q++) {
-      re += sred[((size_t)q * nv + kk) * 4 + 2 * ch];
-      im += sred[((size_t)q * nv + kk) * 4 + 2 * ch + 1];
+    for (int q = 0; q < nw; q++) {
+      re += sacc[(size_t)q * 2 * nv + t].x;
+      im += sacc[(size_t)q * 2 * nv + t].y;
     }
-    reinterpret_cast<float2*>(out)[(size_t)cc * 2 * nv + t] = make_float2((float)re, (float)im);
+    const float sc = t < nv ? s0 : s1;
+    reinterpret_cast<float2*>(out)[(size_t)cc * 2 * nv + t] = make_float2((float)(sc * re), (float)(sc * im));
   }
 }
 
 void restrict_vec(const TransferOp& T, float* out_c, const float* v, bool even_only, cudaStream_t s) {
   TArgs a = targs(T);
-  const int G = kBS / T.nv;
-  const size_t sm = sizeof(double) * 4 * (size_t)G * T.nv;
+  const size_t sm = sizeof(float2) * (kBS / 32) * 2 * (size_t)T.nv;
   switch (T.store) {
     case STORE_F32: k_restrict<STORE_F32><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
     case STORE_F16: k_restrict<STORE_F16><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
