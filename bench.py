@@ -38,6 +38,10 @@ TOL = 1e-10
 HBM_DIMS = (32, 32, 32, 64)          # 1.1 GB per FP32 fused-dslash launch: far beyond the 129 MB L2
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_DR = 5                    # oracle D_r applications in one CPU sample
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fused
+# dslash on 32^3x64, from the ncu capture in profiles/dslash_fp32_32x32x32x64.md
+# (set to None whenever that kernel changes)
+DSLASH_TRAFFIC_BYTES = 1.125e9
 
 
 def workload_name(m0):
@@ -358,7 +362,8 @@ def main():
     k = r["kern"]["dslash_clover_fp32"]
     roof = {"kernel": "fused hop + clover-inverse dslash, FP32, 32^3x64 (HBM-resident)", "bound": "hbm",
             "achieved": k["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": k["gbs"] / hbm_peak,
-            "traffic": None, "peak_kind": peak_kind, "bytes_per_launch": k["bytes"], "ms_per_launch": k["ms"]}
+            "traffic": DSLASH_TRAFFIC_BYTES, "peak_kind": peak_kind, "bytes_per_launch": k["bytes"],
+            "ms_per_launch": k["ms"]}
     line = {"metric": METRIC, "value": r["ms"], "unit": "ms", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
