@@ -38,6 +38,10 @@ TOL = 1e-10
 HBM_DIMS = (32, 32, 32, 64)          # 1.1 GB per FP32 fused-dslash launch: far beyond the 129 MB L2
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_DR = 5                    # oracle D_r applications in one CPU sample
+# fine D_r applications of one MG-GCR solve of the 16^3x32 workload at m0=-0.35
+# (the GPU arm's solve.fine_dr_applications on GB300: 42 outer iterations);
+# projects the reference arm's sample to one solve
+REFERENCE_DR_PER_SOLVE = 257
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fused
 # dslash on 32^3x64, from the ncu capture in profiles/dslash_fp32_32x32x32x64.md
 # (set to None whenever that kernel changes)
@@ -390,10 +394,6 @@ def main():
         print(json.dumps(line))
     dist.close()
 
-
-# fine D_r applications of one MG-GCR solve of this workload (measured by the
-# GPU arm, solve.fine_dr_applications); used to project the reference arm's sample
-REFERENCE_DR_PER_SOLVE = 300
 
 if __name__ == "__main__":
     main()
