@@ -95,6 +95,11 @@ enum mg_prec { MG_FP64 = 0, MG_FP32 = 1 };
 enum mg_storage { MG_STORE_FP32 = 0, MG_STORE_FP16 = 1, MG_STORE_BF16 = 2 };
 enum mg_mode { MG_MODE_MG = 0, MG_MODE_EO_GCR = 1 };
 enum mg_coarse_op { MG_COARSE_DP = 0, MG_COARSE_D = 1 };
+/* Output of mg_force. */
+enum mg_force_kind {
+  MG_FORCE_SU3 = 0,        /* su(3) force sum_a F^a T_a (traceless Hermitian), T_a = lambda_a / 2     */
+  MG_FORCE_WIRTINGER = 1   /* unconstrained gradient dL/dRe U + i dL/dIm U of every complex link entry */
+};
 
 /* Multigrid parameters (section "Implementation"; section "Setup procedure").
  * Arrays are indexed by the level they map FROM: block[l], nv[l] build P_l
@@ -202,6 +207,34 @@ MG_API int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where)
  * MG_ERR_NOT_CONVERGED (psi holds the best iterate), MG_ERR_CUDA. */
 MG_API int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
              mg_solve_info* info);
+
+/* Solve the adjoint system D^dag psi = eta with the same solver and
+ * multigrid, through gamma_5-hermiticity D^dag = gamma_5 D gamma_5:
+ * psi = gamma_5 D^{-1} (gamma_5 eta).  This is the backward solve of a
+ * differentiated solve (the paper has no gradient; it solves D only).
+ * Arguments, layouts, tolerance (on ||eta - D^dag psi|| / ||eta||, equal to
+ * the residual of the gamma_5-rotated system) and errors as mg_solve; eta is
+ * not modified. */
+MG_API int mg_solve_dagger(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
+                           mg_solve_info* info);
+
+/* Gauge-link derivative of f(U) = -Re <lambda, D(U) psi> for fixed fine
+ * vectors lambda and psi (complex128, fine-vector layout, one right-hand
+ * side each; `where` says host or device for all three buffers).  With
+ * psi = D^{-1} eta and lambda = D^{-dag} chi (mg_solve_dagger) it is the
+ * derivative of L = Re <chi, D^{-1} eta> with respect to the gauge field --
+ * an extension: the paper does not differentiate the solve.  Both the hopping
+ * term and the clover term (through its plaquette leaves, with the csw of the
+ * last mg_set_clover) are differentiated, in FP64.
+ *   MG_FORCE_SU3:       F_mu(x) = sum_a F^a T_a with F^a = df/d omega^a for
+ *                       U_mu(x) -> exp(i omega^a T_a) U_mu(x), T_a = lambda_a/2;
+ *   MG_FORCE_WIRTINGER: g_mu(x) with df = Re sum tr(g^dag dU) for any complex
+ *                       dU (the gradient convention of torch for complex
+ *                       tensors).
+ * `F` has the gauge-field layout [t][z][y][x][mu][3][3] complex128 and is
+ * owned by the caller.  Errors: MG_ERR_ARG, MG_ERR_STATE (no clover),
+ * MG_ERR_CUDA. */
+MG_API int mg_force(void* ctx, void* F, const void* lambda, const void* psi, int kind, int where);
 
 /* Apply operator `op` (enum mg_op) of level `level` to nrhs vectors of that
  * level (for MG_OP_R the output is a level+1 vector, for MG_OP_P the input

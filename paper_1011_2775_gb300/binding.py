@@ -32,12 +32,14 @@ MG_FP64, MG_FP32 = 0, 1
 MG_STORE_FP32, MG_STORE_FP16, MG_STORE_BF16 = 0, 1, 2
 MG_MODE_MG, MG_MODE_EO_GCR = 0, 1
 MG_COARSE_DP, MG_COARSE_D = 0, 1
+MG_FORCE_SU3, MG_FORCE_WIRTINGER = 0, 1
 
 MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_DR = range(4)
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_solve", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_level_info"]
+            "mg_solve", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel",
+            "mg_level_info"]
 
 
 class mg_params(ctypes.Structure):
@@ -110,6 +112,8 @@ def lib() -> ctypes.CDLL:
             "mg_set_null_vectors": [vp, ip, vp, ip, ip],
             "mg_get_null_vectors": [vp, ip, vp, ip, ip],
             "mg_solve": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
+            "mg_solve_dagger": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
+            "mg_force": [vp, vp, vp, vp, ip, ip],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
             "mg_benchmark_kernel": [vp, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_apply_noalloc": [vp, ip, vp, vp, ip],
@@ -213,6 +217,27 @@ def mg_solve(ctx, psi, eta, nrhs: int, tol: float, mode: int = MG_MODE_MG, allow
     st = lib().mg_solve(ctx, pp, pe, int(nrhs), float(tol), int(mode), wp, ctypes.byref(info))
     _check(st, "mg_solve", allow=(MG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return st, info
+
+
+def mg_solve_dagger(ctx, psi, eta, nrhs: int, tol: float, mode: int = MG_MODE_MG, allow_not_converged=False):
+    """Solves ``D^dag psi = eta``; returns ``(status, mg_solve_info)``."""
+    pp, wp = _buf(psi, writable=True)
+    pe, we = _buf(eta)
+    if wp != we:
+        raise TypeError("psi and eta must both be host or both be device buffers")
+    info = mg_solve_info()
+    st = lib().mg_solve_dagger(ctx, pp, pe, int(nrhs), float(tol), int(mode), wp, ctypes.byref(info))
+    _check(st, "mg_solve_dagger", allow=(MG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return st, info
+
+
+def mg_force(ctx, F, lam, psi, kind: int = MG_FORCE_SU3) -> None:
+    pf, wf = _buf(F, writable=True)
+    pl, wl = _buf(lam)
+    pp, wp = _buf(psi)
+    if not (wf == wl == wp):
+        raise TypeError("F, lambda and psi must all be host or all be device buffers")
+    _check(lib().mg_force(ctx, pf, pl, pp, int(kind), wf), "mg_force")
 
 
 def mg_apply(ctx, op: int, level: int, out, x, nrhs: int = 1, prec: int = MG_FP64) -> None:

@@ -84,6 +84,50 @@ void stage_out_finish(mg::Ctx* c, Staged& st, void* user, size_t bytes, int wher
 void check_where(int where) {
   if (where != MG_HOST && where != MG_DEVICE) mg::raise(MG_ERR_ARG, "where must be MG_HOST or MG_DEVICE");
 }
+
+// mg_solve / mg_solve_dagger.  The dagger form solves D^dag psi = eta as
+// psi = gamma_5 D^{-1} gamma_5 eta (D^dag = gamma_5 D gamma_5).
+int solve_impl(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
+               mg_solve_info* info, bool dagger) {
+  const auto t0 = std::chrono::steady_clock::now();
+  mg::Ctx* c = as_ctx(ctx);
+  check_where(where);
+  if (!psi || !eta || nrhs < 1 || !(tol > 0)) mg::raise(MG_ERR_ARG, "bad solve arguments");
+  if (mode != MG_MODE_MG && mode != MG_MODE_EO_GCR) mg::raise(MG_ERR_ARG, "bad mode");
+  if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
+  if (mode == MG_MODE_MG && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+  mg_solve_info local;
+  std::memset(&local, 0, sizeof(local));
+  local.true_residual = 0.0;
+  mg::mg_reset_counters(c);
+  const long long launches0 = c->dslash_launches;
+  const long long kernels0 = mg::launches_so_far();
+  const size_t per = sizeof(double) * 24 * c->V;
+  Staged si, so;
+  if (dagger && where == MG_DEVICE) {
+    // gamma_5 must not touch the caller's source: work on a copy
+    si.own.alloc(per * nrhs);
+    si.ptr = si.own.as<double>();
+    MG_CUDA(cudaMemcpyAsync(si.ptr, eta, per * nrhs, cudaMemcpyDeviceToDevice, c->stream));
+  } else {
+    stage_in(c, si, eta, per * nrhs, where);
+  }
+  stage_out_alloc(so, psi, per * nrhs, where);
+  if (dagger) mg::gamma5_abi(si.ptr, c->V * nrhs, c->stream);
+  int status = MG_OK;
+  for (int r = 0; r < nrhs; r++) {
+    const int st = mg::solve_fine(c, so.ptr + (size_t)r * 24 * c->V, si.ptr + (size_t)r * 24 * c->V, tol, mode, &local);
+    if (st != MG_OK) status = st;
+  }
+  if (dagger) mg::gamma5_abi(so.ptr, c->V * nrhs, c->stream);
+  stage_out_finish(c, so, psi, per * nrhs, where);
+  mg::mg_read_counters(c, local.coarse_iterations);
+  local.dslash_launches = c->dslash_launches - launches0;
+  local.kernel_launches = mg::launches_so_far() - kernels0;
+  local.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = local;
+  return status;
+}
 }  // namespace
 
 namespace mg {
@@ -306,36 +350,29 @@ int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where) {
 }
 
 int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where, mg_solve_info* info) {
+  return guarded([&]() { return solve_impl(ctx, psi, eta, nrhs, tol, mode, where, info, false); });
+}
+
+int mg_solve_dagger(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
+                    mg_solve_info* info) {
+  return guarded([&]() { return solve_impl(ctx, psi, eta, nrhs, tol, mode, where, info, true); });
+}
+
+int mg_force(void* ctx, void* F, const void* lambda, const void* psi, int kind, int where) {
   return guarded([&]() {
-    const auto t0 = std::chrono::steady_clock::now();
     mg::Ctx* c = as_ctx(ctx);
     check_where(where);
-    if (!psi || !eta || nrhs < 1 || !(tol > 0)) mg::raise(MG_ERR_ARG, "bad solve arguments");
-    if (mode != MG_MODE_MG && mode != MG_MODE_EO_GCR) mg::raise(MG_ERR_ARG, "bad mode");
+    if (!F || !lambda || !psi) mg::raise(MG_ERR_ARG, "null buffer");
+    if (kind != MG_FORCE_SU3 && kind != MG_FORCE_WIRTINGER) mg::raise(MG_ERR_ARG, "bad force kind");
     if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
-    if (mode == MG_MODE_MG && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
-    mg_solve_info local;
-    std::memset(&local, 0, sizeof(local));
-    local.true_residual = 0.0;
-    mg::mg_reset_counters(c);
-    const long long launches0 = c->dslash_launches;
-    const long long kernels0 = mg::launches_so_far();
-    const size_t per = sizeof(double) * 24 * c->V;
-    Staged si, so;
-    stage_in(c, si, eta, per * nrhs, where);
-    stage_out_alloc(so, psi, per * nrhs, where);
-    int status = MG_OK;
-    for (int r = 0; r < nrhs; r++) {
-      const int st = mg::solve_fine(c, so.ptr + (size_t)r * 24 * c->V, si.ptr + (size_t)r * 24 * c->V, tol, mode, &local);
-      if (st != MG_OK) status = st;
-    }
-    stage_out_finish(c, so, psi, per * nrhs, where);
-    mg::mg_read_counters(c, local.coarse_iterations);
-    local.dslash_launches = c->dslash_launches - launches0;
-    local.kernel_launches = mg::launches_so_far() - kernels0;
-    local.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (info) *info = local;
-    return status;
+    const size_t vbytes = sizeof(double) * 24 * c->V, fbytes = sizeof(double) * 72 * c->V;
+    Staged sl, sp, so;
+    stage_in(c, sl, lambda, vbytes, where);
+    stage_in(c, sp, psi, vbytes, where);
+    stage_out_alloc(so, F, fbytes, where);
+    mg::gauge_force(c, so.ptr, sl.ptr, sp.ptr, kind);
+    stage_out_finish(c, so, F, fbytes, where);
+    return MG_OK;
   });
 }
 

@@ -1,0 +1,333 @@
+// Gauge-link derivative of the Wilson-clover operator, for the gradient of a
+// solve (the paper has no gradient; this is the adjoint-method extension).
+//
+// For fixed fine vectors lam and psi, f(U) = -Re <lam, D(U) psi> changes under
+// a complex variation dU of the links by  df = Re sum_{x,mu} tr(dU_mu(x) K_mu(x)).
+// With psi = D^{-1} eta and lam = D^{-dag} chi this is the derivative of
+// L = Re <chi, D^{-1} eta>.  The kernels return K^dag (the unconstrained
+// gradient in the convention dL/dRe U + i dL/dIm U) or the su(3) force
+// sum_a F^a T_a, F^a = df/d omega^a for U -> exp(i omega^a T_a) U, which is
+// (H - tr(H)/3)/2 with G = i U K and H = (G + G^dag)/2.
+//
+// K has a hopping part (one outer product per end of the link) and a clover
+// part.  The clover part: lam^dag (sigma_{mu nu} x dF_{mu nu}) psi = tr(dF S),
+// S = sum_s (sigma psi)_s lam_s^dag; with C = -(i csw/4) S, C0 = C - tr(C)/3
+// and F = (Q - Q^dag)/8 - trace, the clover variation is
+// Re sum_{mu<nu} tr(dQ_{mu nu} W_{mu nu}) with W = (C0 - C0^dag)/4 (both
+// orders mu,nu and nu,mu give the same term).  Every plaquette of a plane is
+// a leaf of Q at each of its four corners, so the link's own position in the
+// plaquette collects the cyclic product of the other three links with W of
+// every corner inserted where that corner's leaf begins.
+//
+// Two kernels: k_force_insertion writes W_{mu nu}(x) for the six planes of
+// every site (FP64, [parity][plane][9][Vh]); k_force_links computes K (or the
+// force) of every link and writes it in the ABI gauge layout.
+#include <cstring>
+
+#include "internal.h"
+#include "wilson_dev.cuh"
+
+namespace mg {
+void set_last_error(const std::string& what);
+
+namespace {
+typedef cx<double> cd;
+
+__device__ __forceinline__ void m_mul(const cd a[9], const cd b[9], cd c[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      cd s = a[i * 3] * b[j];
+      s = cfma(a[i * 3 + 1], b[3 + j], s);
+      s = cfma(a[i * 3 + 2], b[6 + j], s);
+      c[i * 3 + j] = s;
+    }
+}
+__device__ __forceinline__ void m_mul_acc(const cd a[9], const cd b[9], cd c[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+      cd s = c[i * 3 + j];
+      s = cfma(a[i * 3], b[j], s);
+      s = cfma(a[i * 3 + 1], b[3 + j], s);
+      s = cfma(a[i * 3 + 2], b[6 + j], s);
+      c[i * 3 + j] = s;
+    }
+}
+__device__ __forceinline__ void m_dag_inplace(cd a[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; i++) {
+    a[i * 3 + i] = conj(a[i * 3 + i]);
+#pragma unroll
+    for (int j = i + 1; j < 3; j++) {
+      const cd t = a[i * 3 + j];
+      a[i * 3 + j] = conj(a[j * 3 + i]);
+      a[j * 3 + i] = conj(t);
+    }
+  }
+}
+
+// gamma_mu psi in the block form [[0, a_mu], [b_mu, 0]] (see wilson_dev.cuh)
+template <int MU>
+__device__ __forceinline__ void gamma_mul(const cd in[12], cd out[12]) {
+#pragma unroll
+  for (int col = 0; col < 3; col++) {
+    mul_a<MU, double>(in[6 + col], in[9 + col], out[col], out[3 + col]);
+    mul_b<MU, double>(in[col], in[3 + col], out[6 + col], out[9 + col]);
+  }
+}
+__device__ __forceinline__ void gamma_dyn(int mu, const cd in[12], cd out[12]) {
+  switch (mu) {
+    case 0: gamma_mul<0>(in, out); break;
+    case 1: gamma_mul<1>(in, out); break;
+    case 2: gamma_mul<2>(in, out); break;
+    default: gamma_mul<3>(in, out); break;
+  }
+}
+
+__device__ __forceinline__ int plane_of(int a, int b) { return a == 0 ? b - 1 : (a == 1 ? b + 1 : 5); }
+
+__device__ __forceinline__ void step(const Geom& g, int c[4], int mu, int d) {
+  c[mu] += d;
+  if (c[mu] < 0) c[mu] += g.L[mu];
+  if (c[mu] >= g.L[mu]) c[mu] -= g.L[mu];
+}
+
+__device__ __forceinline__ void link_at(const Geom& g, const double* gauge, const int c[4], int mu, cd u[9]) {
+  load_link<double>(gauge, g.Vh, (c[0] + c[1] + c[2] + c[3]) & 1, mu, cb_index(g, c), u);
+}
+
+__device__ __forceinline__ void w_at(const Geom& g, const double2* W, const int c[4], int p, cd w[9]) {
+  const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
+  const double2* q = W + (size_t)(par * 6 + p) * 9 * g.Vh + cb_index(g, c);
+#pragma unroll
+  for (int e = 0; e < 9; e++) {
+    const double2 v = q[(size_t)e * g.Vh];
+    w[e] = mkc(v.x, v.y);
+  }
+}
+
+// W_{mu nu}(x) for the six planes mu < nu of every site.
+__global__ void __launch_bounds__(128) k_force_insertion(Geom g, const double* lam_e, const double* lam_o,
+                                                         const double* psi_e, const double* psi_o, double csw,
+                                                         double2* W) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * g.Vh) return;
+  const int par = t >= g.Vh;
+  const int i = t - par * g.Vh;
+  cd lam[12], psi[12];
+  SpinorIO<double>::load(par ? lam_o : lam_e, g.Vh, i, lam);
+  SpinorIO<double>::load(par ? psi_o : psi_e, g.Vh, i, psi);
+  const double q = -0.25 * csw;   // C = -(i csw/4) S = q * (i S)
+  for (int mu = 0; mu < 4; mu++)
+    for (int nu = mu + 1; nu < 4; nu++) {
+      cd gn[12], gmn[12];
+      gamma_dyn(nu, psi, gn);
+      gamma_dyn(mu, gn, gmn);            // sigma_{mu nu} psi = i gamma_mu gamma_nu psi
+      cd C[9];
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+          cd s = mkc(0.0, 0.0);
+#pragma unroll
+          for (int sp = 0; sp < 4; sp++) s = cfma_conj(lam[3 * sp + b], gmn[3 * sp + a], s);
+          // S_ab = sum_s (sigma psi)_{s a} conj(lam_{s b}) = i * s;  C = q * i * S = -q * s
+          C[a * 3 + b] = mkc(-q * s.re, -q * s.im);
+        }
+      const cd tr3 = mkc((C[0].re + C[4].re + C[8].re) / 3.0, (C[0].im + C[4].im + C[8].im) / 3.0);
+      C[0] = C[0] - tr3;
+      C[4] = C[4] - tr3;
+      C[8] = C[8] - tr3;
+      const int p = plane_of(mu, nu);
+      double2* out = W + (size_t)(par * 6 + p) * 9 * g.Vh + i;
+#pragma unroll
+      for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+          const cd w = C[a * 3 + b] - conj(C[b * 3 + a]);
+          out[(size_t)(a * 3 + b) * g.Vh] = make_double2(0.25 * w.re, 0.25 * w.im);
+        }
+    }
+}
+
+// K_mu(x) (or the force) of every link; thread = (site, mu = blockIdx.y).
+__global__ void __launch_bounds__(128) k_force_links(Geom g, const double* lam_e, const double* lam_o,
+                                                     const double* psi_e, const double* psi_o, const double* gauge,
+                                                     const double2* W, int kind, double2* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * g.Vh) return;
+  const int mu = blockIdx.y;
+  const int par = t >= g.Vh;
+  const int i = t - par * g.Vh;
+  int x[4];
+  cb_coords(g, i, par, x);
+  cd K[9];
+
+  // ---- hopping part: (s/2) [ sum_t psi(x+mu)_t ((1-g)lam(x))_t^dag + sum_s lam(x+mu)_s ((1+g)psi(x))_s^dag ]
+  {
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    step(g, y, mu, +1);
+    const int j = cb_index(g, y);
+    const double sgn = (mu == 3 && g.apbc && x[3] == g.L[3] - 1) ? -1.0 : 1.0;
+    cd a[12], b[12], ga[12];
+    // first outer product: psi(x+mu) against (1 - gamma) lam(x)
+    SpinorIO<double>::load(par ? lam_o : lam_e, g.Vh, i, a);
+    gamma_dyn(mu, a, ga);
+#pragma unroll
+    for (int k = 0; k < 12; k++) a[k] = a[k] - ga[k];
+    SpinorIO<double>::load(par ? psi_e : psi_o, g.Vh, j, b);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        cd s = mkc(0.0, 0.0);
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++) s = cfma_conj(a[3 * sp + c], b[3 * sp + r], s);
+        K[r * 3 + c] = s;
+      }
+    // second: lam(x+mu) against (1 + gamma) psi(x)
+    SpinorIO<double>::load(par ? psi_o : psi_e, g.Vh, i, a);
+    gamma_dyn(mu, a, ga);
+#pragma unroll
+    for (int k = 0; k < 12; k++) a[k] = a[k] + ga[k];
+    SpinorIO<double>::load(par ? lam_e : lam_o, g.Vh, j, b);
+#pragma unroll
+    for (int r = 0; r < 3; r++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        cd s = K[r * 3 + c];
+#pragma unroll
+        for (int sp = 0; sp < 4; sp++) s = cfma_conj(a[3 * sp + c], b[3 * sp + r], s);
+        K[r * 3 + c] = mkc(0.5 * sgn * s.re, 0.5 * sgn * s.im);
+      }
+  }
+
+  // ---- clover part: two plaquettes per plane containing mu
+  for (int nu = 0; nu < 4; nu++) {
+    if (nu == mu) continue;
+    const int al = mu < nu ? mu : nu, be = mu < nu ? nu : mu;
+    const int p = plane_of(al, be);
+    for (int h = 0; h < 2; h++) {
+      // base corner b and the link's position j in the plaquette
+      //   L0 = U_al(b), L1 = U_be(b+al), L2 = U_al(b+be)^dag, L3 = U_be(b)^dag
+      int jpos;
+      int b[4] = {x[0], x[1], x[2], x[3]};
+      if (mu == al) {
+        if (h == 0) { jpos = 0; } else { jpos = 2; step(g, b, be, -1); }
+      } else {
+        if (h == 0) { jpos = 1; step(g, b, al, -1); } else { jpos = 3; }
+      }
+      int cr[4][4];
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int m = 0; m < 4; m++) cr[k][m] = b[m];
+      step(g, cr[1], al, +1);
+      step(g, cr[2], al, +1);
+      step(g, cr[2], be, +1);
+      step(g, cr[3], be, +1);
+      // factor k of the plaquette
+      auto factor = [&](int k, cd u[9]) {
+        switch (k & 3) {
+          case 0: link_at(g, gauge, cr[0], al, u); break;
+          case 1: link_at(g, gauge, cr[1], be, u); break;
+          case 2: link_at(g, gauge, cr[3], al, u); m_dag_inplace(u); break;
+          default: link_at(g, gauge, cr[0], be, u); m_dag_inplace(u); break;
+        }
+      };
+      // R = ((W1 A1 + A1 W2) A2 + A1 A2 W3) A3 + A1 A2 A3 W0, A_n = L_{j+n}, W_n = W(corner j+n)
+      cd A[9], M[9], T[9], P[9], R[9];
+      factor(jpos + 1, A);
+      w_at(g, W, cr[(jpos + 1) & 3], p, M);
+      m_mul(M, A, T);
+      w_at(g, W, cr[(jpos + 2) & 3], p, M);
+      m_mul_acc(A, M, T);
+#pragma unroll
+      for (int e = 0; e < 9; e++) P[e] = A[e];
+      factor(jpos + 2, A);
+      m_mul(T, A, R);
+      m_mul(P, A, T);                        // T = A1 A2
+      w_at(g, W, cr[(jpos + 3) & 3], p, M);
+      m_mul_acc(T, M, R);                    // R = (W1 A1 + A1 W2) A2 + A1 A2 W3
+      factor(jpos + 3, A);
+      m_mul(R, A, P);                        // P = R A3
+      m_mul(T, A, R);                        // R = A1 A2 A3
+      w_at(g, W, cr[jpos], p, M);
+      m_mul_acc(R, M, P);                    // P = full R
+      if (jpos >= 2) m_dag_inplace(P);
+#pragma unroll
+      for (int e = 0; e < 9; e++) K[e] = K[e] + P[e];
+    }
+  }
+
+  // ---- output
+  cd o[9];
+  if (kind == MG_FORCE_WIRTINGER) {
+#pragma unroll
+    for (int e = 0; e < 9; e++) o[e] = K[e];
+    m_dag_inplace(o);
+  } else {
+    cd u[9], G[9];
+    load_link<double>(gauge, g.Vh, par, mu, i, u);
+    m_mul(u, K, G);                          // G = i U K (the i is applied below)
+#pragma unroll
+    for (int e = 0; e < 9; e++) G[e] = times_i(G[e]);
+    // H = (G + G^dag)/2, F = (H - tr(H)/3)/2
+    const double trh = (G[0].re + G[4].re + G[8].re) / 3.0;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        cd hh = G[a * 3 + c] + conj(G[c * 3 + a]);
+        hh = mkc(0.5 * hh.re, 0.5 * hh.im);
+        if (a == c) hh.re -= trh;
+        o[a * 3 + c] = mkc(0.5 * hh.re, 0.5 * hh.im);
+      }
+  }
+  const size_t lex = ((((size_t)x[3] * g.L[2] + x[2]) * g.L[1] + x[1]) * g.L[0] + x[0]);
+  double2* dst = out + (lex * 4 + mu) * 9;
+#pragma unroll
+  for (int e = 0; e < 9; e++) dst[e] = make_double2(o[e].re, o[e].im);
+}
+
+// psi <- gamma_5 psi on an ABI fine vector (complex128 [site][spin][colour])
+__global__ void k_gamma5_abi(double2* v, size_t sites) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= sites * 6) return;
+  const size_t site = t / 6, k = 6 + t % 6;   // spins 2, 3
+  double2 z = v[site * 12 + k];
+  v[site * 12 + k] = make_double2(-z.x, -z.y);
+}
+}  // namespace
+
+void gamma5_abi(double* v, size_t sites, cudaStream_t s) {
+  const size_t n = sites * 6;
+  const int bs = 256;
+  k_gamma5_abi<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>((double2*)v, sites);
+  MG_LAUNCH();
+}
+
+void gauge_force(Ctx* c, double* out_abi, const double* lam_abi, const double* psi_abi, int kind) {
+  const Geom& g = c->g;
+  const size_t half = 24 * c->Vh;   // doubles per half vector
+  DBuf vec(sizeof(double) * 4 * half);
+  DBuf W(sizeof(double) * 2 * 6 * 9 * c->V);
+  double* lam_e = vec.as<double>();
+  double* lam_o = lam_e + half;
+  double* psi_e = lam_o + half;
+  double* psi_o = psi_e + half;
+  pack_spinor(g, lam_abi, lam_e, lam_o, false, c->stream);
+  pack_spinor(g, psi_abi, psi_e, psi_o, false, c->stream);
+  const int bs = 128;
+  const int nb = (int)((2 * c->Vh + bs - 1) / bs);
+  k_force_insertion<<<nb, bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, c->csw, W.as<double2>());
+  MG_LAUNCH();
+  k_force_links<<<dim3(nb, 4), bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, c->gauge<double>(),
+                                                   W.as<double2>(), kind, (double2*)out_abi);
+  MG_LAUNCH();
+  c->sync();
+}
+}  // namespace mg

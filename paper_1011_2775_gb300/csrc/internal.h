@@ -268,6 +268,13 @@ void mr_smooth(Ctx* c, const std::function<void(T*, const T*)>& A, T* e, T* r, T
 // --------------------------------------------------------------------------- solve drivers (solver.cu)
 int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int mode, mg_solve_info* info);
 
+// --------------------------------------------------------------------------- gauge derivative (force.cu)
+// gamma_5 in place on ABI fine vectors (`sites` sites of 12 complex128)
+void gamma5_abi(double* v, size_t sites, cudaStream_t s);
+// derivative of -Re<lam, D(U) psi> with respect to the links (ABI layouts;
+// kind = MG_FORCE_SU3 or MG_FORCE_WIRTINGER), see force.cu
+void gauge_force(Ctx* c, double* out_abi, const double* lam_abi, const double* psi_abi, int kind);
+
 // --------------------------------------------------------------------------- multigrid (multigrid.cu)
 void mg_build(Ctx* c, mg_setup_info* info);
 void mg_destroy_hierarchy(Ctx* c);

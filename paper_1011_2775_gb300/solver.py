@@ -18,6 +18,8 @@ class Solver:
         self.dims = tuple(int(d) for d in dims)
         self.ctx = B.mg_create(self.dims, device, stream)
         self.params = B.mg_default_params()
+        self.gauge_ref = None
+        self.gauge_version = None
 
     # -- lifecycle
     def close(self):
@@ -40,6 +42,9 @@ class Solver:
     # -- configuration
     def load_gauge(self, U):
         B.mg_load_gauge(self.ctx, U)
+        # the field the operator was built from (checked by the autograd Function)
+        self.gauge_ref = U
+        self.gauge_version = getattr(U, "_version", None)
 
     def set_clover(self, csw: float, m0: float):
         B.mg_set_clover(self.ctx, csw, m0)
@@ -84,6 +89,22 @@ class Solver:
             out = eta.new_zeros(eta.shape) if not isinstance(eta, np.ndarray) else np.zeros_like(eta)
         st, info = B.mg_solve(self.ctx, out, eta, nrhs, tol, mode, allow_not_converged)
         return out, info
+
+    def solve_dagger(self, eta, tol: float = 1e-10, mode: int = B.MG_MODE_MG, out=None, allow_not_converged=False):
+        """Solve ``D^dag psi = eta`` (same shapes as :meth:`solve`)."""
+        nrhs = 1 if eta.ndim == 6 else eta.shape[0]
+        if out is None:
+            out = eta.new_zeros(eta.shape) if not isinstance(eta, np.ndarray) else np.zeros_like(eta)
+        st, info = B.mg_solve_dagger(self.ctx, out, eta, nrhs, tol, mode, allow_not_converged)
+        return out, info
+
+    def force(self, lam, psi, kind: int = B.MG_FORCE_SU3, out=None):
+        """Derivative of ``-Re<lam, D(U) psi>`` with respect to the links, shaped like the gauge field."""
+        shape = tuple(psi.shape[:4]) + (4, 3, 3)
+        if out is None:
+            out = np.zeros(shape, dtype=np.complex128) if isinstance(psi, np.ndarray) else psi.new_zeros(shape)
+        B.mg_force(self.ctx, out, lam, psi, kind)
+        return out
 
     def apply(self, op: int, x, level: int = 0, prec: int = B.MG_FP64, out_shape=None):
         if out_shape is None:
