@@ -38,7 +38,10 @@
  *   Q the sum of the four plaquette leaves.  D_ee = A_e, D_oo = A_o.
  * - Working precision is internal: FP64 for the outer GCR, FP32 for the
  *   multigrid preconditioner, FP32/FP16/BF16 storage for prolongators and
- *   coarse links (mg_params.storage).  The ABI always exchanges complex128.
+ *   coarse links (mg_params.storage; 16-bit values carry one FP32 scale per
+ *   (block, chirality) tile of P and per (site, direction) tile of the links;
+ *   X, X^{-1} and all vectors stay FP32, accumulation is FP32).  The ABI
+ *   always exchanges complex128.
  */
 #ifndef MGCLOVER_H
 #define MGCLOVER_H
@@ -199,6 +202,17 @@ MG_API int mg_setup(void* ctx, mg_setup_info* info);
  * and to reuse a setup).  get returns the vectors of the last setup. */
 MG_API int mg_set_null_vectors(void* ctx, int level, const void* V, int nv, int where);
 MG_API int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where);
+
+/* Read the coarse operator of level `level` (1 .. levels-1) after mg_setup,
+ * as the solver applies it: the Galerkin links of section "Implementation"
+ * (D_hat v(x) = X(x) v(x) + sum_d Y_d(x) v(x + d), d < 4: from x + mu,
+ * d >= 4: from x - mu), dequantised from their storage format (FP16/BF16
+ * values times their per-tile scale) to complex128.  Layouts (nc = 2 Nv of
+ * the transfer into the level, sites lexicographic as in coarse vectors):
+ * Y [t_c][z_c][y_c][x_c][d 8][row nc][col nc], X [t_c][z_c][y_c][x_c][row nc][col nc].
+ * Buffers are owned by the caller.  Errors: MG_ERR_ARG, MG_ERR_STATE,
+ * MG_ERR_CUDA. */
+MG_API int mg_get_coarse_links(void* ctx, int level, void* Y, void* X, int where);
 
 /* Solve D psi = eta for nrhs right-hand sides (layout above) to
  * ||eta - D psi|| / ||eta|| <= tol, in MG_MODE_MG (multigrid-preconditioned

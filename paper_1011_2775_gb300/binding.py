@@ -38,7 +38,7 @@ MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_D
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_solve", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel",
+            "mg_get_coarse_links", "mg_solve", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel",
             "mg_level_info"]
 
 
@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
             "mg_solve": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
             "mg_solve_dagger": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
             "mg_force": [vp, vp, vp, vp, ip, ip],
+            "mg_get_coarse_links": [vp, ip, vp, vp, ip],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
             "mg_benchmark_kernel": [vp, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_apply_noalloc": [vp, ip, vp, vp, ip],
@@ -229,6 +230,14 @@ def mg_solve_dagger(ctx, psi, eta, nrhs: int, tol: float, mode: int = MG_MODE_MG
     st = lib().mg_solve_dagger(ctx, pp, pe, int(nrhs), float(tol), int(mode), wp, ctypes.byref(info))
     _check(st, "mg_solve_dagger", allow=(MG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return st, info
+
+
+def mg_get_coarse_links(ctx, level: int, Y, X) -> None:
+    py, wy = _buf(Y, writable=True)
+    px, wx = _buf(X, writable=True)
+    if wy != wx:
+        raise TypeError("Y and X must both be host or both be device buffers")
+    _check(lib().mg_get_coarse_links(ctx, int(level), py, px, wy), "mg_get_coarse_links")
 
 
 def mg_force(ctx, F, lam, psi, kind: int = MG_FORCE_SU3) -> None:

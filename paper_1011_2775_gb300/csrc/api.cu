@@ -349,6 +349,27 @@ int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where) {
   });
 }
 
+int mg_get_coarse_links(void* ctx, int level, void* Y, void* X, int where) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    check_where(where);
+    if (!Y || !X) mg::raise(MG_ERR_ARG, "null buffer");
+    if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    if (level < 1 || level >= c->params.levels) mg::raise(MG_ERR_ARG, "level must be a coarse level");
+    int ndof = 0;
+    const size_t sites = level_vec_complex(c, level, &ndof) / ndof;
+    const size_t ybytes = sizeof(double) * 2 * sites * 8 * ndof * ndof;
+    const size_t xbytes = sizeof(double) * 2 * sites * ndof * ndof;
+    Staged sy, sx;
+    stage_out_alloc(sy, Y, ybytes, where);
+    stage_out_alloc(sx, X, xbytes, where);
+    mg::mg_get_links(c, level, sy.ptr, sx.ptr);
+    if (where == MG_HOST) MG_CUDA(cudaMemcpyAsync(Y, sy.ptr, ybytes, cudaMemcpyDeviceToHost, c->stream));
+    stage_out_finish(c, sx, X, xbytes, where);
+    return MG_OK;
+  });
+}
+
 int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where, mg_solve_info* info) {
   return guarded([&]() { return solve_impl(ctx, psi, eta, nrhs, tol, mode, where, info, false); });
 }

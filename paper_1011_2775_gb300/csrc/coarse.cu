@@ -353,7 +353,7 @@ void restrict9(const TransferOp& T, CoarseOp& C, const float* const W[9], int co
 struct HopArgs {
   int nc, s0, dirmask;
   const int* nbr;
-  const float2* Y;
+  const void* Y;    // links in the level's storage format
   const float* Ys;
   const float2* C;  // X or Xinv
   float2* out;
@@ -362,7 +362,7 @@ struct HopArgs {
   float a;
 };
 
-template <int EPI>
+template <int EPI, int ST>
 __global__ void __launch_bounds__(256) k_coarse_hop(HopArgs h) {
   extern __shared__ __align__(16) float2 sm[];  // vin[8 nc], t[nc], vx[nc]
   const int nc = h.nc;
@@ -387,7 +387,8 @@ __global__ void __launch_bounds__(256) k_coarse_hop(HopArgs h) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int rpw = (nc + nw - 1) / nw;
   float2 res[kGemvMaxRows];
-  warp_gemv(h.Y + (size_t)s * nc * 8 * nc, nc, 8 * nc, vin, w, rpw, lane, res);
+  warp_gemv<ST>(static_cast<const char*>(h.Y) + (size_t)s * nc * 8 * nc * link_bytes<ST>(), nc, 8 * nc, vin, w, rpw,
+                lane, res);
   if (lane == 0)
 #pragma unroll
     for (int r = 0; r < kGemvMaxRows; r++) {
@@ -425,7 +426,7 @@ void coarse_hop(const LevelGeom& G, const CoarseOp& C, Epilogue epi, bool use_in
   h.s0 = s0;
   h.dirmask = dirmask;
   h.nbr = G.d_nbr.as<int>();
-  h.Y = C.Y.as<float2>();
+  h.Y = C.Y.get();
   h.Ys = C.Yscale.as<float>();
   h.C = use_inv ? C.Xinv.as<float2>() : C.X.as<float2>();
   h.out = (float2*)out;
@@ -434,12 +435,20 @@ void coarse_hop(const LevelGeom& G, const CoarseOp& C, Epilogue epi, bool use_in
   h.a = a;
   const size_t sm = sizeof(float2) * 10 * (size_t)C.nc;
   const int nb = s1 - s0;
-  switch (epi) {
-    case EPI_H: k_coarse_hop<EPI_H><<<nb, 256, sm, s>>>(h); break;
-    case EPI_CH: k_coarse_hop<EPI_CH><<<nb, 256, sm, s>>>(h); break;
-    case EPI_XPAY: k_coarse_hop<EPI_XPAY><<<nb, 256, sm, s>>>(h); break;
-    case EPI_CX_PAY: k_coarse_hop<EPI_CX_PAY><<<nb, 256, sm, s>>>(h); break;
-    case EPI_C_XPAY: k_coarse_hop<EPI_C_XPAY><<<nb, 256, sm, s>>>(h); break;
+  auto launch = [&](auto st) {
+    constexpr int ST = decltype(st)::value;
+    switch (epi) {
+      case EPI_H: k_coarse_hop<EPI_H, ST><<<nb, 256, sm, s>>>(h); break;
+      case EPI_CH: k_coarse_hop<EPI_CH, ST><<<nb, 256, sm, s>>>(h); break;
+      case EPI_XPAY: k_coarse_hop<EPI_XPAY, ST><<<nb, 256, sm, s>>>(h); break;
+      case EPI_CX_PAY: k_coarse_hop<EPI_CX_PAY, ST><<<nb, 256, sm, s>>>(h); break;
+      case EPI_C_XPAY: k_coarse_hop<EPI_C_XPAY, ST><<<nb, 256, sm, s>>>(h); break;
+    }
+  };
+  switch (C.store) {
+    case STORE_F32: launch(std::integral_constant<int, kStF32>()); break;
+    case STORE_F16: launch(std::integral_constant<int, kStF16>()); break;
+    default: launch(std::integral_constant<int, kStBF16>()); break;
   }
   MG_LAUNCH();
 }
@@ -562,7 +571,8 @@ void coarse_invert(const LevelGeom& G, CoarseOp& C, int* flags, cudaStream_t s) 
 
 // --------------------------------------------------------------------------- folded links
 // One CTA per (odd site o, direction d): A_d(o) = X^{-1}(o) Y_d(o) X^{-1}(o + d).
-__global__ void k_fold_eo(int nc, int half, const int* __restrict__ nbr, const float2* __restrict__ Y,
+template <int ST>
+__global__ void k_fold_eo(int nc, int half, const int* __restrict__ nbr, const void* __restrict__ Y,
                           const float* __restrict__ Ys, const float2* __restrict__ Xinv, float2* A) {
   extern __shared__ __align__(16) float2 fs[];  // Xo, Yd, Xn, T: 4 nc^2
   const int o = half + blockIdx.x, d = blockIdx.y;
@@ -576,8 +586,8 @@ __global__ void k_fold_eo(int nc, int half, const int* __restrict__ nbr, const f
   for (int t = threadIdx.x; t < n2; t += blockDim.x) {
     const int i = t / nc, j = t % nc;
     Xo[t] = Xinv[(size_t)o * n2 + t];
-    const float2 y = Y[(((size_t)o * nc + i) * 8 + d) * nc + j];
-    Yd[t] = make_float2(sc * y.x, sc * y.y);
+    const cx<float> y = sget<ST>(Y, (((size_t)o * nc + i) * 8 + d) * nc + j);
+    Yd[t] = make_float2(sc * y.re, sc * y.im);
     Xn[t] = Xinv[(size_t)nb * n2 + t];
   }
   __syncthreads();
@@ -604,7 +614,8 @@ __global__ void k_fold_eo(int nc, int half, const int* __restrict__ nbr, const f
   }
 }
 
-__global__ void k_cat_links(int nc, int nsites, const float2* __restrict__ Y, const float* __restrict__ Ys,
+template <int ST>
+__global__ void k_cat_links(int nc, int nsites, const void* __restrict__ Y, const float* __restrict__ Ys,
                             const float2* __restrict__ X, float2* A) {
   const size_t total = (size_t)nsites * nc * 9 * nc;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
@@ -613,9 +624,9 @@ __global__ void k_cat_links(int nc, int nsites, const float2* __restrict__ Y, co
     const size_t row = t / ((size_t)9 * nc);  // s * nc + i
     const size_t s = row / nc;
     if (d < 8) {
-      const float2 y = Y[(row * 8 + d) * nc + j];
+      const cx<float> y = sget<ST>(Y, (row * 8 + d) * nc + j);
       const float sc = Ys[s * 8 + d];
-      A[t] = make_float2(sc * y.x, sc * y.y);
+      A[t] = make_float2(sc * y.re, sc * y.im);
     } else {
       A[t] = X[row * nc + j];
     }
@@ -624,17 +635,126 @@ __global__ void k_cat_links(int nc, int nsites, const float2* __restrict__ Y, co
 
 void coarse_fold_links(const LevelGeom& G, CoarseOp& C, cudaStream_t s) {
   const int nc = C.nc;
-  if (G.eo) {
-    const int nodd = G.nsites - G.half;
-    C.A.alloc(sizeof(float2) * (size_t)nodd * nc * 8 * nc);
-    const size_t sm = sizeof(float2) * 4 * (size_t)nc * nc;
-    MG_CUDA(cudaFuncSetAttribute(k_fold_eo, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    k_fold_eo<<<dim3(nodd, 8), 256, sm, s>>>(nc, G.half, G.d_nbr.as<int>(), C.Y.as<float2>(), C.Yscale.as<float>(),
-                                             C.Xinv.as<float2>(), C.A.as<float2>());
-  } else {
-    C.A.alloc(sizeof(float2) * (size_t)G.nsites * nc * 9 * nc);
-    k_cat_links<<<152 * 8, 256, 0, s>>>(nc, G.nsites, C.Y.as<float2>(), C.Yscale.as<float>(), C.X.as<float2>(),
-                                         C.A.as<float2>());
+  auto run = [&](auto st) {
+    constexpr int ST = decltype(st)::value;
+    if (G.eo) {
+      const int nodd = G.nsites - G.half;
+      C.A.alloc(sizeof(float2) * (size_t)nodd * nc * 8 * nc);
+      const size_t sm = sizeof(float2) * 4 * (size_t)nc * nc;
+      MG_CUDA(cudaFuncSetAttribute(k_fold_eo<ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      k_fold_eo<ST><<<dim3(nodd, 8), 256, sm, s>>>(nc, G.half, G.d_nbr.as<int>(), C.Y.get(), C.Yscale.as<float>(),
+                                                   C.Xinv.as<float2>(), C.A.as<float2>());
+    } else {
+      C.A.alloc(sizeof(float2) * (size_t)G.nsites * nc * 9 * nc);
+      k_cat_links<ST><<<152 * 8, 256, 0, s>>>(nc, G.nsites, C.Y.get(), C.Yscale.as<float>(), C.X.as<float2>(),
+                                              C.A.as<float2>());
+    }
+    MG_LAUNCH();
+  };
+  switch (C.store) {
+    case STORE_F32: run(std::integral_constant<int, STORE_F32>()); break;
+    case STORE_F16: run(std::integral_constant<int, STORE_F16>()); break;
+    default: run(std::integral_constant<int, STORE_BF16>()); break;
+  }
+}
+
+// --------------------------------------------------------------------------- 16-bit links
+// One CTA per tile (site s = blockIdx.x, block d = blockIdx.y) of an FP32 link
+// array [nsites][nc][nb][nc]: scale = largest |Re|, |Im| of the tile (1 for
+// an all-zero tile), stored value = link / scale in format ST.
+template <int ST>
+__global__ void k_quantize_links(int nc, int nb, const float2* __restrict__ in, void* out, float* scale) {
+  __shared__ float smax[32];
+  __shared__ float sc_s;
+  const int s = blockIdx.x, d = blockIdx.y;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n2 = nc * nc;
+  float m = 0.f;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const int i = t / nc, j = t % nc;
+    const float2 z = in[(((size_t)s * nc + i) * nb + d) * nc + j];
+    m = fmaxf(m, fmaxf(fabsf(z.x), fabsf(z.y)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) smax[wid] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.f;
+    for (int q = 0; q < nw; q++) v = fmaxf(v, smax[q]);
+    sc_s = v > 0.f ? v : 1.f;
+    scale[(size_t)s * nb + d] = sc_s;
+  }
+  __syncthreads();
+  const float inv = 1.f / sc_s;
+  for (int t = threadIdx.x; t < n2; t += blockDim.x) {
+    const int i = t / nc, j = t % nc;
+    const size_t e = (((size_t)s * nc + i) * nb + d) * nc + j;
+    const float2 z = in[e];
+    sput<ST>(out, e, mkc(z.x * inv, z.y * inv));
+  }
+}
+
+namespace {
+// replaces `buf` ([nsites][nc][nb][nc] FP32) by its 16-bit copy; scales -> `scale`
+void quantize_array(DBuf& buf, DBuf& scale, int nsites, int nc, int nb, int store, cudaStream_t s) {
+  DBuf q(sizeof(uint32_t) * (size_t)nsites * nc * nb * nc);
+  scale.alloc(sizeof(float) * (size_t)nsites * nb);
+  const dim3 grid(nsites, nb);
+  if (store == STORE_F16)
+    k_quantize_links<STORE_F16><<<grid, 256, 0, s>>>(nc, nb, buf.as<float2>(), q.get(), scale.as<float>());
+  else
+    k_quantize_links<STORE_BF16><<<grid, 256, 0, s>>>(nc, nb, buf.as<float2>(), q.get(), scale.as<float>());
+  MG_LAUNCH();
+  MG_CUDA(cudaStreamSynchronize(s));
+  buf = std::move(q);
+}
+}  // namespace
+
+void quantize_links(const LevelGeom& G, CoarseOp& C, int store, cudaStream_t s) {
+  if (store == STORE_F32) return;
+  if (C.store != STORE_F32) raise(MG_ERR_STATE, "coarse links are already quantised");
+  if (C.A.get()) raise(MG_ERR_STATE, "quantise the links before folding them");
+  quantize_array(C.Y, C.Yscale, G.nsites, C.nc, 8, store, s);
+  C.store = store;
+}
+
+template <int ST>
+__global__ void k_links_abi(int nc, int nsites, const int* __restrict__ lex_of, const void* Y,
+                            const float* __restrict__ Ys, const float2* __restrict__ X, double2* Yabi, double2* Xabi) {
+  const size_t per = (size_t)9 * nc * nc;
+  const size_t total = (size_t)nsites * per;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t s = t / per;
+    const int r = (int)(t % per);
+    const int d = r / (nc * nc), i = (r / nc) % nc, j = r % nc;
+    const size_t lex = (size_t)lex_of[s];
+    if (d < 8) {
+      const cx<float> z = sget<ST>(Y, ((s * nc + i) * 8 + d) * nc + j);
+      const double sc = Ys[s * 8 + d];
+      Yabi[((lex * 8 + d) * nc + i) * nc + j] = make_double2(sc * z.re, sc * z.im);
+    } else {
+      const float2 z = X[(s * nc + i) * nc + j];
+      Xabi[(lex * nc + i) * nc + j] = make_double2(z.x, z.y);
+    }
+  }
+}
+
+void coarse_links_abi(const LevelGeom& G, const CoarseOp& C, double* Y_abi, double* X_abi, cudaStream_t s) {
+  const int nc = C.nc;
+  const int* lex = G.d_lex_of.as<int>();
+  switch (C.store) {
+    case STORE_F32:
+      k_links_abi<STORE_F32><<<152 * 8, 256, 0, s>>>(nc, G.nsites, lex, C.Y.get(), C.Yscale.as<float>(),
+                                                     C.X.as<float2>(), (double2*)Y_abi, (double2*)X_abi);
+      break;
+    case STORE_F16:
+      k_links_abi<STORE_F16><<<152 * 8, 256, 0, s>>>(nc, G.nsites, lex, C.Y.get(), C.Yscale.as<float>(),
+                                                     C.X.as<float2>(), (double2*)Y_abi, (double2*)X_abi);
+      break;
+    default:
+      k_links_abi<STORE_BF16><<<152 * 8, 256, 0, s>>>(nc, G.nsites, lex, C.Y.get(), C.Yscale.as<float>(),
+                                                      C.X.as<float2>(), (double2*)Y_abi, (double2*)X_abi);
+      break;
   }
   MG_LAUNCH();
 }

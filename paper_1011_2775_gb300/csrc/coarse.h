@@ -69,10 +69,20 @@ struct CoarseOp {
   //  even-odd levels: A[o - half][nc][8][nc] = X_o^{-1} Y_d(o) X^{-1}(o + d) on odd
   //  sites, so that (X_o^{-1} Y_oe X_e^{-1} y)(o) = sum_d A_d(o) y(o + d);
   //  other levels: [site][nc][9][nc] = [Y_0 .. Y_7 | X], so D_hat v is one GEMV.
+  // The folded links are products, built in FP32 from the stored (dequantised)
+  // Y, so the persistent solve applies exactly the operator of Y and X.
   DBuf A;
 };
 
-// builds C.A from Y, X, Xinv (see CoarseOp)
+// Quantises Y from FP32 to `store` (FP16 / BF16) with one scale per
+// (site, direction) tile: the largest |Re|, |Im| of the tile, so that every
+// stored value lies in [-1, 1].  X and X^{-1} stay FP32.  Runs before
+// coarse_fold_links.
+void quantize_links(const LevelGeom& G, CoarseOp& C, int store, cudaStream_t s);
+// dequantised links in ABI order: Y_abi[lex][8][nc][nc], X_abi[lex][nc][nc] complex128
+void coarse_links_abi(const LevelGeom& G, const CoarseOp& C, double* Y_abi, double* X_abi, cudaStream_t s);
+
+// builds C.A from the stored Y, X, Xinv (see CoarseOp)
 void coarse_fold_links(const LevelGeom& G, CoarseOp& C, cudaStream_t s);
 
 // ---- transfer kernels (coarse.cu)

@@ -45,11 +45,11 @@ struct CGArgs {
   int nc, half, nsites, m, maxit, eo, nsplit;
   double tol_rel;
   const int* nbr;
-  const float2* Y;
-  const float* Ys;
+  const void* Y;     // links, storage format of the kernel's ST
+  const float* Ys;   // Y tile scales [site][8]
   const float2* X;
   const float2* Xinv;
-  const float2* A;   // folded links (CoarseOp::A)
+  const float2* A;   // folded links (CoarseOp::A), FP32
   const float2* b;   // full right-hand side
   float2* x;         // full solution
   float2* r;         // residual (half when eo, else full)
@@ -153,6 +153,7 @@ __device__ void site_mul(const CGArgs& a, const float2* C, int s0, int s1, float
 //   mode 2: out = Xinv (x_self - hop(in))      (reconstruction of the odd sites)
 //   mode 3: out = X x_self + hop(in)           (full D_hat, no even-odd)
 // x_self is read from `xs`.
+template <int ST>
 __device__ void hop_phase(const CGArgs& a, int mode, int s0, int s1, float2* out, const float2* in, const float2* xs,
                           float2* sm) {
   const int nc = a.nc;
@@ -171,7 +172,8 @@ __device__ void hop_phase(const CGArgs& a, int mode, int s0, int s1, float2* out
     for (int t = threadIdx.x; t < nc; t += blockDim.x) vx[t] = xs[(size_t)s * nc + t];
     __syncthreads();
     float2 res[kGemvMaxRows];
-    warp_gemv(a.Y + (size_t)s * nc * 8 * nc, nc, 8 * nc, vin, w, rpw, lane, res);
+    warp_gemv<ST>(static_cast<const char*>(a.Y) + (size_t)s * nc * 8 * nc * link_bytes<ST>(), nc, 8 * nc, vin, w, rpw,
+                  lane, res);
     if (lane == 0)
 #pragma unroll
       for (int r = 0; r < kGemvMaxRows; r++) {
@@ -203,10 +205,13 @@ __device__ void hop_phase(const CGArgs& a, int mode, int s0, int s1, float2* out
 
 // One GEMV per site with the site's rows split over a.nsplit work items, so
 // the blocks stay balanced when there are fewer sites than 2x blocks.
-// Links L: site s uses L + (s - lbase) * nc * nb * nc (row-major, nb blocks of
-// nc columns); its vector gathers the 8 neighbours (and, for nb == 9, the
-// site itself).  subtract: out = xs - L v, else out = L v.
-__device__ void hop_rows(const CGArgs& a, const float2* L, const float* scale, int lbase, int nb, bool subtract,
+// Links L (storage format ST): site s uses L + (s - lbase) * nc * nb * nc
+// (row-major, nb blocks of nc columns) with tile scales
+// scale[(s - lbase) * nb + block] (null: 1); its vector gathers the 8
+// neighbours (and, for nb == 9, the site itself).  subtract: out = xs - L v,
+// else out = L v.
+template <int ST>
+__device__ void hop_rows(const CGArgs& a, const void* L, const float* scale, int lbase, int nb, bool subtract,
                          int s0, int s1, float2* out, const float2* in, const float2* xs, float2* sm) {
   const int nc = a.nc;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -219,15 +224,16 @@ __device__ void hop_rows(const CGArgs& a, const float2* L, const float* scale, i
     for (int t = threadIdx.x; t < nb * nc; t += blockDim.x) {
       const int d = t / nc, j = t % nc;
       float2 x = d < 8 ? in[(size_t)a.nbr[(size_t)s * 8 + d] * nc + j] : in[(size_t)s * nc + j];
-      if (scale && d < 8) {
-        const float sc = scale[(size_t)s * 8 + d];
+      if (scale) {
+        const float sc = scale[(size_t)(s - lbase) * nb + d];
         x = make_float2(sc * x.x, sc * x.y);
       }
       sm[t] = x;
     }
     __syncthreads();
     float2 res[kGemvMaxRows];
-    warp_gemv_rows(L + (size_t)(s - lbase) * nc * nb * nc, row0, row1, nb * nc, sm, w, rpw, lane, res);
+    warp_gemv_rows<ST>(static_cast<const char*>(L) + (size_t)(s - lbase) * nc * nb * nc * link_bytes<ST>(), row0, row1,
+                       nb * nc, sm, w, rpw, lane, res);
     if (lane == 0)
 #pragma unroll
       for (int r = 0; r < kGemvMaxRows; r++) {
@@ -247,19 +253,21 @@ __device__ void hop_rows(const CGArgs& a, const float2* L, const float* scale, i
 
 // w = A v with A = D_r on the even sites (folded links: two GEMV phases, one
 // barrier) or the full D_hat (one GEMV phase over [Y | X])
+template <int ST>
 __device__ void apply_A(const CGArgs& a, cg::grid_group& grid, float2* w, const float2* v, float2* sm) {
   if (a.eo) {
-    hop_rows(a, a.A, nullptr, a.half, 8, false, a.half, a.nsites, a.tB, v, nullptr, sm);  // X_o^-1 Y_oe X_e^-1 v_e
+    hop_rows<kStF32>(a, a.A, nullptr, a.half, 8, false, a.half, a.nsites, a.tB, v, nullptr, sm);  // X_o^-1 Y_oe X_e^-1 v_e
     grid.sync();
-    hop_rows(a, a.Y, a.Ys, 0, 8, true, 0, a.half, w, a.tB, v, sm);                       // w_e = v_e - Y_eo t_o
+    hop_rows<ST>(a, a.Y, a.Ys, 0, 8, true, 0, a.half, w, a.tB, v, sm);                            // w_e = v_e - Y_eo t_o
   } else {
-    hop_rows(a, a.A, nullptr, 0, 9, false, 0, a.nsites, w, v, nullptr, sm);              // w = [Y | X] v
+    hop_rows<kStF32>(a, a.A, nullptr, 0, 9, false, 0, a.nsites, w, v, nullptr, sm);               // w = [Y | X] v
   }
 }
 
 // Each block owns a contiguous chunk [e0, e1) of every (half) vector for the
 // element-wise phases; the stencil phases own whole sites.  Phases with
 // different ownership are always separated by a grid barrier.
+template <int ST>
 __global__ void __launch_bounds__(kThreads) k_coarse_gcr(CGArgs a) {
   cg::grid_group grid = cg::this_grid();
   extern __shared__ __align__(16) double dsm[];
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_gcr(CGArgs a) {
   if (a.eo) {
     site_mul(a, a.Xinv, a.half, a.nsites, a.tB, a.b, sm);        // t_o = X_o^{-1} b_o
     grid.sync();
-    hop_rows(a, a.Y, a.Ys, 0, 8, true, 0, a.half, a.br, a.tB, a.b, sm);  // b_r = b_e - Y_eo t_o
+    hop_rows<ST>(a, a.Y, a.Ys, 0, 8, true, 0, a.half, a.br, a.tB, a.b, sm);  // b_r = b_e - Y_eo t_o
     rhs = a.br;
   }
   grid.sync();
@@ -315,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_gcr(CGArgs a) {
       float2* wk = a.W + (size_t)k * n;
       float2* zk = a.Z + (size_t)k * n;
       for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) zk[e] = a.r[e];
-      apply_A(a, grid, wk, a.r, sm);
+      apply_A<ST>(a, grid, wk, a.r, sm);
       grid.sync();
       // beta_j = <w_j, w> over this block's chunk: warp w owns j = w + u*nw,
       // u < 4, and issues the loads of all four before reducing
@@ -432,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_gcr(CGArgs a) {
     grid.sync();
     if (done) break;
     // true residual r = rhs - A y
-    apply_A(a, grid, a.r, a.y, sm);
+    apply_A<ST>(a, grid, a.r, a.y, sm);
     grid.sync();
     v[0] = 0.0;
     for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -451,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) k_coarse_gcr(CGArgs a) {
   if (a.eo) {
     site_mul(a, a.Xinv, 0, a.half, a.x, a.y, sm);                 // x_e = X_e^{-1} y_e
     grid.sync();
-    hop_phase(a, 2, a.half, a.nsites, a.x, a.x, a.b, sm);         // x_o = X_o^{-1}(b_o - Y_oe x_e)
+    hop_phase<ST>(a, 2, a.half, a.nsites, a.x, a.x, a.b, sm);     // x_o = X_o^{-1}(b_o - Y_oe x_e)
   } else {
     for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) a.x[e] = a.y[e];
   }
@@ -468,8 +476,16 @@ int coarse_gcr_grid(int nc) {
   int sms = 0;
   MG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const size_t smem = sizeof(double) * (kNR * 8 + kNR) + sizeof(float2) * 10 * (size_t)nc;
-  int per = 0;
-  MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_coarse_gcr, kThreads, smem));
+  // the smallest residency of the three storage instantiations, so that any
+  // of them can be launched cooperatively on this grid
+  int per = 1 << 20;
+  const void* kernels[3] = {(const void*)k_coarse_gcr<kStF32>, (const void*)k_coarse_gcr<kStF16>,
+                            (const void*)k_coarse_gcr<kStBF16>};
+  for (const void* k : kernels) {
+    int p = 0;
+    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, k, kThreads, smem));
+    per = p < per ? p : per;
+  }
   if (per < 1) raise(MG_ERR_CUDA, "persistent coarse GCR cannot be resident");
   return sms * (per < 4 ? per : 4);
 }
@@ -486,7 +502,7 @@ void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuff
   a.eo = G.eo ? 1 : 0;
   a.tol_rel = tol_rel;
   a.nbr = G.d_nbr.as<int>();
-  a.Y = C.Y.as<float2>();
+  a.Y = C.Y.get();
   a.Ys = C.Yscale.as<float>();
   a.X = C.X.as<float2>();
   a.Xinv = C.Xinv.as<float2>();
@@ -509,7 +525,10 @@ void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuff
   const size_t smem = sizeof(double) * (kNR * 8 + kNR) + sizeof(float2) * 10 * (size_t)C.nc;
   const int grid = B.grid;
   void* params[] = {&a};
-  MG_CUDA(cudaLaunchCooperativeKernel((const void*)k_coarse_gcr, dim3(grid), dim3(kThreads), params, smem, s));
+  const void* kern = C.store == STORE_F16    ? (const void*)k_coarse_gcr<kStF16>
+                     : C.store == STORE_BF16 ? (const void*)k_coarse_gcr<kStBF16>
+                                             : (const void*)k_coarse_gcr<kStF32>;
+  MG_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), params, smem, s));
   MG_LAUNCH();
 }
 

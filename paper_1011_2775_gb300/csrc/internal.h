@@ -282,6 +282,8 @@ void mg_destroy_hierarchy(Ctx* c);
 void mg_precondition(Ctx* c, float* z_e, const float* r_e);
 void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in_abi);
 void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv);
+// dequantised coarse links of level >= 1 (ABI layouts, see mg_get_coarse_links)
+void mg_get_links(Ctx* c, int level, double* Y_abi, double* X_abi);
 void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof);
 void mg_reset_counters(Ctx* c);
 // times `iters` applications of the level-1 coarse D_hat_r (see mg_benchmark_kernel)

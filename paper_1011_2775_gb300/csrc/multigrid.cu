@@ -370,6 +370,7 @@ void build_coarse_links(Ctx* c, Hierarchy& H, int l) {
     }
   coarse_invert(Gc, C, c->ws.flags.as<int>(), s);
   if (c->read_flag(FLAG_SINGULAR, true)) raise(MG_ERR_SINGULAR_CLOVER, "singular coarse diagonal block");
+  quantize_links(Gc, C, T.store, s);               // 16-bit storage of Y (FP32: no-op)
   if (l + 2 == H.L) coarse_fold_links(Gc, C, s);  // the coarsest level runs the persistent solver
 }
 
@@ -551,6 +552,12 @@ void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof) {
   if (!c->mg || level >= c->mg->L) raise(MG_ERR_STATE, "level not set up");
   for (int m = 0; m < 4; m++) dims[m] = c->mg->geo[level].L[m];
   *ndof = c->mg->geo[level].ndof;
+}
+
+void mg_get_links(Ctx* c, int level, double* Y_abi, double* X_abi) {
+  if (!c->mg || level < 1 || level >= c->mg->L) raise(MG_ERR_STATE, "coarse level not set up");
+  Hierarchy& H = *c->mg;
+  coarse_links_abi(H.geo[level], H.cop[level], Y_abi, X_abi, c->stream);
 }
 
 void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv) {

@@ -75,6 +75,16 @@ class Solver:
         B.mg_get_null_vectors(self.ctx, level, out, out.shape[0])
         return out
 
+    def coarse_links(self, level: int):
+        """Dequantised coarse links ``(Y, X)`` of a coarse level: ``Y`` shaped
+        ``(Tc, Zc, Yc, Xc, 8, nc, nc)``, ``X`` shaped ``(Tc, Zc, Yc, Xc, nc, nc)``."""
+        dims, nc = self.level_info(level)
+        shp = (dims[3], dims[2], dims[1], dims[0])
+        Y = np.zeros(shp + (8, nc, nc), dtype=np.complex128)
+        X = np.zeros(shp + (nc, nc), dtype=np.complex128)
+        B.mg_get_coarse_links(self.ctx, level, Y, X)
+        return Y, X
+
     def setup(self):
         return B.mg_setup(self.ctx)
 
