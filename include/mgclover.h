@@ -123,6 +123,8 @@ typedef struct {
   int storage;                    /* mg_storage of prolongators and coarse links                 */
   int coarse_op;                  /* mg_coarse_op: Galerkin projection of D_p (paper) or of D    */
   uint64_t seed;                  /* Philox4x32-10 key of the setup's random start vectors       */
+  int rhs_block;                  /* mg_solve (MG mode): right-hand sides solved together in      */
+                                  /* lock-step, 1..16 (1: one after another)                      */
 } mg_params;
 
 typedef struct {
@@ -161,7 +163,7 @@ MG_API const char* mg_last_error(void);
 /* Fill `p` with the defaults: 2 levels, 4^4 blocks, Nv = 24, 20 passes of 8
  * GCR iterations, RQ tolerance 0.05, nu_post = 4, coarse tolerance 0.1,
  * coarse restart 32 / cap 50, outer restart 16 / cap 500, FP32 storage,
- * Galerkin projection of D_p, seed 3. */
+ * Galerkin projection of D_p, seed 3, rhs_block 16. */
 MG_API int mg_default_params(mg_params* p);
 
 /* Create a context for a lattice of `dims` on CUDA device `device`; kernels
@@ -216,7 +218,14 @@ MG_API int mg_get_coarse_links(void* ctx, int level, void* Y, void* X, int where
 
 /* Solve D psi = eta for nrhs right-hand sides (layout above) to
  * ||eta - D psi|| / ||eta|| <= tol, in MG_MODE_MG (multigrid-preconditioned
- * FGCR; needs mg_setup) or MG_MODE_EO_GCR (plain FP64 even-odd GCR).  `info`
+ * FGCR; needs mg_setup) or MG_MODE_EO_GCR (plain FP64 even-odd GCR).  In
+ * MG mode groups of up to mg_params.rhs_block right-hand sides are solved
+ * together: one FGCR per right-hand side, run in lock-step so that every
+ * iteration applies D_r to all of them in one multi-RHS launch and the
+ * multigrid cycle to all of them at once (all coarsest-level solves in one
+ * persistent launch); each right-hand side keeps its own Krylov space and
+ * convergence test, so the results match separate solves to the tolerance.
+ * info->outer_iterations sums the iterations of every right-hand side.  `info`
  * may be NULL.  Errors: MG_ERR_STATE, MG_ERR_ARG, MG_ERR_NAN,
  * MG_ERR_NOT_CONVERGED (psi holds the best iterate), MG_ERR_CUDA. */
 MG_API int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
@@ -298,6 +307,17 @@ MG_API int mg_apply_noalloc(void* ctx, int op, void* out, const void* in, int pr
  * MG_ERR_STATE, MG_ERR_CUDA. */
 MG_API int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int iters, double* avg_ms,
                                double* bytes_per_launch);
+
+/* mg_benchmark_kernel for nrhs right-hand sides per launch (fine kernels:
+ * the multi-RHS forms with their autotuned CTA size; nrhs = 1 is
+ * mg_benchmark_kernel).  Algorithmic bytes count links and clover once per
+ * site and spinors once per (site, rhs):
+ *   DSLASH_CLOVER: Vh * (144 + 72 + 48 nrhs) reals,
+ *   DSLASH_XPAY:   Vh * (144 + 72 nrhs) reals,
+ *   DR:            Vh * (432 + 168 nrhs) reals.
+ * Errors as mg_benchmark_kernel; MG_KERNEL_COARSE_DR takes nrhs = 1 only. */
+MG_API int mg_benchmark_kernel_nrhs(void* ctx, int kernel, int prec, int nrhs, int warmup, int iters, double* avg_ms,
+                                    double* bytes_per_launch);
 
 /* Lattice size of level `level` after setup (dims_out[4] = {Lx,Ly,Lz,Lt})
  * and its dof per site (12 on the fine level, 2*nv[level-1] on coarse ones). */

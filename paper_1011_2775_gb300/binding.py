@@ -38,7 +38,7 @@ MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_D
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_get_coarse_links", "mg_solve", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel",
+            "mg_get_coarse_links", "mg_solve", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
             "mg_level_info"]
 
 
@@ -58,7 +58,8 @@ class mg_params(ctypes.Structure):
                 ("maxit_fine", ctypes.c_int),
                 ("storage", ctypes.c_int),
                 ("coarse_op", ctypes.c_int),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64),
+                ("rhs_block", ctypes.c_int)]
 
 
 class mg_setup_info(ctypes.Structure):
@@ -118,6 +119,7 @@ def lib() -> ctypes.CDLL:
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
             "mg_benchmark_kernel": [vp, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_apply_noalloc": [vp, ip, vp, vp, ip],
+            "mg_benchmark_kernel_nrhs": [vp, ip, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_level_info": [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)],
         }
         for name, args in sig.items():
@@ -271,6 +273,14 @@ def mg_benchmark_kernel(ctx, kernel: int, prec: int = MG_FP32, warmup: int = 5, 
     ms, by = ctypes.c_double(), ctypes.c_double()
     _check(lib().mg_benchmark_kernel(ctx, int(kernel), int(prec), int(warmup), int(iters), ctypes.byref(ms),
                                      ctypes.byref(by)), "mg_benchmark_kernel")
+    return ms.value, by.value
+
+
+def mg_benchmark_kernel_nrhs(ctx, kernel: int, prec: int = MG_FP32, nrhs: int = 1, warmup: int = 5, iters: int = 50):
+    """Returns ``(avg_ms_per_launch, algorithmic_bytes_per_launch)`` for nrhs right-hand sides."""
+    ms, by = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mg_benchmark_kernel_nrhs(ctx, int(kernel), int(prec), int(nrhs), int(warmup), int(iters),
+                                          ctypes.byref(ms), ctypes.byref(by)), "mg_benchmark_kernel_nrhs")
     return ms.value, by.value
 
 

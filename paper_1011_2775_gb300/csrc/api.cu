@@ -115,8 +115,12 @@ int solve_impl(void* ctx, void* psi, const void* eta, int nrhs, double tol, int 
   stage_out_alloc(so, psi, per * nrhs, where);
   if (dagger) mg::gamma5_abi(si.ptr, c->V * nrhs, c->stream);
   int status = MG_OK;
-  for (int r = 0; r < nrhs; r++) {
-    const int st = mg::solve_fine(c, so.ptr + (size_t)r * 24 * c->V, si.ptr + (size_t)r * 24 * c->V, tol, mode, &local);
+  const int blk = mode == MG_MODE_MG ? c->params.rhs_block : 1;
+  for (int r = 0; r < nrhs; r += blk) {
+    const int nb = nrhs - r < blk ? nrhs - r : blk;
+    double* po = so.ptr + (size_t)r * 24 * c->V;
+    const double* pi = si.ptr + (size_t)r * 24 * c->V;
+    const int st = nb > 1 ? mg::solve_fine_block(c, po, pi, nb, tol, &local) : mg::solve_fine(c, po, pi, tol, mode, &local);
     if (st != MG_OK) status = st;
   }
   if (dagger) mg::gamma5_abi(so.ptr, c->V * nrhs, c->stream);
@@ -177,6 +181,7 @@ int mg_default_params(mg_params* p) {
   p->storage = MG_STORE_FP32;
   p->coarse_op = MG_COARSE_DP;
   p->seed = 3;
+  p->rhs_block = 16;
   return MG_OK;
 }
 
@@ -274,6 +279,7 @@ int mg_set_params(void* ctx, const mg_params* p) {
     if (p->restart_fine < 1 || p->restart_fine > 64 || p->maxit_fine < 1) mg::raise(MG_ERR_ARG, "bad outer solver parameters");
     if (p->storage < MG_STORE_FP32 || p->storage > MG_STORE_BF16) mg::raise(MG_ERR_ARG, "bad storage");
     if (p->coarse_op != MG_COARSE_DP && p->coarse_op != MG_COARSE_D) mg::raise(MG_ERR_ARG, "bad coarse_op");
+    if (p->rhs_block < 1 || p->rhs_block > 16) mg::raise(MG_ERR_ARG, "rhs_block must be in [1, 16]");
     int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
     int ndof = 12;
     for (int l = 0; l + 1 < p->levels; l++) {
@@ -416,35 +422,50 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
     Staged si, so;
     stage_in(c, si, in, sizeof(double) * 2 * nin * nrhs, where);
     stage_out_alloc(so, out, sizeof(double) * 2 * nout * nrhs, where);
-    for (int r = 0; r < nrhs; r++) {
-      const double* ip = si.ptr + (size_t)r * 2 * nin;
-      double* op_ = so.ptr + (size_t)r * 2 * nout;
-      if (level > 0 || op == MG_OP_R || op == MG_OP_P || op == MG_OP_CYCLE) {
-        mg::mg_apply_level(c, op, level, op_, ip);
-        continue;
-      }
+    if (op == MG_OP_CYCLE && level == 0 && nrhs > 1) {
+      mg::mg_cycle_batch(c, so.ptr, si.ptr, nrhs);   // all rhs through the batched cycle
+    } else if (level > 0 || op == MG_OP_R || op == MG_OP_P || op == MG_OP_CYCLE) {
+      for (int r = 0; r < nrhs; r++)
+        mg::mg_apply_level(c, op, level, so.ptr + (size_t)r * 2 * nout, si.ptr + (size_t)r * 2 * nin);
+    } else {
+      // fine level: all right-hand sides in one launch per kernel, as packed
+      // half vectors [even halves of every rhs][odd halves of every rhs]
       const bool f32 = prec == MG_FP32;
       const size_t es = f32 ? sizeof(float) : sizeof(double);
       const size_t half = 24 * c->Vh;  // reals per half vector
-      mg::DBuf ib(es * 2 * half), ob(es * 2 * half);
-      MG_CUDA(cudaMemsetAsync(ob.get(), 0, es * 2 * half, c->stream));
+      mg::DBuf ib(es * 2 * half * nrhs), ob(es * 2 * half * nrhs);
+      MG_CUDA(cudaMemsetAsync(ob.get(), 0, es * 2 * half * nrhs, c->stream));
       char* ie = ib.as<char>();
-      char* io = ie + es * half;
+      char* io = ie + es * half * nrhs;
       char* oe = ob.as<char>();
-      char* oo = oe + es * half;
-      mg::pack_spinor(c->g, ip, ie, io, f32, c->stream);
+      char* oo = oe + es * half * nrhs;
+      for (int r = 0; r < nrhs; r++)
+        mg::pack_spinor(c->g, si.ptr + (size_t)r * 2 * nin, ie + es * half * r, io + es * half * r, f32, c->stream);
       auto run = [&](auto* tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
         mg::FineOps<T> F(c);
         T *ie_ = (T*)ie, *io_ = (T*)io, *oe_ = (T*)oe, *oo_ = (T*)oo;
+        if (nrhs == 1) {
+          switch (op) {
+            case MG_OP_D: F.D(oe_, oo_, ie_, io_); break;
+            case MG_OP_DP: F.Dp(oe_, oo_, ie_, io_); break;
+            case MG_OP_DR: F.Dr(oe_, ie_); break;
+            case MG_OP_BR: F.br(oe_, ie_, io_); break;
+            case MG_OP_M: F.M(oe_, oo_, ie_, io_, false); break;
+            case MG_OP_MINV: F.M(oe_, oo_, ie_, io_, true); break;
+            case MG_OP_HOP: F.H(oe_, oo_, ie_, io_); break;
+            default: mg::raise(MG_ERR_ARG, "bad operator");
+          }
+          return;
+        }
         switch (op) {
-          case MG_OP_D: F.D(oe_, oo_, ie_, io_); break;
-          case MG_OP_DP: F.Dp(oe_, oo_, ie_, io_); break;
-          case MG_OP_DR: F.Dr(oe_, ie_); break;
-          case MG_OP_BR: F.br(oe_, ie_, io_); break;
-          case MG_OP_M: F.M(oe_, oo_, ie_, io_, false); break;
-          case MG_OP_MINV: F.M(oe_, oo_, ie_, io_, true); break;
-          case MG_OP_HOP: F.H(oe_, oo_, ie_, io_); break;
+          case MG_OP_D: F.D_multi(oe_, oo_, ie_, io_, nrhs, half); break;
+          case MG_OP_DP: F.Dp_multi(oe_, oo_, ie_, io_, nrhs, half); break;
+          case MG_OP_DR: F.Dr_multi(oe_, ie_, nrhs, half); break;
+          case MG_OP_BR: F.br_multi(oe_, ie_, io_, nrhs, half); break;
+          case MG_OP_M: F.M_multi(oe_, oo_, ie_, io_, false, nrhs, half); break;
+          case MG_OP_MINV: F.M_multi(oe_, oo_, ie_, io_, true, nrhs, half); break;
+          case MG_OP_HOP: F.H_multi(oe_, oo_, ie_, io_, nrhs, half); break;
           default: mg::raise(MG_ERR_ARG, "bad operator");
         }
       };
@@ -452,7 +473,8 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
         run((float*)nullptr);
       else
         run((double*)nullptr);
-      mg::unpack_spinor(c->g, oe, oo, f32, op_, c->stream);
+      for (int r = 0; r < nrhs; r++)
+        mg::unpack_spinor(c->g, oe + es * half * r, oo + es * half * r, f32, so.ptr + (size_t)r * 2 * nout, c->stream);
       c->sync();
     }
     stage_out_finish(c, so, out, sizeof(double) * 2 * nout * nrhs, where);
@@ -462,12 +484,18 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
 
 int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int iters, double* avg_ms,
                         double* bytes_per_launch) {
+  return mg_benchmark_kernel_nrhs(ctx, kernel, prec, 1, warmup, iters, avg_ms, bytes_per_launch);
+}
+
+int mg_benchmark_kernel_nrhs(void* ctx, int kernel, int prec, int nrhs, int warmup, int iters, double* avg_ms,
+                             double* bytes_per_launch) {
   return guarded([&]() {
     mg::Ctx* c = as_ctx(ctx);
-    if (!avg_ms || !bytes_per_launch || iters < 1 || warmup < 0) mg::raise(MG_ERR_ARG, "bad benchmark arguments");
+    if (!avg_ms || !bytes_per_launch || iters < 1 || warmup < 0 || nrhs < 1) mg::raise(MG_ERR_ARG, "bad benchmark arguments");
     if (prec != MG_FP64 && prec != MG_FP32) mg::raise(MG_ERR_ARG, "bad precision");
     if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
     if (kernel == MG_KERNEL_COARSE_DR) {
+      if (nrhs != 1) mg::raise(MG_ERR_ARG, "the coarse benchmark takes one right-hand side");
       mg::mg_benchmark_coarse(c, warmup, iters, avg_ms, bytes_per_launch);
       return MG_OK;
     }
@@ -482,22 +510,51 @@ int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int iters, 
     double ms = 0, bytes = 0;
     auto run = [&](auto* tag) {
       using T = std::remove_pointer_t<decltype(tag)>;
-      mg::DBuf in(sizeof(T) * half_reals), x(sizeof(T) * half_reals), out(sizeof(T) * half_reals);
-      mg::blas_convert<float, T>(in.as<T>(), a32.as<float>(), half_reals / 2, c->stream);
-      mg::blas_convert<float, T>(x.as<T>(), a32.as<float>() + half_reals, half_reals / 2, c->stream);
+      const size_t hn = half_reals * nrhs;
+      mg::DBuf in(sizeof(T) * hn), x(sizeof(T) * hn), out(sizeof(T) * hn);
+      for (int q = 0; q < nrhs; q++) {
+        mg::blas_convert<float, T>(in.as<T>() + q * half_reals, a32.as<float>(), half_reals / 2, c->stream);
+        mg::blas_convert<float, T>(x.as<T>() + q * half_reals, a32.as<float>() + half_reals, half_reals / 2, c->stream);
+      }
       mg::FineOps<T> F(c);
       const mg::Geom& g = c->g;
+      int blk_ch = 128, blk_xp = 128;
+      if (nrhs > 1) {   // the autotuned CTA sizes the solver would use
+        auto kch = [&](int b) {
+          mg::dslash_mrhs<T>(g, mg::EPI_CH, 1, nrhs, half_reals, out.as<T>(), in.as<T>(), c->gauge<T>(), c->Ainv<T>(1),
+                             nullptr, 0.0, 0xff, b, c->stream);
+        };
+        auto kxp = [&](int b) {
+          mg::dslash_mrhs<T>(g, mg::EPI_XPAY, 0, nrhs, half_reals, out.as<T>(), in.as<T>(), c->gauge<T>(), nullptr,
+                             x.as<T>(), -1.0, 0xff, b, c->stream);
+        };
+        blk_ch = F.block_for("dslash_ch", nrhs, kch);
+        blk_xp = F.block_for("dslash_xpay", nrhs, kxp);
+      }
       auto launch = [&]() {
         switch (kernel) {
           case MG_KERNEL_DSLASH_CLOVER:
-            mg::dslash<T>(g, mg::EPI_CH, 1, out.as<T>(), in.as<T>(), c->gauge<T>(), c->Ainv<T>(1), nullptr, 0.0, 0xff,
-                          c->stream);
+            if (nrhs == 1)
+              mg::dslash<T>(g, mg::EPI_CH, 1, out.as<T>(), in.as<T>(), c->gauge<T>(), c->Ainv<T>(1), nullptr, 0.0,
+                            0xff, c->stream);
+            else
+              mg::dslash_mrhs<T>(g, mg::EPI_CH, 1, nrhs, half_reals, out.as<T>(), in.as<T>(), c->gauge<T>(),
+                                 c->Ainv<T>(1), nullptr, 0.0, 0xff, blk_ch, c->stream);
             break;
           case MG_KERNEL_DSLASH_XPAY:
-            mg::dslash<T>(g, mg::EPI_XPAY, 0, out.as<T>(), in.as<T>(), c->gauge<T>(), nullptr, x.as<T>(), -1.0, 0xff,
-                          c->stream);
+            if (nrhs == 1)
+              mg::dslash<T>(g, mg::EPI_XPAY, 0, out.as<T>(), in.as<T>(), c->gauge<T>(), nullptr, x.as<T>(), -1.0,
+                            0xff, c->stream);
+            else
+              mg::dslash_mrhs<T>(g, mg::EPI_XPAY, 0, nrhs, half_reals, out.as<T>(), in.as<T>(), c->gauge<T>(),
+                                 nullptr, x.as<T>(), -1.0, 0xff, blk_xp, c->stream);
             break;
-          default: F.Dr(out.as<T>(), in.as<T>()); break;
+          default:
+            if (nrhs == 1)
+              F.Dr(out.as<T>(), in.as<T>());
+            else
+              F.Dr_multi(out.as<T>(), in.as<T>(), nrhs, half_reals);
+            break;
         }
       };
       for (int w = 0; w < warmup; w++) launch();
@@ -508,7 +565,14 @@ int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int iters, 
       float t = 0;
       MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
       ms = t / iters;
-      const double reals = kernel == MG_KERNEL_DSLASH_CLOVER ? 264.0 : (kernel == MG_KERNEL_DSLASH_XPAY ? 216.0 : 600.0);
+      // reals per output site: links and clover once, spinors once per rhs
+      double reals;
+      if (kernel == MG_KERNEL_DSLASH_CLOVER)
+        reals = 144.0 + 72.0 + 48.0 * nrhs;
+      else if (kernel == MG_KERNEL_DSLASH_XPAY)
+        reals = 144.0 + 72.0 * nrhs;
+      else
+        reals = 432.0 + 168.0 * nrhs;
       bytes = reals * sizeof(T) * (double)c->Vh;
     };
     if (f32)

@@ -112,6 +112,10 @@ struct CoarseGCRBuffers {
   int grid = 0;            // co-resident blocks of the cooperative launch
   int nsplit = 1;          // work items per site in the stencil phases (row split)
   DBuf r, y, br, tA, tB, W, Z, partials, scal;
+  // batched solve (allocated on first use, for up to bcap problems)
+  int bcap = 0, bm = 0, bgrid = 0;
+  size_t bnscal = 0;
+  DBuf bx_r, bx_y, bx_br, bx_tB, bx_W, bx_Z, bx_part, bx_scal;
   void init(const LevelGeom& G, int nc, int m);
 };
 // x = D_hat^{-1} b to ||b - D_hat x|| <= tol_rel ||b|| (or maxit iterations) by
@@ -119,6 +123,14 @@ struct CoarseGCRBuffers {
 // an odd extent); adds the iterations run to *d_iters (device)
 void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuffers& B, int m, int maxit,
                       double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s);
+
+// The same solve for nb right-hand sides b[p] (full vectors, [nb][nsites nc])
+// in one cooperative launch, each to its own tolerance; x[p] likewise.
+// nb <= coarse_gcr_batch_max().  Adds the iterations of all problems to *d_iters.
+int coarse_gcr_batch_max();
+void coarse_gcr_solve_batch(const LevelGeom& G, const CoarseOp& C, CoarseGCRBuffers& B, int m, int maxit,
+                            double tol_rel, int nb, const float* b, float* x, long long* d_iters, int* flags,
+                            cudaStream_t s);
 
 // ---- setup kernels
 // Philox start vector on a coarse level (AoS)

@@ -94,6 +94,13 @@ void clover_apply(const Geom& g, T* out, const T* in, const T* clov, cudaStream_
 template <typename T>
 void dslash(const Geom& g, Epilogue epi, int parity, T* out, const T* in, const T* gauge, const T* clov,
             const T* x, double a, int dirmask, cudaStream_t s);
+// nrhs right-hand sides at `stride` elements of T apart (out, in and x alike),
+// one launch; `block` = threads per CTA (64, 128 or 256)
+template <typename T>
+void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
+                 const T* gauge, const T* clov, const T* x, double a, int dirmask, int block, cudaStream_t s);
+template <typename T>
+void clover_apply_mrhs(const Geom& g, int nrhs, size_t stride, T* out, const T* in, const T* clov, cudaStream_t s);
 // the 8 directional terms H_d in (without summation), written to out[d]
 // (whole-lattice FP32 vectors, [even half][odd half] each)
 void hop_directions(const Geom& g, float* const out[8], const float* in_even, const float* in_odd,
@@ -147,6 +154,20 @@ void blas_normalize(T* x, const double* d_norm2, size_t n, cudaStream_t s);
 template <typename T>
 void blas_dot2(const T* w, const T* r, size_t n, double* d_out, Workspace& ws, cudaStream_t s);
 
+// --------------------------------------------------------------------------- autotuner (tune.cu)
+struct TuneKey {
+  const char* kernel;
+  int dims[4];
+  int nrhs;
+  int prec;   // 0 FP64, 1 FP32
+};
+// CTA size for `k`: looked up, or chosen by timing `launch(block)` for every
+// candidate on stream `s` (the launches must be idempotent: no output aliases
+// an input).  Thread-safe.
+int tuned_block(const TuneKey& k, const std::vector<int>& candidates, const std::function<void(int)>& launch,
+                cudaStream_t s);
+int tune_entries();
+
 // --------------------------------------------------------------------------- context
 struct Level;     // multigrid level (coarse.cu / multigrid.cu)
 struct Hierarchy;
@@ -176,6 +197,7 @@ struct Ctx {
   DBuf stage_in, stage_out;              // complex128 whole-lattice staging
   long long dslash_launches = 0;
   std::shared_ptr<void> solve_work;      // solve buffers (solver.cu), kept between calls
+  std::shared_ptr<void> block_work;      // block-solve buffers (block.cu), kept between calls
 
   const double* A64(int p) const { return clov64.as<double>() + (size_t)p * 72 * Vh; }
   const double* Ainv64(int p) const { return clovinv64.as<double>() + (size_t)p * 72 * Vh; }
@@ -227,6 +249,21 @@ struct FineOps {
   void Dp(T* oe, T* oo, const T* ie, const T* io);
   void H(T* oe, T* oo, const T* ie, const T* io);
   void M(T* oe, T* oo, const T* ie, const T* io, bool inverse);
+  // nrhs vectors as packed half vectors: rhs r of a half at base + r * stride
+  // with stride = 24 Vh elements of T (the even halves of all rhs, and
+  // separately the odd halves, are contiguous).
+  // Multi-RHS kernels: links and clover are read once per site for all rhs.
+  DBuf m1, m2;
+  size_t mcap = 0;
+  void reserve_multi(int nrhs);
+  int block_for(const char* kernel, int nrhs, const std::function<void(int)>& launch);
+  void Dr_multi(T* out_e, const T* in_e, int nrhs, size_t stride);
+  void br_multi(T* out_e, const T* b_e, const T* b_o, int nrhs, size_t stride);
+  void reconstruct_multi(T* x_e, T* x_o, const T* y_e, const T* b_o, int nrhs, size_t stride);
+  void D_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride);
+  void Dp_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride);
+  void H_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride);
+  void M_multi(T* oe, T* oo, const T* ie, const T* io, bool inverse, int nrhs, size_t stride);
 };
 
 // --------------------------------------------------------------------------- GCR
@@ -267,6 +304,9 @@ void mr_smooth(Ctx* c, const std::function<void(T*, const T*)>& A, T* e, T* r, T
 
 // --------------------------------------------------------------------------- solve drivers (solver.cu)
 int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int mode, mg_solve_info* info);
+// nb right-hand sides (ABI vectors, consecutive) solved together by
+// lock-step multigrid-preconditioned FGCR (block.cu)
+int solve_fine_block(Ctx* c, double* psi_abi, const double* eta_abi, int nb, double tol, mg_solve_info* info);
 
 // --------------------------------------------------------------------------- gauge derivative (force.cu)
 // gamma_5 in place on ABI fine vectors (`sites` sites of 12 complex128)
@@ -280,6 +320,10 @@ void mg_build(Ctx* c, mg_setup_info* info);
 void mg_destroy_hierarchy(Ctx* c);
 // preconditioner of the fine D_r in FP32 (z_e, r_e half vectors)
 void mg_precondition(Ctx* c, float* z_e, const float* r_e);
+// the same for nb right-hand sides (packed half vectors, stride 24 Vh floats)
+void mg_precondition_batch(Ctx* c, float* z_e, const float* r_e, int nb);
+// MG_OP_CYCLE of level 0 for nb ABI vectors through mg_precondition_batch
+void mg_cycle_batch(Ctx* c, double* out_abi, const double* in_abi, int nb);
 void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in_abi);
 void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv);
 // dequantised coarse links of level >= 1 (ABI layouts, see mg_get_coarse_links)

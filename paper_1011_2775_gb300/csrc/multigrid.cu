@@ -89,7 +89,14 @@ struct LevelWork {
   DBuf res, w, e, z0;      // this level's half vectors for smoothing
 };
 
+// level-0 temporaries of the batched cycle (allocated for up to `cap` rhs)
+struct BatchWork {
+  int cap = 0;
+  DBuf rc, ec, res, w, e, z0, scr;
+};
+
 struct Hierarchy {
+  BatchWork bw;
   int L = 0;
   std::vector<LevelGeom> geo;
   std::vector<CoarseOp> cop;
@@ -495,6 +502,97 @@ void mg_build(Ctx* c, mg_setup_info* info) {
   c->sync();
   c->mg = std::move(H);
   if (info) info->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// The cycle of level 0 for nb right-hand sides at once (packed half vectors,
+// stride 24 Vh floats): multi-RHS D_r in the smoother, all coarsest-level
+// solves in one persistent launch per group of up to coarse_gcr_batch_max().
+// Each rhs gets exactly the arithmetic of mg_precondition.
+void mg_precondition_batch(Ctx* c, float* z, const float* r, int nb) {
+  if (!c->mg) raise(MG_ERR_STATE, "multigrid not set up");
+  Hierarchy& H = *c->mg;
+  const mg_params& p = c->params;
+  cudaStream_t s = c->stream;
+  const size_t n = half_n(H, 0), hs = 2 * n;
+  const size_t nfc = full_n(H, 1), cs = 2 * nfc;
+  const TransferOp& T = H.tr[0];
+  BatchWork& bw = H.bw;
+  if (bw.cap < nb) {
+    bw.rc.alloc(sizeof(float) * cs * nb);
+    bw.ec.alloc(sizeof(float) * cs * nb);
+    for (DBuf* d : {&bw.res, &bw.w, &bw.e, &bw.z0}) d->alloc(sizeof(float) * hs * nb);
+    bw.scr.alloc(sizeof(double) * 4 * nb);
+    bw.cap = nb;
+  }
+  float* rc = bw.rc.as<float>();
+  float* ec = bw.ec.as<float>();
+  float* res = bw.res.as<float>();
+  float* w = bw.w.as<float>();
+  float* e = bw.e.as<float>();
+  double* scr = bw.scr.as<double>();
+  auto Drm = [&](float* o, const float* i) { H.F32->Dr_multi(o, i, nb, hs); };
+  auto mr = [&](float* ev, float* rv, int nu) {   // ev = MR_nu(D_r, rv), rv consumed
+    blas_zero<float>(ev, n * nb, s);
+    for (int it = 0; it < nu; it++) {
+      Drm(w, rv);
+      for (int q = 0; q < nb; q++) {
+        blas_dot2<float>(w + q * hs, rv + q * hs, n, scr + 4 * q, c->ws, s);
+        blas_mr_update<float>(ev + q * hs, rv + q * hs, w + q * hs, scr + 4 * q, n, s);
+      }
+    }
+  };
+  const float* rin = r;
+  if (p.nu_pre > 0) {
+    blas_convert<float, float>(res, r, n * nb, s);
+    mr(z, res, p.nu_pre);
+    Drm(w, z);
+    blas_convert<float, float>(res, r, n * nb, s);
+    blas_axpby<float>(-1.0, w, 1.0, res, n * nb, s);
+    rin = res;
+  }
+  for (int q = 0; q < nb; q++) restrict_vec(T, rc + q * cs, rin + q * hs, true, s);
+  if (H.L == 2) {
+    const int restart = p.restart_coarse > 0 ? p.restart_coarse : 32;
+    const int gmax = coarse_gcr_batch_max();
+    for (int q0 = 0; q0 < nb; q0 += gmax) {
+      const int g = nb - q0 < gmax ? nb - q0 : gmax;
+      coarse_gcr_solve_batch(H.geo[1], H.cop[1], H.work[1].cg, restart, p.maxit_coarse, p.tol_coarse, g,
+                             rc + q0 * cs, ec + q0 * cs, H.d_iters.as<long long>() + 1, c->ws.flags.as<int>(), s);
+    }
+  } else {
+    for (int q = 0; q < nb; q++) coarse_solve(c, H, 1, ec + q * cs, rc + q * cs);
+  }
+  if (p.nu_pre > 0) {
+    float* z0 = bw.z0.as<float>();
+    for (int q = 0; q < nb; q++) prolong_vec(T, z0 + q * hs, ec + q * cs, true, s);
+    blas_axpby<float>(1.0, z0, 1.0, z, n * nb, s);
+  } else {
+    for (int q = 0; q < nb; q++) prolong_vec(T, z + q * hs, ec + q * cs, true, s);
+  }
+  if (p.nu_post > 0) {
+    Drm(w, z);
+    blas_convert<float, float>(res, r, n * nb, s);
+    blas_axpby<float>(-1.0, w, 1.0, res, n * nb, s);
+    mr(e, res, p.nu_post);
+    blas_axpby<float>(1.0, e, 1.0, z, n * nb, s);
+  }
+}
+
+void mg_cycle_batch(Ctx* c, double* out_abi, const double* in_abi, int nb) {
+  if (!c->mg) raise(MG_ERR_STATE, "multigrid not set up");
+  if (c->mg->L < 2) raise(MG_ERR_ARG, "no coarser level");
+  const size_t hs = 24 * c->Vh;
+  cudaStream_t s = c->stream;
+  DBuf ib(sizeof(float) * 2 * hs * nb), ob(sizeof(float) * 2 * hs * nb);
+  MG_CUDA(cudaMemsetAsync(ob.get(), 0, sizeof(float) * 2 * hs * nb, s));
+  float* ie = ib.as<float>();
+  float* io = ie + hs * nb;
+  float* oe = ob.as<float>();
+  float* oo = oe + hs * nb;   // stays zero: the cycle writes even sites only
+  for (int q = 0; q < nb; q++) pack_spinor(c->g, in_abi + (size_t)q * 24 * c->V, ie + q * hs, io + q * hs, true, s);
+  mg_precondition_batch(c, oe, ie, nb);
+  for (int q = 0; q < nb; q++) unpack_spinor(c->g, oe + q * hs, oo + q * hs, true, out_abi + (size_t)q * 24 * c->V, s);
+  c->sync();
 }
 
 void mg_precondition(Ctx* c, float* z_e, const float* r_e) {

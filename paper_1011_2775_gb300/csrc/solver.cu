@@ -159,6 +159,100 @@ void FineOps<T>::M(T* oe, T* oo, const T* ie, const T* io, bool inverse) {
   clover_apply<T>(g, oo, io, inverse ? c->Ainv<T>(1) : c->A<T>(1), c->stream);
 }
 
+// ---- multi-RHS forms
+template <typename T>
+void FineOps<T>::reserve_multi(int nrhs) {
+  const size_t need = sizeof(T) * 24 * c->Vh * (size_t)nrhs;
+  if (mcap >= need) return;
+  m1.alloc(need);
+  m2.alloc(need);
+  mcap = need;
+}
+
+template <typename T>
+int FineOps<T>::block_for(const char* kernel, int nrhs, const std::function<void(int)>& launch) {
+  TuneKey k{kernel, {c->dims[0], c->dims[1], c->dims[2], c->dims[3]}, nrhs, std::is_same<T, float>::value ? 1 : 0};
+  return tuned_block(k, {64, 128, 256}, launch, c->stream);
+}
+
+template <typename T>
+void FineOps<T>::Dr_multi(T* out_e, const T* in_e, int nrhs, size_t stride) {
+  const Geom& g = c->g;
+  cudaStream_t st = c->stream;
+  reserve_multi(nrhs);
+  const size_t ts = 24 * c->Vh;  // temporaries are packed at half-vector stride
+  if (stride != ts) raise(MG_ERR_ARG, "multi-RHS operators take packed half vectors");
+  T* s = m1.as<T>();
+  T* t = m2.as<T>();
+  clover_apply_mrhs<T>(g, nrhs, stride, s, in_e, c->Ainv<T>(0), st);
+  auto k1 = [&](int b) {
+    dslash_mrhs<T>(g, EPI_CH, 1, nrhs, ts, t, s, c->gauge<T>(), c->Ainv<T>(1), nullptr, 0.0, 0xff, b, st);
+  };
+  auto k2 = [&](int b) {
+    dslash_mrhs<T>(g, EPI_XPAY, 0, nrhs, ts, out_e, t, c->gauge<T>(), nullptr, in_e, -1.0, 0xff, b, st);
+  };
+  k1(block_for("dslash_ch", nrhs, k1));
+  k2(block_for("dslash_xpay", nrhs, k2));
+  c->dslash_launches += 2;
+}
+
+template <typename T>
+void FineOps<T>::br_multi(T* out_e, const T* b_e, const T* b_o, int nrhs, size_t stride) {
+  const Geom& g = c->g;
+  if (stride != 24 * c->Vh) raise(MG_ERR_ARG, "multi-RHS operators take packed half vectors");
+  reserve_multi(nrhs);
+  T* t = m1.as<T>();
+  clover_apply_mrhs<T>(g, nrhs, stride, t, b_o, c->Ainv<T>(1), c->stream);
+  dslash_mrhs<T>(g, EPI_XPAY, 0, nrhs, stride, out_e, t, c->gauge<T>(), nullptr, b_e, -1.0, 0xff, 128, c->stream);
+  c->dslash_launches += 1;
+}
+
+template <typename T>
+void FineOps<T>::reconstruct_multi(T* x_e, T* x_o, const T* y_e, const T* b_o, int nrhs, size_t stride) {
+  const Geom& g = c->g;
+  clover_apply_mrhs<T>(g, nrhs, stride, x_e, y_e, c->Ainv<T>(0), c->stream);
+  dslash_mrhs<T>(g, EPI_C_XPAY, 1, nrhs, stride, x_o, x_e, c->gauge<T>(), c->Ainv<T>(1), b_o, -1.0, 0xff, 128,
+                 c->stream);
+  c->dslash_launches += 1;
+}
+
+template <typename T>
+void FineOps<T>::D_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride) {
+  const Geom& g = c->g;
+  dslash_mrhs<T>(g, EPI_CX_PAY, 0, nrhs, stride, oe, io, c->gauge<T>(), c->A<T>(0), ie, 1.0, 0xff, 128, c->stream);
+  dslash_mrhs<T>(g, EPI_CX_PAY, 1, nrhs, stride, oo, ie, c->gauge<T>(), c->A<T>(1), io, 1.0, 0xff, 128, c->stream);
+  c->dslash_launches += 2;
+}
+
+template <typename T>
+void FineOps<T>::Dp_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride) {
+  const Geom& g = c->g;
+  if (stride != 24 * c->Vh) raise(MG_ERR_ARG, "multi-RHS operators take packed half vectors");
+  reserve_multi(nrhs);
+  T* se = m1.as<T>();
+  T* so = m2.as<T>();
+  clover_apply_mrhs<T>(g, nrhs, stride, se, ie, c->Ainv<T>(0), c->stream);
+  clover_apply_mrhs<T>(g, nrhs, stride, so, io, c->Ainv<T>(1), c->stream);
+  dslash_mrhs<T>(g, EPI_XPAY, 0, nrhs, stride, oe, so, c->gauge<T>(), nullptr, ie, 1.0, 0xff, 128, c->stream);
+  dslash_mrhs<T>(g, EPI_XPAY, 1, nrhs, stride, oo, se, c->gauge<T>(), nullptr, io, 1.0, 0xff, 128, c->stream);
+  c->dslash_launches += 2;
+}
+
+template <typename T>
+void FineOps<T>::H_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride) {
+  const Geom& g = c->g;
+  dslash_mrhs<T>(g, EPI_H, 0, nrhs, stride, oe, io, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, 128, c->stream);
+  dslash_mrhs<T>(g, EPI_H, 1, nrhs, stride, oo, ie, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, 128, c->stream);
+  c->dslash_launches += 2;
+}
+
+template <typename T>
+void FineOps<T>::M_multi(T* oe, T* oo, const T* ie, const T* io, bool inverse, int nrhs, size_t stride) {
+  const Geom& g = c->g;
+  clover_apply_mrhs<T>(g, nrhs, stride, oe, ie, inverse ? c->Ainv<T>(0) : c->A<T>(0), c->stream);
+  clover_apply_mrhs<T>(g, nrhs, stride, oo, io, inverse ? c->Ainv<T>(1) : c->A<T>(1), c->stream);
+}
+
 template struct FineOps<float>;
 template struct FineOps<double>;
 

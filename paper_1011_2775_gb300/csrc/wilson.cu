@@ -379,12 +379,11 @@ template void clover_apply<float>(const Geom&, float*, const float*, const float
 template void clover_apply<double>(const Geom&, double*, const double*, const double*, cudaStream_t);
 
 // --------------------------------------------------------------------------- dslash
+// One output site: out = epilogue(-1/2 H in) (see Epilogue).
 template <typename T, int EPI>
-__global__ void __launch_bounds__(128) k_dslash(Geom g, int par, T* out, const T* __restrict__ in,
-                                                 const T* __restrict__ gauge, const T* __restrict__ clov,
-                                                 const T* __restrict__ x, T a, int dirmask) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= g.Vh) return;
+__device__ __forceinline__ void dslash_site(const Geom& g, int par, int i, T* out, const T* __restrict__ in,
+                                            const T* __restrict__ gauge, const T* __restrict__ clov,
+                                            const T* __restrict__ x, T a, int dirmask) {
   int c[4];
   cb_coords(g, i, par, c);
   cx<T> acc[12];
@@ -424,6 +423,31 @@ __global__ void __launch_bounds__(128) k_dslash(Geom g, int par, T* out, const T
   SpinorIO<T>::store(out, g.Vh, i, res);
 }
 
+template <typename T, int EPI>
+__global__ void __launch_bounds__(128) k_dslash(Geom g, int par, T* out, const T* __restrict__ in,
+                                                 const T* __restrict__ gauge, const T* __restrict__ clov,
+                                                 const T* __restrict__ x, T a, int dirmask) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= g.Vh) return;
+  dslash_site<T, EPI>(g, par, i, out, in, gauge, clov, x, a, dirmask);
+}
+
+// Multi-RHS form: nrhs vectors at a fixed stride (in elements of T).  The
+// right-hand side is the fastest-varying thread index, so the nrhs lanes of a
+// site read the same links and clover entries in one warp instruction: link
+// and clover bytes are paid once per site, spinor bytes once per (site, rhs).
+template <typename T, int EPI, int BS>
+__global__ void __launch_bounds__(BS) k_dslash_mrhs(Geom g, int par, int nrhs, size_t stride, T* out,
+                                                    const T* __restrict__ in, const T* __restrict__ gauge,
+                                                    const T* __restrict__ clov, const T* __restrict__ x, T a,
+                                                    int dirmask) {
+  const long long t = (long long)blockIdx.x * BS + threadIdx.x;
+  const int i = (int)(t / nrhs), r = (int)(t % nrhs);
+  if (i >= g.Vh) return;
+  const size_t o = (size_t)r * stride;
+  dslash_site<T, EPI>(g, par, i, out + o, in + o, gauge, clov, x ? x + o : nullptr, a, dirmask);
+}
+
 template <typename T>
 void dslash(const Geom& g, Epilogue epi, int parity, T* out, const T* in, const T* gauge, const T* clov, const T* x,
             double a, int dirmask, cudaStream_t s) {
@@ -442,6 +466,59 @@ template void dslash<float>(const Geom&, Epilogue, int, float*, const float*, co
                             const float*, double, int, cudaStream_t);
 template void dslash<double>(const Geom&, Epilogue, int, double*, const double*, const double*, const double*,
                              const double*, double, int, cudaStream_t);
+
+template <typename T, int BS>
+void dslash_mrhs_bs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
+                    const T* gauge, const T* clov, const T* x, double a, int dirmask, cudaStream_t s) {
+  const long long threads = (long long)g.Vh * nrhs;
+  const unsigned nb = (unsigned)((threads + BS - 1) / BS);
+  switch (epi) {
+    case EPI_H: k_dslash_mrhs<T, EPI_H, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CH: k_dslash_mrhs<T, EPI_CH, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_XPAY: k_dslash_mrhs<T, EPI_XPAY, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CX_PAY: k_dslash_mrhs<T, EPI_CX_PAY, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_C_XPAY: k_dslash_mrhs<T, EPI_C_XPAY, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+  }
+  MG_LAUNCH();
+}
+
+template <typename T>
+void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
+                 const T* gauge, const T* clov, const T* x, double a, int dirmask, int block, cudaStream_t s) {
+  if (nrhs < 1) raise(MG_ERR_ARG, "nrhs must be positive");
+  switch (block) {
+    case 64: dslash_mrhs_bs<T, 64>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s); break;
+    case 256: dslash_mrhs_bs<T, 256>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s); break;
+    default: dslash_mrhs_bs<T, 128>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s); break;
+  }
+}
+template void dslash_mrhs<float>(const Geom&, Epilogue, int, int, size_t, float*, const float*, const float*,
+                                 const float*, const float*, double, int, int, cudaStream_t);
+template void dslash_mrhs<double>(const Geom&, Epilogue, int, int, size_t, double*, const double*, const double*,
+                                  const double*, const double*, double, int, int, cudaStream_t);
+
+// clover multiply of nrhs vectors (rhs fastest, as the multi-RHS dslash)
+template <typename T>
+__global__ void k_clover_apply_mrhs(Geom g, int nrhs, size_t stride, T* out, const T* __restrict__ in,
+                                    const T* __restrict__ clov) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (int)(t / nrhs), r = (int)(t % nrhs);
+  if (i >= g.Vh) return;
+  cx<T> x[12], y[12];
+  SpinorIO<T>::load(in + (size_t)r * stride, g.Vh, i, x);
+  clover_mul<T>(clov, g.Vh, i, x, y);
+  SpinorIO<T>::store(out + (size_t)r * stride, g.Vh, i, y);
+}
+
+template <typename T>
+void clover_apply_mrhs(const Geom& g, int nrhs, size_t stride, T* out, const T* in, const T* clov, cudaStream_t s) {
+  const int bs = 128;
+  const long long threads = (long long)g.Vh * nrhs;
+  k_clover_apply_mrhs<T><<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(g, nrhs, stride, out, in, clov);
+  MG_LAUNCH();
+}
+template void clover_apply_mrhs<float>(const Geom&, int, size_t, float*, const float*, const float*, cudaStream_t);
+template void clover_apply_mrhs<double>(const Geom&, int, size_t, double*, const double*, const double*, cudaStream_t);
 
 // --------------------------------------------------------------------------- directional terms
 struct DirOut {

@@ -116,11 +116,11 @@ class Solver:
         B.mg_force(self.ctx, out, lam, psi, kind)
         return out
 
-    def apply(self, op: int, x, level: int = 0, prec: int = B.MG_FP64, out_shape=None):
+    def apply(self, op: int, x, level: int = 0, prec: int = B.MG_FP64, out_shape=None, nrhs: int = 1):
+        """Apply operator ``op`` of ``level`` to ``nrhs`` consecutive vectors in ``x``."""
         if out_shape is None:
             out = x.new_zeros(x.shape) if not isinstance(x, np.ndarray) else np.zeros_like(x)
         else:
             out = np.zeros(out_shape, dtype=np.complex128) if isinstance(x, np.ndarray) else x.new_zeros(out_shape)
-        nrhs = 1
         B.mg_apply(self.ctx, op, level, out, x, nrhs, prec)
         return out
