@@ -38,6 +38,10 @@ TOL = 1e-10
 HBM_DIMS = (32, 32, 32, 64)          # 1.1 GB per FP32 fused-dslash launch: far beyond the 129 MB L2
 L2_FLUSH_BYTES = 512 << 20
 CPU_SAMPLE_DR = 5                    # oracle D_r applications in one CPU sample
+BATCH_RHS = 12                       # right-hand sides of the batched solve
+MRHS = (4, 12)                       # right-hand sides of the multi-RHS D_r measurements
+PROFILE_MRHS = 4                     # --profile dslash_mrhs: right-hand sides per launch
+PROFILE_MRHS_DIMS = (32, 32, 32, 32) # ... on a lattice that keeps an ncu capture to a few GB
 # fine D_r applications of one MG-GCR solve of the 16^3x32 workload at m0=-0.35
 # (the GPU arm's solve.fine_dr_applications on GB300: 42 outer iterations);
 # projects the reference arm's sample to one solve
@@ -193,18 +197,42 @@ def profile_main(args):
         print(json.dumps({"profile": "solve", "steps": args.steps, "kernel_launches": info.kernel_launches,
                           "outer_iterations": info.outer_iterations, "true_residual": info.true_residual}))
         S.close()
-    else:
-        reps = [h // d for h, d in zip(HBM_DIMS, DIMS)]
-        H = Solver(HBM_DIMS)
-        H.load_gauge(np.tile(U, (reps[3], reps[2], reps[1], reps[0], 1, 1, 1)))
-        H.set_clover(CSW, args.mass)
-        B.mg_benchmark_kernel(H.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, warmup=args.warmup, iters=1)
+    elif args.profile == "block":
+        etas = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED + 10, nrhs=BATCH_RHS)).cuda()
+        psis = torch.zeros_like(etas)
+        S = Solver(DIMS)
+        S.load_gauge(U)
+        S.set_clover(CSW, args.mass)
+        S.set_params(seed=NULLVEC_SEED, maxit_fine=2000, rhs_block=BATCH_RHS, **MG)
+        S.setup()
+        for _ in range(args.warmup):
+            S.solve(etas, TOL, B.MG_MODE_MG, out=psis)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
-        ms, by = B.mg_benchmark_kernel(H.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, warmup=0, iters=args.steps)
+        for _ in range(args.steps):
+            _, info = S.solve(etas, TOL, B.MG_MODE_MG, out=psis)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
-        print(json.dumps({"profile": "dslash", "launches": args.steps, "bytes_per_launch": by}))
+        print(json.dumps({"profile": "block", "nrhs": BATCH_RHS, "steps": args.steps,
+                          "kernel_launches": info.kernel_launches, "outer_iterations": info.outer_iterations,
+                          "true_residual": info.true_residual}))
+        S.close()
+    else:
+        nrhs = 1 if args.profile == "dslash" else PROFILE_MRHS
+        dims = HBM_DIMS if args.profile == "dslash" else PROFILE_MRHS_DIMS
+        reps = [h // d for h, d in zip(dims, DIMS)]
+        H = Solver(dims)
+        H.load_gauge(np.tile(U, (reps[3], reps[2], reps[1], reps[0], 1, 1, 1)))
+        H.set_clover(CSW, args.mass)
+        B.mg_benchmark_kernel_nrhs(H.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, nrhs, warmup=args.warmup, iters=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        ms, by = B.mg_benchmark_kernel_nrhs(H.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, nrhs, warmup=0,
+                                            iters=args.steps)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile": args.profile, "nrhs": nrhs, "launches": args.steps, "bytes_per_launch": by,
+                          "ms_per_launch": ms}))
         H.close()
 
 
@@ -276,6 +304,10 @@ def run_gpu(args, dist: Dist) -> dict:
     e2e_ms = dist.max(statistics.median(e2e_times))
     nbytes = eta.nbytes
 
+    extra = {}
+    if not args.no_extra:
+        extra = run_extras(args, S, U, eta, flush, stream, dev)
+
     # plain FP64 even-odd GCR on the same system (bounded)
     eo = None
     if not args.no_eo:
@@ -306,9 +338,90 @@ def run_gpu(args, dist: Dist) -> dict:
                              ("dslash_clover_fp64", B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP64)]:
         ms_k, by = B.mg_benchmark_kernel(H.ctx, code, prec, warmup=10, iters=50)
         kern[name] = {"ms": ms_k, "bytes": by, "gbs": by / ms_k / 1e6}
+    if not args.no_extra:
+        # multi-RHS D_r (links and clover read once per site for all rhs)
+        for nrhs in MRHS:
+            ms_k, by = B.mg_benchmark_kernel_nrhs(H.ctx, B.MG_KERNEL_DR, B.MG_FP32, nrhs, warmup=3, iters=10)
+            kern[f"dr_fp32_nrhs{nrhs}"] = {"ms": ms_k, "bytes": by, "gbs": by / ms_k / 1e6, "ms_per_rhs": ms_k / nrhs}
     H.close()
     return dict(ms=ms, times=times, info=last, setup_ms=setup_ms, sinfo=sinfo, e2e_ms=e2e_ms, nbytes=nbytes,
-                eo=eo, kern=kern, clocks=clk, launches=launches // max(1, args.steps))
+                eo=eo, kern=kern, clocks=clk, launches=launches // max(1, args.steps), extra=extra)
+
+
+def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
+    """The batching, storage and differentiation rows on the same workload:
+    a block solve of BATCH_RHS right-hand sides against the same sources solved
+    one at a time, an FP16-storage solve, and a differentiated solve (forward
+    solve, adjoint solve, link derivative)."""
+    import torch
+    from paper_1011_2775_gb300 import binding as B
+    from paper_1011_2775_gb300 import inputs as I
+    from paper_1011_2775_gb300.autograd import dirac_solve
+    from paper_1011_2775_gb300.solver import Solver
+
+    out = {}
+
+    def timed(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    # ---- batched right-hand sides (12 Gaussian sources, the point-source count of one propagator)
+    etas = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED + 10, nrhs=BATCH_RHS)).to(f"cuda:{dev}")
+    psis = torch.zeros_like(etas)
+    S.set_params(rhs_block=BATCH_RHS)
+    S.solve(etas, TOL, B.MG_MODE_MG, out=psis)   # warm-up (allocations, autotuning)
+    t_blk, (_, bi) = timed(lambda: S.solve(etas, TOL, B.MG_MODE_MG, out=psis))
+    S.set_params(rhs_block=1)
+    t_seq, (_, si) = timed(lambda: S.solve(etas, TOL, B.MG_MODE_MG, out=psis))
+    S.set_params(rhs_block=16)
+    out["batched"] = {"nrhs": BATCH_RHS, "block_ms": t_blk, "sequential_ms": t_seq,
+                      "block_ms_per_rhs": t_blk / BATCH_RHS, "sequential_ms_per_rhs": t_seq / BATCH_RHS,
+                      "speedup": t_seq / t_blk, "block_outer_iterations": bi.outer_iterations,
+                      "sequential_outer_iterations": si.outer_iterations,
+                      "true_residual_max": max(bi.true_residual, si.true_residual)}
+    del etas, psis
+
+    # ---- differentiated solve: L = Re<chi, D^{-1} eta>, grads w.r.t. eta and U
+    eta_d = torch.from_numpy(eta).to(f"cuda:{dev}").requires_grad_(True)
+    U_d = torch.from_numpy(U).to(f"cuda:{dev}").requires_grad_(True)
+    chi_d = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED + 20)).to(f"cuda:{dev}")
+    S.load_gauge(U_d)                              # the same field; the setup must be redone after a load
+    S.set_clover(CSW, args.mass)
+    S.setup()
+    t_fwd, psi = timed(lambda: dirac_solve(S, eta_d, U_d, tol=TOL))
+    loss = torch.sum(torch.conj(chi_d) * psi).real
+    t_bwd, _ = timed(lambda: loss.backward())
+    lam = eta_d.grad.detach()
+    t_force, _ = timed(lambda: S.force(lam, psi.detach(), kind=B.MG_FORCE_SU3))
+    out["gradient"] = {"forward_ms": t_fwd, "backward_ms": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+                       "force_ms": t_force, "what": "backward = adjoint MG solve through gamma_5 D gamma_5 + "
+                                                   "FP64 hop and clover link derivative"}
+    del eta_d, U_d, chi_d, psi, lam, loss
+
+    # ---- FP16 storage of P and the coarse links
+    Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
+    Q.load_gauge(U)
+    Q.set_clover(CSW, args.mass)
+    Q.set_params(seed=NULLVEC_SEED, maxit_fine=2000, storage=B.MG_STORE_FP16, **MG)
+    Q.setup()
+    e_d = torch.from_numpy(eta).to(f"cuda:{dev}")
+    p_d = torch.zeros_like(e_d)
+    Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
+    ts = []
+    for _ in range(3):
+        t, (_, qi) = timed(lambda: Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
+        ts.append(t)
+    out["fp16_storage"] = {"ms": statistics.median(ts), "outer_iterations": qi.outer_iterations,
+                           "coarse_iterations": qi.coarse_iterations[1], "true_residual": qi.true_residual}
+    Q.close()
+    return out
 
 
 def main():
@@ -321,9 +434,12 @@ def main():
     ap.add_argument("--no-eo", action="store_true", help="skip the plain EO-GCR comparison")
     ap.add_argument("--eo-maxit", type=int, default=20000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--profile", choices=["solve", "dslash"],
-                    help="for ncu --profile-from-start off: bracket `steps` solves (after setup and warm-up), or "
-                         "`steps` launches of the HBM-size FP32 fused dslash, with cudaProfilerStart/Stop; "
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched, FP16-storage, gradient and multi-RHS D_r measurements")
+    ap.add_argument("--profile", choices=["solve", "block", "dslash", "dslash_mrhs"],
+                    help="for ncu --profile-from-start off: bracket `steps` solves (after setup and warm-up), "
+                         "`steps` block solves of the batched right-hand sides, or `steps` launches of the FP32 fused "
+                         "dslash (HBM-size lattice; dslash_mrhs: its multi-RHS form), with cudaProfilerStart/Stop; "
                          "nothing else is run")
     ap.add_argument("--cpu-sample", nargs=2, help=argparse.SUPPRESS)
     args = ap.parse_args()
@@ -383,7 +499,7 @@ def main():
                       "true_residual": info.true_residual, "fine_dr_applications": dr_per_solve,
                       "step_ms": r["times"]},
             "setup_ms": r["setup_ms"], "setup_passes": r["sinfo"].passes[0],
-            "eo_gcr": r["eo"], "kernels": r["kern"]}
+            "eo_gcr": r["eo"], "kernels": r["kern"], **r["extra"]}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
         s = cpu_sample(args.mass, CPU_SAMPLE_DR)
         line["cpu_baseline"] = {"value": s["ms_per_dr"] * dr_per_solve, "unit": "ms", "cores": 1, "kind": "oracle",

@@ -185,7 +185,10 @@ MG_API int mg_load_gauge(void* ctx, const void* U, int where);
  * 1e-12 of its largest entry). */
 MG_API int mg_set_clover(void* ctx, double csw, double m0);
 
-/* Set multigrid parameters (copied).  Invalidates the setup.  Errors:
+/* Set multigrid parameters (copied).  Invalidates the setup (and any
+ * injected null vectors) when a field the setup depends on changes: levels,
+ * block, nv, setup_iters, setup_inner, setup_rq_tol, restart_coarse, storage,
+ * coarse_op or seed; the other fields take effect at the next solve.  Errors:
  * MG_ERR_ARG, MG_ERR_DIMS (a block does not divide its lattice, or a level
  * below the coarsest has an odd extent), MG_ERR_NV. */
 MG_API int mg_set_params(void* ctx, const mg_params* p);

@@ -300,11 +300,27 @@ int mg_set_params(void* ctx, const mg_params* p) {
         for (int m = 0; m < 4; m++)
           if (d[m] % 2) mg::raise(MG_ERR_DIMS, "a level below the coarsest has an odd extent");
     }
+    // the setup (hierarchy, injected vectors) depends on these fields only;
+    // smoothing, tolerances, caps, restart_fine and rhs_block take effect at
+    // the next solve without a new setup
+    const mg_params& o = c->params;
+    bool setup_changed = !c->have_params || o.levels != p->levels || o.setup_iters != p->setup_iters ||
+                         o.setup_inner != p->setup_inner || o.setup_rq_tol != p->setup_rq_tol ||
+                         o.restart_coarse != p->restart_coarse || o.storage != p->storage ||
+                         o.coarse_op != p->coarse_op || o.seed != p->seed;
+    for (int l = 0; l + 1 < p->levels && !setup_changed; l++) {
+      if (o.nv[l] != p->nv[l]) setup_changed = true;
+      for (int m = 0; m < 4; m++)
+        if (o.block[l][m] != p->block[l][m]) setup_changed = true;
+    }
     c->params = *p;
     c->have_params = true;
-    c->mg.reset();
+    if (setup_changed) {
+      c->mg.reset();
+      c->injected.assign(MG_MAX_LEVELS, std::vector<double>());
+    }
     c->solve_work.reset();
-    c->injected.assign(MG_MAX_LEVELS, std::vector<double>());
+    c->block_work.reset();
     return MG_OK;
   });
 }
@@ -518,7 +534,7 @@ int mg_benchmark_kernel_nrhs(void* ctx, int kernel, int prec, int nrhs, int warm
       }
       mg::FineOps<T> F(c);
       const mg::Geom& g = c->g;
-      int blk_ch = 128, blk_xp = 128;
+      int blk_ch = 0, blk_xp = 0;
       if (nrhs > 1) {   // the autotuned CTA sizes the solver would use
         auto kch = [&](int b) {
           mg::dslash_mrhs<T>(g, mg::EPI_CH, 1, nrhs, half_reals, out.as<T>(), in.as<T>(), c->gauge<T>(), c->Ainv<T>(1),

@@ -113,7 +113,7 @@ struct CoarseGCRBuffers {
   int nsplit = 1;          // work items per site in the stencil phases (row split)
   DBuf r, y, br, tA, tB, W, Z, partials, scal;
   // batched solve (allocated on first use, for up to bcap problems)
-  int bcap = 0, bm = 0, bgrid = 0;
+  int bcap = 0, bm = 0, bgrid = 0, bnb = 0, bGp = 0;
   size_t bnscal = 0;
   DBuf bx_r, bx_y, bx_br, bx_tB, bx_W, bx_Z, bx_part, bx_scal;
   void init(const LevelGeom& G, int nc, int m);

@@ -112,6 +112,51 @@ __device__ __forceinline__ void warp_gemv_rows(const void* __restrict__ M, int r
   }
 }
 
+// Multi-vector form for RB consecutive rows i0 .. i0+RB-1 (rows >= nrows are
+// skipped): res[r][p] = sum_k M[i0+r][k] * v_p[k] for np <= PB vectors
+// v_p = v + p * vstride (shared memory, vstride complex, even).  Each link
+// pair is loaded once and applied to all np vectors; callers loop over row
+// blocks so that the accumulators stay at RB * PB complex numbers.
+template <int ST, int RB, int PB>
+__device__ __forceinline__ void warp_gemv_multi(const void* __restrict__ M, int i0, int nrows, int K,
+                                                const float2* v, int vstride, int np, int lane,
+                                                float2 res[RB][PB]) {
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  const int K4 = K >> 1, vs4 = vstride >> 1;
+  float re[RB][PB], im[RB][PB];
+#pragma unroll
+  for (int r = 0; r < RB; r++)
+#pragma unroll
+    for (int p = 0; p < PB; p++) re[r][p] = im[r][p] = 0.f;
+  for (int q = lane; q < K4; q += 32) {
+    float4 a[RB];
+#pragma unroll
+    for (int r = 0; r < RB; r++)
+      a[r] = (i0 + r < nrows) ? LinkPair<ST>::decode(LinkPair<ST>::load(M, (size_t)(i0 + r) * K4 + q))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < PB; p++) {
+      if (p >= np) break;
+      const float4 x = v4[p * vs4 + q];
+#pragma unroll
+      for (int r = 0; r < RB; r++) {
+        re[r][p] = fmaf(a[r].x, x.x, re[r][p]);
+        re[r][p] = fmaf(-a[r].y, x.y, re[r][p]);
+        re[r][p] = fmaf(a[r].z, x.z, re[r][p]);
+        re[r][p] = fmaf(-a[r].w, x.w, re[r][p]);
+        im[r][p] = fmaf(a[r].x, x.y, im[r][p]);
+        im[r][p] = fmaf(a[r].y, x.x, im[r][p]);
+        im[r][p] = fmaf(a[r].z, x.w, im[r][p]);
+        im[r][p] = fmaf(a[r].w, x.z, im[r][p]);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < RB; r++)
+#pragma unroll
+    for (int p = 0; p < PB; p++) res[r][p] = make_float2(gemv_wsum(re[r][p]), gemv_wsum(im[r][p]));
+}
+
 template <int ST = kStF32>
 __device__ __forceinline__ void warp_gemv(const void* __restrict__ M, int nrows, int K, const float2* v, int w,
                                           int rpw, int lane, float2 res[kGemvMaxRows]) {

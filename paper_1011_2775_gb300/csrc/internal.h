@@ -95,10 +95,13 @@ template <typename T>
 void dslash(const Geom& g, Epilogue epi, int parity, T* out, const T* in, const T* gauge, const T* clov,
             const T* x, double a, int dirmask, cudaStream_t s);
 // nrhs right-hand sides at `stride` elements of T apart (out, in and x alike),
-// one launch; `block` = threads per CTA (64, 128 or 256)
+// one launch; `config` = (right-hand sides per thread) * 1000 + CTA size, one
+// of dslash_mrhs_configs()
 template <typename T>
 void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
-                 const T* gauge, const T* clov, const T* x, double a, int dirmask, int block, cudaStream_t s);
+                 const T* gauge, const T* clov, const T* x, double a, int dirmask, int config, cudaStream_t s);
+std::vector<int> dslash_mrhs_configs(bool fp32);
+int dslash_mrhs_default(bool fp32);
 template <typename T>
 void clover_apply_mrhs(const Geom& g, int nrhs, size_t stride, T* out, const T* in, const T* clov, cudaStream_t s);
 // the 8 directional terms H_d in (without summation), written to out[d]

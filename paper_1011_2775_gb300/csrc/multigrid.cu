@@ -87,6 +87,8 @@ struct LevelWork {
   CoarseGCRBuffers cg;     // coarsest level: buffers of the persistent solver
   DBuf rc, ec;             // next level's rhs / solution (this level's cycle)
   DBuf res, w, e, z0;      // this level's half vectors for smoothing
+  int coarse_impl = -1;    // coarsest level: persistent solver chosen by the autotuner (-1: not yet)
+  DBuf tune_iters;         // iteration counter of the tuning runs
 };
 
 // level-0 temporaries of the batched cycle (allocated for up to `cap` rhs)
@@ -224,10 +226,26 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
   LevelWork& W = H.work[l];
   cudaStream_t s = c->stream;
   if (l + 1 == H.L) {
-    // coarsest level: one persistent kernel, no host round trip
+    // coarsest level: one persistent kernel, no host round trip.  Two
+    // implementations of the same GCR: the single-system kernel, and the
+    // batched kernel with one system (row-blocked GEMV: fewer registers, more
+    // co-resident CTAs).  The autotuner times both on the first solve of this
+    // lattice (the tuning runs do not count towards the iteration statistics).
     const int restart = p.restart_coarse > 0 ? p.restart_coarse : 32;
-    coarse_gcr_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, b, x,
-                     H.d_iters.as<long long>() + l, c->ws.flags.as<int>(), s);
+    long long* d_it = H.d_iters.as<long long>() + l;
+    auto run = [&](int which, long long* it) {
+      if (which == 1)
+        coarse_gcr_solve_batch(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, 1, b, x, it,
+                               c->ws.flags.as<int>(), s);
+      else
+        coarse_gcr_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, b, x, it, c->ws.flags.as<int>(), s);
+    };
+    if (W.coarse_impl < 0) {
+      if (!W.tune_iters.get()) W.tune_iters.alloc(sizeof(long long));
+      TuneKey key{"coarse_gcr", {G.L[0], G.L[1], G.L[2], G.L[3]}, H.cop[l].nc, H.cop[l].store};
+      W.coarse_impl = tuned_block(key, {0, 1}, [&](int which) { run(which, W.tune_iters.as<long long>()); }, s);
+    }
+    run(W.coarse_impl, d_it);
     return;
   }
   double* scr = c->ws.scalars.as<double>() + 32 + l;

@@ -172,7 +172,7 @@ void FineOps<T>::reserve_multi(int nrhs) {
 template <typename T>
 int FineOps<T>::block_for(const char* kernel, int nrhs, const std::function<void(int)>& launch) {
   TuneKey k{kernel, {c->dims[0], c->dims[1], c->dims[2], c->dims[3]}, nrhs, std::is_same<T, float>::value ? 1 : 0};
-  return tuned_block(k, {64, 128, 256}, launch, c->stream);
+  return tuned_block(k, dslash_mrhs_configs(std::is_same<T, float>::value), launch, c->stream);
 }
 
 template <typename T>
@@ -203,7 +203,7 @@ void FineOps<T>::br_multi(T* out_e, const T* b_e, const T* b_o, int nrhs, size_t
   reserve_multi(nrhs);
   T* t = m1.as<T>();
   clover_apply_mrhs<T>(g, nrhs, stride, t, b_o, c->Ainv<T>(1), c->stream);
-  dslash_mrhs<T>(g, EPI_XPAY, 0, nrhs, stride, out_e, t, c->gauge<T>(), nullptr, b_e, -1.0, 0xff, 128, c->stream);
+  dslash_mrhs<T>(g, EPI_XPAY, 0, nrhs, stride, out_e, t, c->gauge<T>(), nullptr, b_e, -1.0, 0xff, dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
   c->dslash_launches += 1;
 }
 
@@ -211,16 +211,16 @@ template <typename T>
 void FineOps<T>::reconstruct_multi(T* x_e, T* x_o, const T* y_e, const T* b_o, int nrhs, size_t stride) {
   const Geom& g = c->g;
   clover_apply_mrhs<T>(g, nrhs, stride, x_e, y_e, c->Ainv<T>(0), c->stream);
-  dslash_mrhs<T>(g, EPI_C_XPAY, 1, nrhs, stride, x_o, x_e, c->gauge<T>(), c->Ainv<T>(1), b_o, -1.0, 0xff, 128,
-                 c->stream);
+  dslash_mrhs<T>(g, EPI_C_XPAY, 1, nrhs, stride, x_o, x_e, c->gauge<T>(), c->Ainv<T>(1), b_o, -1.0, 0xff,
+                 dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
   c->dslash_launches += 1;
 }
 
 template <typename T>
 void FineOps<T>::D_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride) {
   const Geom& g = c->g;
-  dslash_mrhs<T>(g, EPI_CX_PAY, 0, nrhs, stride, oe, io, c->gauge<T>(), c->A<T>(0), ie, 1.0, 0xff, 128, c->stream);
-  dslash_mrhs<T>(g, EPI_CX_PAY, 1, nrhs, stride, oo, ie, c->gauge<T>(), c->A<T>(1), io, 1.0, 0xff, 128, c->stream);
+  dslash_mrhs<T>(g, EPI_CX_PAY, 0, nrhs, stride, oe, io, c->gauge<T>(), c->A<T>(0), ie, 1.0, 0xff, dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
+  dslash_mrhs<T>(g, EPI_CX_PAY, 1, nrhs, stride, oo, ie, c->gauge<T>(), c->A<T>(1), io, 1.0, 0xff, dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
   c->dslash_launches += 2;
 }
 
@@ -233,16 +233,16 @@ void FineOps<T>::Dp_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size
   T* so = m2.as<T>();
   clover_apply_mrhs<T>(g, nrhs, stride, se, ie, c->Ainv<T>(0), c->stream);
   clover_apply_mrhs<T>(g, nrhs, stride, so, io, c->Ainv<T>(1), c->stream);
-  dslash_mrhs<T>(g, EPI_XPAY, 0, nrhs, stride, oe, so, c->gauge<T>(), nullptr, ie, 1.0, 0xff, 128, c->stream);
-  dslash_mrhs<T>(g, EPI_XPAY, 1, nrhs, stride, oo, se, c->gauge<T>(), nullptr, io, 1.0, 0xff, 128, c->stream);
+  dslash_mrhs<T>(g, EPI_XPAY, 0, nrhs, stride, oe, so, c->gauge<T>(), nullptr, ie, 1.0, 0xff, dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
+  dslash_mrhs<T>(g, EPI_XPAY, 1, nrhs, stride, oo, se, c->gauge<T>(), nullptr, io, 1.0, 0xff, dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
   c->dslash_launches += 2;
 }
 
 template <typename T>
 void FineOps<T>::H_multi(T* oe, T* oo, const T* ie, const T* io, int nrhs, size_t stride) {
   const Geom& g = c->g;
-  dslash_mrhs<T>(g, EPI_H, 0, nrhs, stride, oe, io, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, 128, c->stream);
-  dslash_mrhs<T>(g, EPI_H, 1, nrhs, stride, oo, ie, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, 128, c->stream);
+  dslash_mrhs<T>(g, EPI_H, 0, nrhs, stride, oe, io, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
+  dslash_mrhs<T>(g, EPI_H, 1, nrhs, stride, oo, ie, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, dslash_mrhs_default(std::is_same<T, float>::value), c->stream);
   c->dslash_launches += 2;
 }
 

@@ -15,6 +15,8 @@
 // that a warp reads contiguous 512-byte spans.
 #include <cmath>
 #include <cstdio>
+#include <type_traits>
+#include <vector>
 
 #include "internal.h"
 #include "philox.cuh"
@@ -432,20 +434,68 @@ __global__ void __launch_bounds__(128) k_dslash(Geom g, int par, T* out, const T
   dslash_site<T, EPI>(g, par, i, out, in, gauge, clov, x, a, dirmask);
 }
 
-// Multi-RHS form: nrhs vectors at a fixed stride (in elements of T).  The
-// right-hand side is the fastest-varying thread index, so the nrhs lanes of a
-// site read the same links and clover entries in one warp instruction: link
-// and clover bytes are paid once per site, spinor bytes once per (site, rhs).
-template <typename T, int EPI, int BS>
+// Multi-RHS form: nrhs vectors at a fixed stride (in elements of T).  A
+// thread owns one site and NR right-hand sides (the block index selects the
+// site block and the group of NR, group fastest): every link is loaded once
+// into registers and applied to the NR
+// neighbour spinors, so link bytes are paid once per site and NR rhs while
+// the spinor loads stay coalesced over consecutive sites.
+template <typename T, int EPI, int NR, int BS>
 __global__ void __launch_bounds__(BS) k_dslash_mrhs(Geom g, int par, int nrhs, size_t stride, T* out,
                                                     const T* __restrict__ in, const T* __restrict__ gauge,
                                                     const T* __restrict__ clov, const T* __restrict__ x, T a,
                                                     int dirmask) {
-  const long long t = (long long)blockIdx.x * BS + threadIdx.x;
-  const int i = (int)(t / nrhs), r = (int)(t % nrhs);
+  // 1-D grid, rhs group fastest: CTAs that run together share the sites
+  // (and so the link and clover lines in L2) of consecutive rhs groups
+  const int ngroups = (nrhs + NR - 1) / NR;
+  const int i = (int)(blockIdx.x / ngroups) * BS + threadIdx.x;
   if (i >= g.Vh) return;
-  const size_t o = (size_t)r * stride;
-  dslash_site<T, EPI>(g, par, i, out + o, in + o, gauge, clov, x ? x + o : nullptr, a, dirmask);
+  const int r0 = (int)(blockIdx.x % ngroups) * NR;
+  const int nr = nrhs - r0 < NR ? nrhs - r0 : NR;
+  int c[4];
+  cb_coords(g, i, par, c);
+  cx<T> acc[NR][12];
+#pragma unroll
+  for (int r = 0; r < NR; r++)
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[r][k] = mkc<T>(0, 0);
+  hop_sum_nr<T, NR>(g, in + (size_t)r0 * stride, stride, nr, gauge, par, i, c, dirmask, acc);
+  const T half = (T)-0.5;
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    if (r >= nr) break;
+    const size_t o = (size_t)(r0 + r) * stride;
+    cx<T> res[12];
+    if (EPI == EPI_H) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = half * acc[r][k];
+    } else if (EPI == EPI_CH) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[r][k] = half * acc[r][k];
+      clover_mul<T>(clov, g.Vh, i, acc[r], res);
+    } else if (EPI == EPI_XPAY) {
+      cx<T> xv[12];
+      SpinorIO<T>::load(x + o, g.Vh, i, xv);
+      const T f = half * a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = xv[k] + f * acc[r][k];
+    } else if (EPI == EPI_CX_PAY) {
+      cx<T> xv[12];
+      SpinorIO<T>::load(x + o, g.Vh, i, xv);
+      clover_mul<T>(clov, g.Vh, i, xv, res);
+      const T f = half * a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = res[k] + f * acc[r][k];
+    } else {  // EPI_C_XPAY
+      cx<T> xv[12];
+      SpinorIO<T>::load(x + o, g.Vh, i, xv);
+      const T f = half * a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) xv[k] = xv[k] + f * acc[r][k];
+      clover_mul<T>(clov, g.Vh, i, xv, res);
+    }
+    SpinorIO<T>::store(out + o, g.Vh, i, res);
+  }
 }
 
 template <typename T>
@@ -467,29 +517,78 @@ template void dslash<float>(const Geom&, Epilogue, int, float*, const float*, co
 template void dslash<double>(const Geom&, Epilogue, int, double*, const double*, const double*, const double*,
                              const double*, double, int, cudaStream_t);
 
-template <typename T, int BS>
-void dslash_mrhs_bs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
-                    const T* gauge, const T* clov, const T* x, double a, int dirmask, cudaStream_t s) {
-  const long long threads = (long long)g.Vh * nrhs;
-  const unsigned nb = (unsigned)((threads + BS - 1) / BS);
+// Second mapping: one (site, rhs) per thread, the CTA is 32 consecutive sites
+// (threadIdx.x) x NY right-hand sides (threadIdx.y).  Each warp reads 32
+// consecutive sites of one rhs (coalesced spinors) with the register
+// footprint of the single-RHS kernel; the NY warps of a CTA read the same
+// link and clover lines, which the first one brings into L1.
+template <typename T, int EPI, int NY>
+__global__ void __launch_bounds__(32 * NY) k_dslash_mrhs_y(Geom g, int par, int nrhs, size_t stride, T* out,
+                                                            const T* __restrict__ in, const T* __restrict__ gauge,
+                                                            const T* __restrict__ clov, const T* __restrict__ x, T a,
+                                                            int dirmask) {
+  const int ngroups = (nrhs + NY - 1) / NY;   // rhs group fastest in the 1-D grid
+  const int i = (int)(blockIdx.x / ngroups) * 32 + threadIdx.x;
+  const int r = (int)(blockIdx.x % ngroups) * NY + threadIdx.y;
+  if (i >= g.Vh || r >= nrhs) return;
+  const size_t o = (size_t)r * stride;
+  dslash_site<T, EPI>(g, par, i, out + o, in + o, gauge, clov, x ? x + o : nullptr, a, dirmask);
+}
+
+template <typename T, int NY>
+void dslash_mrhs_y(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
+                   const T* gauge, const T* clov, const T* x, double a, int dirmask, cudaStream_t s) {
+  const dim3 grid((unsigned)(((g.Vh + 31) / 32) * ((nrhs + NY - 1) / NY))), block(32, NY);
   switch (epi) {
-    case EPI_H: k_dslash_mrhs<T, EPI_H, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_CH: k_dslash_mrhs<T, EPI_CH, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_XPAY: k_dslash_mrhs<T, EPI_XPAY, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_CX_PAY: k_dslash_mrhs<T, EPI_CX_PAY, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_C_XPAY: k_dslash_mrhs<T, EPI_C_XPAY, BS><<<nb, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_H: k_dslash_mrhs_y<T, EPI_H, NY><<<grid, block, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CH: k_dslash_mrhs_y<T, EPI_CH, NY><<<grid, block, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_XPAY: k_dslash_mrhs_y<T, EPI_XPAY, NY><<<grid, block, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CX_PAY: k_dslash_mrhs_y<T, EPI_CX_PAY, NY><<<grid, block, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_C_XPAY: k_dslash_mrhs_y<T, EPI_C_XPAY, NY><<<grid, block, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
   }
   MG_LAUNCH();
 }
 
+template <typename T, int NR, int BS>
+void dslash_mrhs_cfg(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
+                     const T* gauge, const T* clov, const T* x, double a, int dirmask, cudaStream_t s) {
+  const dim3 grid((unsigned)(((g.Vh + BS - 1) / BS) * ((nrhs + NR - 1) / NR)));
+  switch (epi) {
+    case EPI_H: k_dslash_mrhs<T, EPI_H, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CH: k_dslash_mrhs<T, EPI_CH, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_XPAY: k_dslash_mrhs<T, EPI_XPAY, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CX_PAY: k_dslash_mrhs<T, EPI_CX_PAY, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_C_XPAY: k_dslash_mrhs<T, EPI_C_XPAY, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+  }
+  MG_LAUNCH();
+}
+
+// config = NR * 1000 + CTA size (NR right-hand sides per thread; FP32: NR in
+// {2, 4}, FP64: NR in {1, 2}), or 100000 + NY (rhs in threadIdx.y, NY in {4, 8})
 template <typename T>
 void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
-                 const T* gauge, const T* clov, const T* x, double a, int dirmask, int block, cudaStream_t s) {
+                 const T* gauge, const T* clov, const T* x, double a, int dirmask, int config, cudaStream_t s) {
   if (nrhs < 1) raise(MG_ERR_ARG, "nrhs must be positive");
-  switch (block) {
-    case 64: dslash_mrhs_bs<T, 64>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s); break;
-    case 256: dslash_mrhs_bs<T, 256>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s); break;
-    default: dslash_mrhs_bs<T, 128>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s); break;
+  if (config >= 100000) {
+    if (config % 100 == 8)
+      dslash_mrhs_y<T, 8>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
+    else
+      dslash_mrhs_y<T, 4>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
+    return;
+  }
+  constexpr bool f32 = std::is_same<T, float>::value;
+  constexpr int NA = f32 ? 2 : 1, NB = f32 ? 4 : 2;
+  const int nr = config / 1000, bs = config % 1000;
+  if (nr == NB) {
+    if (bs == 64)
+      dslash_mrhs_cfg<T, NB, 64>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
+    else
+      dslash_mrhs_cfg<T, NB, 128>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
+  } else {
+    if (bs == 64)
+      dslash_mrhs_cfg<T, NA, 64>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
+    else
+      dslash_mrhs_cfg<T, NA, 128>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
   }
 }
 template void dslash_mrhs<float>(const Geom&, Epilogue, int, int, size_t, float*, const float*, const float*,
@@ -497,12 +596,18 @@ template void dslash_mrhs<float>(const Geom&, Epilogue, int, int, size_t, float*
 template void dslash_mrhs<double>(const Geom&, Epilogue, int, int, size_t, double*, const double*, const double*,
                                   const double*, const double*, double, int, int, cudaStream_t);
 
-// clover multiply of nrhs vectors (rhs fastest, as the multi-RHS dslash)
+std::vector<int> dslash_mrhs_configs(bool fp32) {
+  return fp32 ? std::vector<int>{2064, 2128, 4064, 4128, 100004, 100008}
+              : std::vector<int>{1064, 1128, 2064, 2128, 100004, 100008};
+}
+int dslash_mrhs_default(bool fp32) { (void)fp32; return 100004; }
+
+// clover multiply of nrhs vectors (one thread per (site, rhs); the rhs is the
+// fastest block index, so the clover lines of a site block are shared in L2)
 template <typename T>
 __global__ void k_clover_apply_mrhs(Geom g, int nrhs, size_t stride, T* out, const T* __restrict__ in,
                                     const T* __restrict__ clov) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int i = (int)(t / nrhs), r = (int)(t % nrhs);
+  const int i = (int)(blockIdx.x / nrhs) * blockDim.x + threadIdx.x, r = (int)(blockIdx.x % nrhs);
   if (i >= g.Vh) return;
   cx<T> x[12], y[12];
   SpinorIO<T>::load(in + (size_t)r * stride, g.Vh, i, x);
@@ -513,8 +618,7 @@ __global__ void k_clover_apply_mrhs(Geom g, int nrhs, size_t stride, T* out, con
 template <typename T>
 void clover_apply_mrhs(const Geom& g, int nrhs, size_t stride, T* out, const T* in, const T* clov, cudaStream_t s) {
   const int bs = 128;
-  const long long threads = (long long)g.Vh * nrhs;
-  k_clover_apply_mrhs<T><<<(unsigned)((threads + bs - 1) / bs), bs, 0, s>>>(g, nrhs, stride, out, in, clov);
+  k_clover_apply_mrhs<T><<<(unsigned)(((g.Vh + bs - 1) / bs) * nrhs), bs, 0, s>>>(g, nrhs, stride, out, in, clov);
   MG_LAUNCH();
 }
 template void clover_apply_mrhs<float>(const Geom&, int, size_t, float*, const float*, const float*, cudaStream_t);

@@ -129,6 +129,80 @@ __device__ __forceinline__ void hop_sum(const Geom& g, const T* __restrict__ in,
   if (dirmask & 0x80) hop_term<T, 3, false>(g, in, gauge, par, i, c, acc);
 }
 
+// Multi-RHS form of hop_term: the link is loaded once and applied to the
+// neighbour spinors of nr <= NR right-hand sides (in + r * stride).
+template <typename T, int MU, bool FWD, int NR>
+__device__ __forceinline__ void hop_term_nr(const Geom& g, const T* __restrict__ in, size_t stride, int nr,
+                                            const T* __restrict__ gauge, int par, int i, const int c[4],
+                                            cx<T> acc[NR][12]) {
+  int sgn;
+  const int j = neighbour<MU, FWD>(g, c, sgn);
+  cx<T> u[9];
+  if (FWD)
+    load_link<T>(gauge, g.Vh, par, MU, i, u);
+  else
+    load_link<T>(gauge, g.Vh, 1 - par, MU, j, u);
+  const T s = (T)sgn;
+#pragma unroll
+  for (int r = 0; r < NR; r++) {
+    if (r >= nr) break;
+    cx<T> psi[12];
+    SpinorIO<T>::load(in + r * stride, g.Vh, j, psi);
+    cx<T> h0[3], h1[3];
+#pragma unroll
+    for (int col = 0; col < 3; col++) {
+      cx<T> a0, a1;
+      mul_a<MU, T>(psi[6 + col], psi[9 + col], a0, a1);
+      if (FWD) {
+        h0[col] = s * (psi[col] - a0);
+        h1[col] = s * (psi[3 + col] - a1);
+      } else {
+        h0[col] = s * (psi[col] + a0);
+        h1[col] = s * (psi[3 + col] + a1);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      cx<T> g0 = mkc<T>(0, 0), g1 = mkc<T>(0, 0);
+#pragma unroll
+      for (int b = 0; b < 3; b++) {
+        if (FWD) {
+          g0 = cfma(u[a * 3 + b], h0[b], g0);
+          g1 = cfma(u[a * 3 + b], h1[b], g1);
+        } else {
+          g0 = cfma_conj(u[b * 3 + a], h0[b], g0);
+          g1 = cfma_conj(u[b * 3 + a], h1[b], g1);
+        }
+      }
+      acc[r][a] = acc[r][a] + g0;
+      acc[r][3 + a] = acc[r][3 + a] + g1;
+      cx<T> b0, b1;
+      mul_b<MU, T>(g0, g1, b0, b1);
+      if (FWD) {
+        acc[r][6 + a] = acc[r][6 + a] - b0;
+        acc[r][9 + a] = acc[r][9 + a] - b1;
+      } else {
+        acc[r][6 + a] = acc[r][6 + a] + b0;
+        acc[r][9 + a] = acc[r][9 + a] + b1;
+      }
+    }
+  }
+}
+
+template <typename T, int NR>
+__device__ __forceinline__ void hop_sum_nr(const Geom& g, const T* __restrict__ in, size_t stride, int nr,
+                                           const T* __restrict__ gauge, int par, int i, const int c[4], int dirmask,
+                                           cx<T> acc[NR][12]) {
+  if (dirmask & 0x01) hop_term_nr<T, 0, true, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+  if (dirmask & 0x10) hop_term_nr<T, 0, false, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+  if (dirmask & 0x02) hop_term_nr<T, 1, true, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+  if (dirmask & 0x20) hop_term_nr<T, 1, false, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+  if (dirmask & 0x04) hop_term_nr<T, 2, true, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+  if (dirmask & 0x40) hop_term_nr<T, 2, false, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+  if (dirmask & 0x08) hop_term_nr<T, 3, true, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+  if (dirmask & 0x80) hop_term_nr<T, 3, false, NR>(g, in, stride, nr, gauge, par, i, c, acc);
+}
+
 // out = C x for a packed two-block clover (A or A^{-1}) at site i.
 template <typename T>
 __device__ __forceinline__ void clover_mul(const T* __restrict__ clov, int Vh, int i, const cx<T> x[12], cx<T> y[12]) {
