@@ -234,6 +234,26 @@ MG_API int mg_get_coarse_links(void* ctx, int level, void* Y, void* X, int where
 MG_API int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
              mg_solve_info* info);
 
+/* Solve several lattices together: context i (its own lattice, gauge field,
+ * clover and multigrid setup; all contexts on one device) solves
+ * D_i psi[i] = eta[i] for nrhs[i] right-hand sides (fine-vector layout of its
+ * lattice) to tolerance tol, by multigrid-preconditioned FGCR, one per
+ * right-hand side, run in lock-step: each iteration applies the fine
+ * operators of every context to all of its right-hand sides in multi-RHS
+ * launches, and puts the coarsest-level solves of all right-hand sides of all
+ * 2-level contexts into shared persistent launches (up to 16 systems and 8
+ * lattices each; contexts whose hierarchy is deeper, or whose coarse storage,
+ * restart or cap differ from the first's, solve their own).  Right-hand sides
+ * are taken in context order in groups of the first context's rhs_block.
+ * The contexts need the same restart_fine.  `where` applies to every buffer;
+ * infos (may be NULL) receives one mg_solve_info per context, solve_ms and
+ * kernel_launches being those of the whole call.  An extension of the paper's
+ * repeated solves "for varying sources and gauge fields".  Errors: MG_ERR_ARG
+ * (a context twice, different devices, ...), MG_ERR_STATE, MG_ERR_NAN,
+ * MG_ERR_NOT_CONVERGED, MG_ERR_CUDA. */
+MG_API int mg_solve_batch(void* const* ctxs, int nctx, void* const* psi, const void* const* eta, const int* nrhs,
+                          double tol, int where, mg_solve_info* infos);
+
 /* Solve the adjoint system D^dag psi = eta with the same solver and
  * multigrid, through gamma_5-hermiticity D^dag = gamma_5 D gamma_5:
  * psi = gamma_5 D^{-1} (gamma_5 eta).  This is the backward solve of a

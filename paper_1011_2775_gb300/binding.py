@@ -38,7 +38,7 @@ MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_D
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_get_coarse_links", "mg_solve", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
+            "mg_get_coarse_links", "mg_solve", "mg_solve_batch", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
             "mg_level_info"]
 
 
@@ -116,6 +116,8 @@ def lib() -> ctypes.CDLL:
             "mg_solve_dagger": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
             "mg_force": [vp, vp, vp, vp, ip, ip],
             "mg_get_coarse_links": [vp, ip, vp, vp, ip],
+            "mg_solve_batch": [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ip), dp,
+                               ip, ctypes.POINTER(mg_solve_info)],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
             "mg_benchmark_kernel": [vp, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_apply_noalloc": [vp, ip, vp, vp, ip],
@@ -220,6 +222,24 @@ def mg_solve(ctx, psi, eta, nrhs: int, tol: float, mode: int = MG_MODE_MG, allow
     st = lib().mg_solve(ctx, pp, pe, int(nrhs), float(tol), int(mode), wp, ctypes.byref(info))
     _check(st, "mg_solve", allow=(MG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return st, info
+
+
+def mg_solve_batch(ctxs, psis, etas, nrhs, tol: float, allow_not_converged=False):
+    """Solves several lattices together (one context each); returns ``(status, [mg_solve_info])``."""
+    n = len(ctxs)
+    bufs = [_buf(p, writable=True) for p in psis]
+    ebufs = [_buf(e) for e in etas]
+    wheres = {w for _, w in bufs} | {w for _, w in ebufs}
+    if len(wheres) != 1:
+        raise TypeError("all buffers must be host or all device buffers")
+    c_ctx = (ctypes.c_void_p * n)(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    c_psi = (ctypes.c_void_p * n)(*[p.value for p, _ in bufs])
+    c_eta = (ctypes.c_void_p * n)(*[p.value for p, _ in ebufs])
+    c_nrhs = (ctypes.c_int * n)(*[int(k) for k in nrhs])
+    infos = (mg_solve_info * n)()
+    st = lib().mg_solve_batch(c_ctx, n, c_psi, c_eta, c_nrhs, float(tol), wheres.pop(), infos)
+    _check(st, "mg_solve_batch", allow=(MG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return st, list(infos)
 
 
 def mg_solve_dagger(ctx, psi, eta, nrhs: int, tol: float, mode: int = MG_MODE_MG, allow_not_converged=False):

@@ -3,7 +3,9 @@
 // Every entry point converts internal exceptions to a status code and keeps
 // the message for mg_last_error().  Host buffers are staged through device
 // memory owned by the context; device buffers are read and written in place.
+#include <algorithm>
 #include <chrono>
+#include <vector>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -399,6 +401,73 @@ int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mo
 int mg_solve_dagger(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where,
                     mg_solve_info* info) {
   return guarded([&]() { return solve_impl(ctx, psi, eta, nrhs, tol, mode, where, info, true); });
+}
+
+int mg_solve_batch(void* const* ctxs, int nctx, void* const* psi, const void* const* eta, const int* nrhs, double tol,
+                   int where, mg_solve_info* infos) {
+  return guarded([&]() {
+    const auto t0 = std::chrono::steady_clock::now();
+    check_where(where);
+    if (!ctxs || !psi || !eta || !nrhs || nctx < 1 || !(tol > 0)) mg::raise(MG_ERR_ARG, "bad batch arguments");
+    std::vector<mg::Ctx*> cs(nctx);
+    for (int i = 0; i < nctx; i++) {
+      cs[i] = as_ctx(ctxs[i]);
+      if (!psi[i] || !eta[i] || nrhs[i] < 1) mg::raise(MG_ERR_ARG, "bad batch arguments");
+      if (!cs[i]->have_clover || !cs[i]->mg) mg::raise(MG_ERR_STATE, "every context needs gauge, clover and mg_setup");
+      if (cs[i]->device != cs[0]->device) mg::raise(MG_ERR_ARG, "contexts of one batch must share a device");
+      for (int j = 0; j < i; j++)
+        if (cs[j] == cs[i]) mg::raise(MG_ERR_ARG, "a context appears twice in the batch");
+    }
+    MG_CUDA(cudaSetDevice(cs[0]->device));
+    const long long kernels0 = mg::launches_so_far();
+    std::vector<Staged> si(nctx), so(nctx);
+    std::vector<mg_solve_info> loc(nctx);
+    for (int i = 0; i < nctx; i++) {
+      mg::Ctx* c = cs[i];
+      const size_t bytes = sizeof(double) * 24 * c->V * nrhs[i];
+      stage_in(c, si[i], eta[i], bytes, where);
+      stage_out_alloc(so[i], psi[i], bytes, where);
+      std::memset(&loc[i], 0, sizeof(mg_solve_info));
+      mg::mg_reset_counters(c);
+    }
+    // groups of right-hand sides (in context order) that one persistent launch can hold
+    const int cap = std::min(16, std::max(1, cs[0]->params.rhs_block));
+    int status = MG_OK;
+    std::vector<mg::BlockPart> parts;
+    int used = 0;
+    auto flush = [&]() {
+      if (parts.empty()) return;
+      const int st = mg::solve_multi_block(parts, tol);
+      if (st != MG_OK) status = st;
+      parts.clear();
+      used = 0;
+    };
+    for (int i = 0; i < nctx; i++) {
+      int q = 0;
+      while (q < nrhs[i]) {
+        const int take = std::min(nrhs[i] - q, cap - used);
+        mg::Ctx* c = cs[i];
+        parts.push_back(mg::BlockPart{c, take, si[i].ptr + (size_t)q * 24 * c->V, so[i].ptr + (size_t)q * 24 * c->V,
+                                      &loc[i]});
+        used += take;
+        q += take;
+        if (used == cap) flush();
+      }
+    }
+    flush();
+    for (int i = 0; i < nctx; i++) {
+      mg::Ctx* c = cs[i];
+      stage_out_finish(c, so[i], psi[i], sizeof(double) * 24 * c->V * nrhs[i], where);
+      mg::mg_read_counters(c, loc[i].coarse_iterations);
+    }
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < nctx; i++) {
+      loc[i].solve_ms = ms;
+      loc[i].kernel_launches = mg::launches_so_far() - kernels0;
+      if (infos) infos[i] = loc[i];
+    }
+    return status;
+  });
 }
 
 int mg_force(void* ctx, void* F, const void* lambda, const void* psi, int kind, int where) {

@@ -1,19 +1,24 @@
-// Several right-hand sides of one lattice solved together.
+// Several right-hand sides -- of one lattice, or of several lattices (contexts)
+// of uneven size -- solved together.
 //
 // The outer solver is the same flexible GCR(m) on D_r as solver.cu (section
-// "Red-black preconditioning"; section "Implementation"), run for nb
-// right-hand sides in lock-step: every iteration applies the multigrid cycle
-// to all residuals at once (mg_precondition_batch: multi-RHS D_r in the
-// smoother, all coarsest-level solves in one persistent launch) and the FP64
-// D_r to all new directions in one multi-RHS launch; the Krylov space,
-// scalars, convergence test and restart of every right-hand side are its own.
-// A right-hand side that has converged stops updating (its slot in the
-// multi-RHS launches is carried along).  Vectors are packed half vectors:
-// rhs q of a half at base + q * 24 Vh doubles.
+// "Red-black preconditioning"; section "Implementation"), run for every
+// right-hand side in lock-step: every iteration applies the multigrid cycle to
+// all residuals of a context at once (multi-RHS D_r in the smoother) and the
+// FP64 D_r to all its new directions in one multi-RHS launch, and the
+// coarsest-level solves of ALL right-hand sides of all contexts go into one
+// persistent launch (coarse_gcr_solve_multi: one coarse lattice per context,
+// systems of one lattice sharing link reads).  The Krylov space, scalars,
+// convergence test and restarts of every right-hand side are its own; a
+// right-hand side that has converged stops updating (its slot in the
+// multi-RHS launches is carried along).  Vectors are packed half vectors: rhs
+// q of a half at base + q * 24 Vh doubles.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "coarse.h"
 #include "internal.h"
 
 namespace mg {
@@ -25,186 +30,347 @@ struct BlockBuffers {
   DBuf r32;                                     // FP32, nb half vectors
   std::vector<DBuf> W, Z;                       // W[k] FP64, Z[k] FP32: nb half vectors each
   DBuf scal;                                    // per rhs: beta[2 m m], alpha[2 m], gam[m], c[2 m], orth[4]
-  DBuf rn2;                                     // per rhs: ||r||^2 (and a second slot)
+  DBuf rn2;                                     // per rhs: two norms
   std::unique_ptr<FineOps<double>> F64;
   size_t per_rhs() const { return 2 * (size_t)m * m + 5 * (size_t)m + 8; }
 };
-}  // namespace
 
-int solve_fine_block(Ctx* c, double* psi_abi, const double* eta_abi, int nb, double tol, mg_solve_info* info) {
-  const size_t n = 12 * c->Vh, hs = 24 * c->Vh;   // complex / doubles per half vector
-  cudaStream_t s = c->stream;
-  const int m = c->params.restart_fine > 0 ? c->params.restart_fine : 16;
+// one context's share of a block solve
+struct Run {
+  Ctx* c = nullptr;
+  int nb = 0;
+  const double* eta = nullptr;   // nb ABI vectors (device)
+  double* psi = nullptr;
+  mg_solve_info* info = nullptr;
+  BlockBuffers* B = nullptr;
+  size_t n = 0, hs = 0;
+  int m = 0, maxit = 0;
+  std::vector<double> bnorm, tol_r, true_res, h;
+  std::vector<char> active, run;
+  std::vector<int> used, kp;
+  int restarts = 0;
+  double* beta(int q) const { return B->scal.as<double>() + q * B->per_rhs(); }
+  double* alpha(int q) const { return beta(q) + 2 * (size_t)m * m; }
+  double* gam(int q) const { return alpha(q) + 2 * m; }
+  double* cc(int q) const { return gam(q) + m; }
+  double* orth(int q) const { return cc(q) + 2 * m; }
+};
+
+bool any_of(const std::vector<char>& f) {
+  for (char v : f)
+    if (v) return true;
+  return false;
+}
+
+void prepare(Run& R, double tol) {
+  Ctx* c = R.c;
+  R.n = 12 * c->Vh;
+  R.hs = 24 * c->Vh;
+  R.m = c->params.restart_fine > 0 ? c->params.restart_fine : 16;
+  R.maxit = c->params.maxit_fine > 0 ? c->params.maxit_fine : 500;
   BlockBuffers* Bp = static_cast<BlockBuffers*>(c->block_work.get());
-  if (!Bp || Bp->nb < nb || Bp->m != m) {
+  if (!Bp || Bp->nb < R.nb || Bp->m != R.m) {
     c->block_work.reset();
     std::shared_ptr<BlockBuffers> nbuf(new BlockBuffers());
     c->block_work = nbuf;
     Bp = nbuf.get();
-    Bp->nb = nb;
-    Bp->m = m;
+    Bp->nb = R.nb;
+    Bp->m = R.m;
     for (DBuf* d : {&Bp->be, &Bp->bo, &Bp->y, &Bp->br, &Bp->r, &Bp->tmp, &Bp->xe, &Bp->xo, &Bp->te, &Bp->to})
-      d->alloc(sizeof(double) * hs * nb);
-    Bp->r32.alloc(sizeof(float) * hs * nb);
-    Bp->W.resize(m);
-    Bp->Z.resize(m);
-    for (int k = 0; k < m; k++) {
-      Bp->W[k].alloc(sizeof(double) * hs * nb);
-      Bp->Z[k].alloc(sizeof(float) * hs * nb);
+      d->alloc(sizeof(double) * R.hs * R.nb);
+    Bp->r32.alloc(sizeof(float) * R.hs * R.nb);
+    Bp->W.resize(R.m);
+    Bp->Z.resize(R.m);
+    for (int k = 0; k < R.m; k++) {
+      Bp->W[k].alloc(sizeof(double) * R.hs * R.nb);
+      Bp->Z[k].alloc(sizeof(float) * R.hs * R.nb);
     }
-    Bp->scal.alloc(sizeof(double) * Bp->per_rhs() * nb);
-    Bp->rn2.alloc(sizeof(double) * 2 * nb);
+    Bp->scal.alloc(sizeof(double) * Bp->per_rhs() * R.nb);
+    Bp->rn2.alloc(sizeof(double) * 2 * R.nb);
     Bp->F64.reset(new FineOps<double>(c));
   }
-  BlockBuffers& B = *Bp;
-  FineOps<double>& F = *B.F64;
-  double* be = B.be.as<double>();
-  double* bo = B.bo.as<double>();
-  double* y = B.y.as<double>();
-  double* br = B.br.as<double>();
-  double* r = B.r.as<double>();
-  double* tmp = B.tmp.as<double>();
-  double* xe = B.xe.as<double>();
-  double* xo = B.xo.as<double>();
-  double* te = B.te.as<double>();
-  double* to = B.to.as<double>();
-  float* r32 = B.r32.as<float>();
-  double* rn2 = B.rn2.as<double>();
-  const size_t ns = B.per_rhs();
-  auto beta = [&](int q) { return B.scal.as<double>() + q * ns; };
-  auto alpha = [&](int q) { return beta(q) + 2 * (size_t)m * m; };
-  auto gam = [&](int q) { return alpha(q) + 2 * m; };
-  auto cc = [&](int q) { return gam(q) + m; };
-  auto orth = [&](int q) { return cc(q) + 2 * m; };
+  R.B = Bp;
+  const int nb = R.nb;
+  R.h.assign(2 * (size_t)nb, 0.0);
+  R.bnorm.assign(nb, 0.0);
+  R.tol_r.assign(nb, 0.0);
+  R.true_res.assign(nb, INFINITY);
+  R.active.assign(nb, 1);
+  R.run.assign(nb, 0);
+  R.used.assign(nb, 0);
+  R.kp.assign(nb, 0);
+  (void)tol;
+}
 
-  for (int q = 0; q < nb; q++) pack_spinor(c->g, eta_abi + (size_t)q * 24 * c->V, be + q * hs, bo + q * hs, false, s);
-  std::vector<double> h(2 * (size_t)nb);
-  auto read_norms = [&](const double* ve, const double* vo, const std::vector<char>& which) {
-    for (int q = 0; q < nb; q++) {
-      if (!which[q]) continue;
-      blas_norm2<double>(ve + q * hs, n, rn2 + 2 * q, c->ws, s);
-      if (vo) blas_norm2<double>(vo + q * hs, n, rn2 + 2 * q + 1, c->ws, s);
-    }
-    if (!vo)
-      for (int q = 0; q < nb; q++)
-        if (which[q]) MG_CUDA(cudaMemsetAsync(rn2 + 2 * q + 1, 0, sizeof(double), s));
-    MG_CUDA(cudaMemcpyAsync(h.data(), rn2, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s));
-    c->sync();
-  };
-  std::vector<char> all(nb, 1), active(nb, 1), run(nb, 0);
-  read_norms(be, bo, all);
-  std::vector<double> bnorm(nb), tol_r(nb), true_res(nb, INFINITY);
-  for (int q = 0; q < nb; q++) {
-    bnorm[q] = std::sqrt(h[2 * q] + h[2 * q + 1]);
-    if (!std::isfinite(bnorm[q])) raise(MG_ERR_NAN, "non-finite source");
-    tol_r[q] = 0.5 * tol * bnorm[q];
-    if (bnorm[q] == 0.0) {
-      active[q] = 0;
-      true_res[q] = 0.0;
-    }
+// norms of the nb half vectors ve (+ vo) of the selected rhs -> R.h (one host sync)
+void read_norms(Run& R, const double* ve, const double* vo, const std::vector<char>& which) {
+  Ctx* c = R.c;
+  double* rn2 = R.B->rn2.as<double>();
+  for (int q = 0; q < R.nb; q++) {
+    if (!which[q]) continue;
+    blas_norm2<double>(ve + q * R.hs, R.n, rn2 + 2 * q, c->ws, c->stream);
+    if (vo)
+      blas_norm2<double>(vo + q * R.hs, R.n, rn2 + 2 * q + 1, c->ws, c->stream);
+    else
+      MG_CUDA(cudaMemsetAsync(rn2 + 2 * q + 1, 0, sizeof(double), c->stream));
   }
-  F.br_multi(br, be, bo, nb, hs);
-  blas_zero<double>(y, n * nb, s);
-  blas_convert<double, double>(r, br, n * nb, s);
-  const int maxit = c->params.maxit_fine > 0 ? c->params.maxit_fine : 500;
-  std::vector<int> used(nb, 0);
-  int it = 0, restarts = 0;
-  auto any = [&](const std::vector<char>& f) {
-    for (char v : f)
-      if (v) return true;
-    return false;
-  };
-  std::vector<const double*> Wp(m);
-  std::vector<const float*> Zp(m);
-  for (int attempt = 0; attempt < 8 && any(active) && it < maxit; attempt++) {
-    while (any(active) && it < maxit) {
-      int k = 0;
-      std::vector<int> kp(nb, 0);
-      run = active;
-      while (k < m && it < maxit && any(run)) {
-        float* zk = B.Z[k].as<float>();
-        double* wk = B.W[k].as<double>();
-        blas_convert<double, float>(r32, r, n * nb, s);
-        mg_precondition_batch(c, zk, r32, nb);
-        blas_convert<float, double>(tmp, zk, n * nb, s);
-        F.Dr_multi(wk, tmp, nb, hs);
-        for (int q = 0; q < nb; q++) {
-          if (!run[q]) continue;
-          for (int j = 0; j < k; j++) Wp[j] = B.W[j].as<double>() + q * hs;
-          double* w = wk + q * hs;
-          double* bk = beta(q) + 2 * (size_t)m * k;
-          if (k > 0) blas_multidot<double>(Wp.data(), k, w, n, bk, c->ws, s);
-          blas_orth_update<double>(w, Wp.data(), bk, k, r + q * hs, n, orth(q), c->ws, s);
-          blas_r_update<double>(w, r + q * hs, n, orth(q), alpha(q) + 2 * k, gam(q) + k, rn2 + 2 * q, c->ws, s);
-        }
-        MG_CUDA(cudaMemcpyAsync(h.data(), rn2, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s));
-        c->sync();
-        k++;
-        it++;
-        for (int q = 0; q < nb; q++) {
-          if (!run[q]) continue;
-          kp[q] = k;
-          used[q]++;
-          const double rn = std::sqrt(h[2 * q]);
-          if (!std::isfinite(rn)) raise(MG_ERR_NAN, "non-finite residual in block GCR");
-          if (rn <= tol_r[q]) run[q] = 0;
-        }
-      }
-      // per rhs: back substitution and y += sum_j c_j z_j
-      for (int q = 0; q < nb; q++) {
-        if (!kp[q]) continue;
-        for (int j = 0; j < kp[q]; j++) Zp[j] = B.Z[j].as<float>() + q * hs;
-        gcr_backsub(beta(q), m, alpha(q), gam(q), kp[q], cc(q), s);
-        blas_lincomb<double, float>(y + q * hs, Zp.data(), cc(q), kp[q], 1.0, n, s);
-      }
-      restarts++;
-      // true residuals of the reduced systems
-      F.Dr_multi(tmp, y, nb, hs);
-      blas_convert<double, double>(r, br, n * nb, s);
-      blas_axpby<double>(-1.0, tmp, 1.0, r, n * nb, s);
-      read_norms(r, nullptr, active);
-      for (int q = 0; q < nb; q++) {
-        if (!active[q]) continue;
-        const double rn = std::sqrt(h[2 * q]);
-        if (!std::isfinite(rn)) raise(MG_ERR_NAN, "non-finite true residual");
-        if (rn <= tol_r[q]) active[q] = 0;
-      }
-    }
-    // reconstruction and the true residual of the full system
-    F.reconstruct_multi(xe, xo, y, bo, nb, hs);
-    F.D_multi(te, to, xe, xo, nb, hs);
-    blas_axpby<double>(1.0, be, -1.0, te, n * nb, s);
-    blas_axpby<double>(1.0, bo, -1.0, to, n * nb, s);
-    std::vector<char> nz(nb);
-    for (int q = 0; q < nb; q++) nz[q] = bnorm[q] > 0.0;
-    read_norms(te, to, nz);
-    for (int q = 0; q < nb; q++) {
-      if (!nz[q]) continue;
-      true_res[q] = std::sqrt(h[2 * q] + h[2 * q + 1]) / bnorm[q];
-      if (!std::isfinite(true_res[q])) raise(MG_ERR_NAN, "non-finite solution");
-      active[q] = true_res[q] > tol;
-    }
-  }
-  for (int q = 0; q < nb; q++) {
-    if (bnorm[q] == 0.0) {
-      MG_CUDA(cudaMemsetAsync(psi_abi + (size_t)q * 24 * c->V, 0, sizeof(double) * 24 * c->V, s));
+  MG_CUDA(cudaMemcpyAsync(R.h.data(), rn2, sizeof(double) * 2 * R.nb, cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+}
+
+// the cycle for every run, with the coarsest solves of the joinable runs in
+// shared launches (the others solve their own)
+void precondition_all(std::vector<Run>& runs, int k) {
+  std::vector<Run*> joint, own;
+  for (Run& R : runs) (mg_batch_joinable(R.c) ? joint : own).push_back(&R);
+  // runs that can share a launch: same device, coarse storage, restart, cap and even-odd structure
+  std::vector<Run*> shared, alone = own;
+  for (Run* R : joint) {
+    if (shared.empty()) {
+      shared.push_back(R);
       continue;
     }
-    unpack_spinor(c->g, xe + q * hs, xo + q * hs, false, psi_abi + (size_t)q * 24 * c->V, s);
+    const mg_params& a = shared[0]->c->params;
+    const mg_params& b = R->c->params;
+    const bool ok = R->c->device == shared[0]->c->device && a.storage == b.storage &&
+                    a.restart_coarse == b.restart_coarse && a.maxit_coarse == b.maxit_coarse;
+    (ok ? shared : alone).push_back(R);
   }
-  c->sync();
-  int status = MG_OK;
-  if (info) {
-    for (int q = 0; q < nb; q++) {
-      info->outer_iterations += used[q];
-      if (true_res[q] > info->true_residual || info->true_residual != info->true_residual)
-        info->true_residual = true_res[q];
+  for (Run& R : runs) {
+    float* zk = R.B->Z[k].as<float>();
+    float* r32 = R.B->r32.as<float>();
+    blas_convert<double, float>(r32, R.B->r.as<double>(), R.n * R.nb, R.c->stream);
+    mg_batch_pre(R.c, zk, r32, R.nb);
+  }
+  for (Run* R : alone) mg_batch_coarse(R->c, R->nb);
+  if (!shared.empty()) {
+    // all systems, in groups the persistent kernel accepts; the first context's stream
+    // runs the shared launches after every participant's restriction
+    Ctx* c0 = shared[0]->c;
+    std::vector<CoarseSystem> sys;
+    std::vector<std::vector<CoarseSystem>> launches;
+    std::vector<const void*> lattices;
+    for (Run* R : shared) {
+      std::vector<CoarseSystem> mine;
+      mg_batch_systems(R->c, R->nb, mine);
+      for (const CoarseSystem& cs : mine) {
+        const bool new_lattice = std::find(lattices.begin(), lattices.end(), (const void*)cs.G) == lattices.end();
+        if ((int)sys.size() == coarse_gcr_batch_max() ||
+            (new_lattice && (int)lattices.size() == coarse_gcr_group_max()) ||
+            (!sys.empty() && (cs.G->eo != sys[0].G->eo))) {
+          launches.push_back(sys);
+          sys.clear();
+          lattices.clear();
+        }
+        if (std::find(lattices.begin(), lattices.end(), (const void*)cs.G) == lattices.end()) lattices.push_back(cs.G);
+        sys.push_back(cs);
+      }
     }
-    info->restarts += restarts;
+    if (!sys.empty()) launches.push_back(sys);
+    std::vector<cudaEvent_t> ev;
+    for (Run* R : shared)
+      if (R->c->stream != c0->stream) {
+        cudaEvent_t e;
+        MG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        MG_CUDA(cudaEventRecord(e, R->c->stream));
+        MG_CUDA(cudaStreamWaitEvent(c0->stream, e, 0));
+        ev.push_back(e);
+      }
+    const mg_params& p0 = c0->params;
+    const int restart = p0.restart_coarse > 0 ? p0.restart_coarse : 32;
+    for (const auto& L : launches)
+      coarse_gcr_solve_multi(L, mg_batch_buffers(c0), restart, p0.maxit_coarse, c0->ws.flags.as<int>(), c0->stream);
+    cudaEvent_t done;
+    MG_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
+    MG_CUDA(cudaEventRecord(done, c0->stream));
+    for (Run* R : shared)
+      if (R->c->stream != c0->stream) MG_CUDA(cudaStreamWaitEvent(R->c->stream, done, 0));
+    MG_CUDA(cudaStreamSynchronize(c0->stream));   // the events may be destroyed once the launches ran
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    cudaEventDestroy(done);
   }
-  for (int q = 0; q < nb; q++)
-    if (!(true_res[q] <= tol)) status = MG_ERR_NOT_CONVERGED;
+  for (Run& R : runs) mg_batch_post(R.c, R.B->Z[k].as<float>(), R.B->r32.as<float>(), R.nb);
+}
+
+int solve_runs(std::vector<Run>& runs, double tol) {
+  for (Run& R : runs) prepare(R, tol);
+  const int m = runs[0].m;
+  for (Run& R : runs)
+    if (R.m != m) raise(MG_ERR_ARG, "contexts solved together need the same restart_fine");
+  // sources, their norms, b_r
+  for (Run& R : runs) {
+    BlockBuffers& B = *R.B;
+    Ctx* c = R.c;
+    for (int q = 0; q < R.nb; q++)
+      pack_spinor(c->g, R.eta + (size_t)q * 24 * c->V, B.be.as<double>() + q * R.hs, B.bo.as<double>() + q * R.hs,
+                  false, c->stream);
+    read_norms(R, B.be.as<double>(), B.bo.as<double>(), std::vector<char>(R.nb, 1));
+    for (int q = 0; q < R.nb; q++) {
+      R.bnorm[q] = std::sqrt(R.h[2 * q] + R.h[2 * q + 1]);
+      if (!std::isfinite(R.bnorm[q])) raise(MG_ERR_NAN, "non-finite source");
+      R.tol_r[q] = 0.5 * tol * R.bnorm[q];
+      if (R.bnorm[q] == 0.0) {
+        R.active[q] = 0;
+        R.true_res[q] = 0.0;
+      }
+    }
+    B.F64->br_multi(B.br.as<double>(), B.be.as<double>(), B.bo.as<double>(), R.nb, R.hs);
+    blas_zero<double>(B.y.as<double>(), R.n * R.nb, c->stream);
+    blas_convert<double, double>(B.r.as<double>(), B.br.as<double>(), R.n * R.nb, c->stream);
+  }
+  auto any_active = [&]() {
+    for (Run& R : runs)
+      if (any_of(R.active)) return true;
+    return false;
+  };
+  auto any_running = [&]() {
+    for (Run& R : runs)
+      if (any_of(R.run)) return true;
+    return false;
+  };
+  int it = 0;
+  int maxit = 0;
+  for (Run& R : runs) maxit = std::max(maxit, R.maxit);
+  std::vector<const double*> Wp(m);
+  std::vector<const float*> Zp(m);
+  for (int attempt = 0; attempt < 8 && any_active() && it < maxit; attempt++) {
+    while (any_active() && it < maxit) {
+      int k = 0;
+      for (Run& R : runs) {
+        std::fill(R.kp.begin(), R.kp.end(), 0);
+        R.run = R.active;
+        if (it >= R.maxit) std::fill(R.run.begin(), R.run.end(), 0);
+      }
+      while (k < m && it < maxit && any_running()) {
+        precondition_all(runs, k);
+        for (Run& R : runs) {
+          BlockBuffers& B = *R.B;
+          Ctx* c = R.c;
+          double* wk = B.W[k].as<double>();
+          double* tmp = B.tmp.as<double>();
+          double* r = B.r.as<double>();
+          blas_convert<float, double>(tmp, B.Z[k].as<float>(), R.n * R.nb, c->stream);
+          B.F64->Dr_multi(wk, tmp, R.nb, R.hs);
+          for (int q = 0; q < R.nb; q++) {
+            if (!R.run[q]) continue;
+            for (int j = 0; j < k; j++) Wp[j] = B.W[j].as<double>() + q * R.hs;
+            double* w = wk + q * R.hs;
+            double* bk = R.beta(q) + 2 * (size_t)m * k;
+            if (k > 0) blas_multidot<double>(Wp.data(), k, w, R.n, bk, c->ws, c->stream);
+            blas_orth_update<double>(w, Wp.data(), bk, k, r + q * R.hs, R.n, R.orth(q), c->ws, c->stream);
+            blas_r_update<double>(w, r + q * R.hs, R.n, R.orth(q), R.alpha(q) + 2 * k, R.gam(q) + k,
+                                  B.rn2.as<double>() + 2 * q, c->ws, c->stream);
+          }
+        }
+        for (Run& R : runs) {
+          MG_CUDA(cudaMemcpyAsync(R.h.data(), R.B->rn2.as<double>(), sizeof(double) * 2 * R.nb,
+                                  cudaMemcpyDeviceToHost, R.c->stream));
+          R.c->sync();
+          for (int q = 0; q < R.nb; q++) {
+            if (!R.run[q]) continue;
+            R.kp[q] = k + 1;
+            R.used[q]++;
+            const double rn = std::sqrt(R.h[2 * q]);
+            if (!std::isfinite(rn)) raise(MG_ERR_NAN, "non-finite residual in block GCR");
+            if (rn <= R.tol_r[q] || it + 1 >= R.maxit) R.run[q] = 0;
+          }
+        }
+        k++;
+        it++;
+      }
+      for (Run& R : runs) {
+        BlockBuffers& B = *R.B;
+        Ctx* c = R.c;
+        double* y = B.y.as<double>();
+        for (int q = 0; q < R.nb; q++) {
+          if (!R.kp[q]) continue;
+          for (int j = 0; j < R.kp[q]; j++) Zp[j] = B.Z[j].as<float>() + q * R.hs;
+          gcr_backsub(R.beta(q), m, R.alpha(q), R.gam(q), R.kp[q], R.cc(q), c->stream);
+          blas_lincomb<double, float>(y + q * R.hs, Zp.data(), R.cc(q), R.kp[q], 1.0, R.n, c->stream);
+        }
+        R.restarts++;
+        // true residuals of the reduced systems
+        double* tmp = B.tmp.as<double>();
+        double* r = B.r.as<double>();
+        B.F64->Dr_multi(tmp, y, R.nb, R.hs);
+        blas_convert<double, double>(r, B.br.as<double>(), R.n * R.nb, c->stream);
+        blas_axpby<double>(-1.0, tmp, 1.0, r, R.n * R.nb, c->stream);
+        read_norms(R, r, nullptr, R.active);
+        for (int q = 0; q < R.nb; q++) {
+          if (!R.active[q]) continue;
+          const double rn = std::sqrt(R.h[2 * q]);
+          if (!std::isfinite(rn)) raise(MG_ERR_NAN, "non-finite true residual");
+          if (rn <= R.tol_r[q] || it >= R.maxit) R.active[q] = 0;
+        }
+      }
+    }
+    // reconstruction and the true residual of the full systems
+    for (Run& R : runs) {
+      BlockBuffers& B = *R.B;
+      double *xe = B.xe.as<double>(), *xo = B.xo.as<double>(), *te = B.te.as<double>(), *to = B.to.as<double>();
+      B.F64->reconstruct_multi(xe, xo, B.y.as<double>(), B.bo.as<double>(), R.nb, R.hs);
+      B.F64->D_multi(te, to, xe, xo, R.nb, R.hs);
+      blas_axpby<double>(1.0, B.be.as<double>(), -1.0, te, R.n * R.nb, R.c->stream);
+      blas_axpby<double>(1.0, B.bo.as<double>(), -1.0, to, R.n * R.nb, R.c->stream);
+      std::vector<char> nz(R.nb);
+      for (int q = 0; q < R.nb; q++) nz[q] = R.bnorm[q] > 0.0;
+      read_norms(R, te, to, nz);
+      for (int q = 0; q < R.nb; q++) {
+        if (!nz[q]) continue;
+        R.true_res[q] = std::sqrt(R.h[2 * q] + R.h[2 * q + 1]) / R.bnorm[q];
+        if (!std::isfinite(R.true_res[q])) raise(MG_ERR_NAN, "non-finite solution");
+        R.active[q] = R.true_res[q] > tol && it < R.maxit;
+      }
+    }
+  }
+  int status = MG_OK;
+  for (Run& R : runs) {
+    BlockBuffers& B = *R.B;
+    Ctx* c = R.c;
+    for (int q = 0; q < R.nb; q++) {
+      double* dst = R.psi + (size_t)q * 24 * c->V;
+      if (R.bnorm[q] == 0.0) {
+        MG_CUDA(cudaMemsetAsync(dst, 0, sizeof(double) * 24 * c->V, c->stream));
+        continue;
+      }
+      unpack_spinor(c->g, B.xe.as<double>() + q * R.hs, B.xo.as<double>() + q * R.hs, false, dst, c->stream);
+    }
+    c->sync();
+    if (R.info) {
+      for (int q = 0; q < R.nb; q++) {
+        R.info->outer_iterations += R.used[q];
+        if (R.true_res[q] > R.info->true_residual || R.info->true_residual != R.info->true_residual)
+          R.info->true_residual = R.true_res[q];
+      }
+      R.info->restarts += R.restarts;
+    }
+    for (int q = 0; q < R.nb; q++)
+      if (!(R.true_res[q] <= tol)) status = MG_ERR_NOT_CONVERGED;
+  }
   return status;
+}
+}  // namespace
+
+int solve_fine_block(Ctx* c, double* psi_abi, const double* eta_abi, int nb, double tol, mg_solve_info* info) {
+  std::vector<Run> runs(1);
+  runs[0].c = c;
+  runs[0].nb = nb;
+  runs[0].eta = eta_abi;
+  runs[0].psi = psi_abi;
+  runs[0].info = info;
+  return solve_runs(runs, tol);
+}
+
+int solve_multi_block(const std::vector<BlockPart>& parts, double tol) {
+  std::vector<Run> runs(parts.size());
+  for (size_t i = 0; i < parts.size(); i++) {
+    runs[i].c = parts[i].c;
+    runs[i].nb = parts[i].nb;
+    runs[i].eta = parts[i].eta;
+    runs[i].psi = parts[i].psi;
+    runs[i].info = parts[i].info;
+  }
+  return solve_runs(runs, tol);
 }
 
 }  // namespace mg

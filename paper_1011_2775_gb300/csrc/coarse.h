@@ -112,9 +112,7 @@ struct CoarseGCRBuffers {
   int grid = 0;            // co-resident blocks of the cooperative launch
   int nsplit = 1;          // work items per site in the stencil phases (row split)
   DBuf r, y, br, tA, tB, W, Z, partials, scal;
-  // batched solve (allocated on first use, for up to bcap problems)
-  int bcap = 0, bm = 0, bgrid = 0, bnb = 0, bGp = 0;
-  size_t bnscal = 0;
+  // batched solves (coarse_batch.cu; grown on demand)
   DBuf bx_r, bx_y, bx_br, bx_tB, bx_W, bx_Z, bx_part, bx_scal;
   void init(const LevelGeom& G, int nc, int m);
 };
@@ -124,13 +122,36 @@ struct CoarseGCRBuffers {
 void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuffers& B, int m, int maxit,
                       double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s);
 
-// The same solve for nb right-hand sides b[p] (full vectors, [nb][nsites nc])
-// in one cooperative launch, each to its own tolerance; x[p] likewise.
-// nb <= coarse_gcr_batch_max().  Adds the iterations of all problems to *d_iters.
+// ---- batched coarsest solves (coarse_batch.cu)
+// One coarse system: the lattice and operator (a level of some context), its
+// right-hand side and solution (full FP32 coarse vectors), its relative
+// tolerance and the device counter its iterations are added to.
+struct CoarseSystem {
+  const LevelGeom* G;
+  const CoarseOp* C;
+  const float* b;
+  float* x;
+  double tol_rel;
+  long long* iters;
+};
+// Solves up to coarse_gcr_batch_max() systems -- of at most
+// coarse_gcr_group_max() different lattices, all even-odd or none, one link
+// storage format -- in one cooperative launch, each to its own tolerance, by
+// the GCR(m) of coarse_gcr_solve.  Buffers in B grow on demand.
 int coarse_gcr_batch_max();
+int coarse_gcr_group_max();
+void coarse_gcr_solve_multi(const std::vector<CoarseSystem>& sys, CoarseGCRBuffers& B, int m, int maxit, int* flags,
+                            cudaStream_t s);
+// nb right-hand sides of one lattice (b, x: [nb][nsites nc] floats x 2)
 void coarse_gcr_solve_batch(const LevelGeom& G, const CoarseOp& C, CoarseGCRBuffers& B, int m, int maxit,
                             double tol_rel, int nb, const float* b, float* x, long long* d_iters, int* flags,
                             cudaStream_t s);
+
+// the coarsest systems of a context's batched cycle (2-level hierarchies; the
+// right-hand sides were written by mg_batch_pre) and the buffers of its
+// batched solves (multigrid.cu)
+void mg_batch_systems(Ctx* c, int nb, std::vector<CoarseSystem>& out);
+CoarseGCRBuffers& mg_batch_buffers(Ctx* c);
 
 // ---- setup kernels
 // Philox start vector on a coarse level (AoS)

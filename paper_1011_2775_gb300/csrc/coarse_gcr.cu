@@ -468,443 +468,6 @@ __global__ void __launch_bounds__(kThreads) k_coarse_gcr(CGArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters += its;
 }
 
-// =========================================================================== batched solve
-// B independent right-hand sides of the same coarsest operator in one
-// cooperative launch.  The coarsest solve is latency-bound (grid barriers and
-// L2 round trips, not bytes), so solving B systems in lock-step costs little
-// more per iteration than solving one:
-//  * stencil phases: a work item is a site, processed for every active
-//    problem -- the neighbour vectors of all problems are gathered once and
-//    every link pair loaded serves kPB problems (warp_gemv_multi);
-//  * element-wise phases: the CTAs are split into B groups of Gp; group p owns
-//    problem p's vectors, so a CTA reduces and reads only its own problem's
-//    partial sums (Gp per slot); the residual norms that decide convergence
-//    are read for every problem by every CTA (B * Gp = gridDim partials).
-// Each problem keeps its own Krylov space, scalars, convergence test and
-// restart decisions; a converged problem is skipped.  All decisions derive
-// from sums every CTA computes in the same order, so the barriers stay
-// uniform.
-constexpr int kMaxBatch = 16;
-constexpr int kPB = 4;   // problems per link pass of the multi-vector GEMV
-constexpr int kRB = 2;   // rows per pass of the multi-vector GEMV
-
-struct BArgs {
-  CGArgs a;          // geometry, links, flags, tolerance; vector fields unused
-  int B;             // problems
-  int Gp;            // CTAs per problem group (gridDim.x >= B * Gp)
-  size_t nfull;      // nsites * nc
-  size_t n;          // half or full vector length
-  const float2* b;   // [B][nfull]
-  float2* x;         // [B][nfull]
-  float2* r;         // [B][n]
-  float2* y;         // [B][n]
-  float2* br;        // [B][n]
-  float2* tB;        // [B][nfull]
-  float2* W;         // [m][B][n]
-  float2* Z;         // [m][B][n]
-  double* partials;  // [kNR][B][Gp]
-  double* scal;      // [B][nscal]
-  size_t nscal;
-};
-
-// block partial sums of nq values of this CTA's problem: slot (q0 + q, p, gi)
-__device__ void own_partials(const BArgs& A, const double* v, int nq, int q0, int p, int gi, double* sred) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = 0; q < nq; q++) {
-    const double t = wsum(v[q]);
-    if (lane == 0) sred[q * 8 + wid] = t;
-  }
-  __syncthreads();
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < nw; w++) s += sred[q * 8 + w];
-    A.partials[((size_t)(q0 + q) * A.B + p) * A.Gp + gi] = s;
-  }
-  __syncthreads();
-}
-
-// totals of slots [q0, q0+nq) of problem p: out[q] (one warp per slot)
-__device__ void own_totals(const BArgs& A, int q0, int nq, int p, double* out) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int q = wid; q < nq; q += nw) {
-    double s = 0.0;
-    for (int g = lane; g < A.Gp; g += 32) s += __ldcg(A.partials + ((size_t)(q0 + q) * A.B + p) * A.Gp + g);
-    s = wsum(s);
-    if (lane == 0) out[q] = s;
-  }
-  __syncthreads();
-}
-
-// slot q of every problem: out[p] (one warp per problem)
-__device__ void all_totals(const BArgs& A, int q, double* out) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int p = wid; p < A.B; p += nw) {
-    double s = 0.0;
-    for (int g = lane; g < A.Gp; g += 32) s += __ldcg(A.partials + ((size_t)q * A.B + p) * A.Gp + g);
-    s = wsum(s);
-    if (lane == 0) out[p] = s;
-  }
-  __syncthreads();
-}
-
-// Stencil over sites [s0, s1) for the np problems in plist:
-//   out_p[s] = [xs_p[s] -] L(s) v_p  with v_p gathered from in_p at the 8
-// neighbours (and s itself when nb == 9), tile scales scale[(s-lbase)*nb+d].
-// Work item = one site for all listed problems.
-// the problems of `mask` as a list in shared memory; returns their number
-__device__ int list_of(unsigned mask, int* slist) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int q = 0;
-    for (int p = 0; p < kMaxBatch; p++)
-      if ((mask >> p) & 1u) slist[q++] = p;
-  }
-  __syncthreads();
-  return __popc(mask);
-}
-
-template <int ST>
-__device__ void msites(const BArgs& A, unsigned mask, int* plist, const void* L, const float* scale, int lbase,
-                       int nb, bool subtract, int s0, int s1, float2* out, size_t ostride, const float2* in,
-                       size_t istride, const float2* xs, size_t xstride, float2* sm) {
-  const int np = list_of(mask, plist);
-  if (np == 0) return;
-  const CGArgs& a = A.a;
-  const int nc = a.nc;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int rpw = (nc + nw - 1) / nw;
-  const int per = nb * nc;
-  for (int s = s0 + blockIdx.x; s < s1; s += gridDim.x) {
-    for (int t = threadIdx.x; t < np * per; t += blockDim.x) {
-      const int q = t / per, rem = t % per, d = rem / nc, j = rem % nc;
-      const float2* inp = in + plist[q] * istride;
-      float2 x = d < 8 ? inp[(size_t)a.nbr[(size_t)s * 8 + d] * nc + j] : inp[(size_t)s * nc + j];
-      if (scale) {
-        const float sc = scale[(size_t)(s - lbase) * nb + d];
-        x = make_float2(sc * x.x, sc * x.y);
-      }
-      sm[t] = x;
-    }
-    __syncthreads();
-    const void* Ls = static_cast<const char*>(L) + (size_t)(s - lbase) * nc * nb * nc * link_bytes<ST>();
-    for (int q0 = 0; q0 < np; q0 += kPB) {
-      const int cnt = np - q0 < kPB ? np - q0 : kPB;
-      for (int rb = 0; rb < rpw; rb += kRB) {
-        const int i0 = w * rpw + rb;
-        if (i0 >= nc) break;
-        float2 res[kRB][kPB];
-        warp_gemv_multi<ST, kRB, kPB>(Ls, i0, nc, per, sm + q0 * per, per, cnt, lane, res);
-        if (lane == 0)
-#pragma unroll
-          for (int r = 0; r < kRB; r++) {
-            const int i = i0 + r;
-            if (rb + r < rpw && i < nc)
-#pragma unroll
-              for (int pp = 0; pp < kPB; pp++) {
-                if (pp >= cnt) break;
-                const int p = plist[q0 + pp];
-                float2 o = res[r][pp];
-                if (subtract) {
-                  const float2 x = xs[p * xstride + (size_t)s * nc + i];
-                  o = make_float2(x.x - o.x, x.y - o.y);
-                }
-                out[p * ostride + (size_t)s * nc + i] = o;
-              }
-          }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// out_p[s] = C(s) in_p[s] for sites [s0, s1) of the listed problems
-__device__ void msite_mul(const BArgs& A, unsigned mask, int* plist, const float2* C, int s0, int s1, float2* out,
-                          size_t ostride, const float2* in, size_t istride, float2* sm) {
-  const int np = list_of(mask, plist);
-  if (np == 0) return;
-  const int nc = A.a.nc;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int rpw = (nc + nw - 1) / nw;
-  for (int s = s0 + blockIdx.x; s < s1; s += gridDim.x) {
-    for (int t = threadIdx.x; t < np * nc; t += blockDim.x) sm[t] = in[plist[t / nc] * istride + (size_t)s * nc + t % nc];
-    __syncthreads();
-    for (int q0 = 0; q0 < np; q0 += kPB) {
-      const int cnt = np - q0 < kPB ? np - q0 : kPB;
-      for (int rb = 0; rb < rpw; rb += kRB) {
-        const int i0 = w * rpw + rb;
-        if (i0 >= nc) break;
-        float2 res[kRB][kPB];
-        warp_gemv_multi<kStF32, kRB, kPB>(C + (size_t)s * nc * nc, i0, nc, nc, sm + q0 * nc, nc, cnt, lane, res);
-        if (lane == 0)
-#pragma unroll
-          for (int r = 0; r < kRB; r++) {
-            const int i = i0 + r;
-            if (rb + r < rpw && i < nc)
-#pragma unroll
-              for (int pp = 0; pp < kPB; pp++) {
-                if (pp >= cnt) break;
-                out[plist[q0 + pp] * ostride + (size_t)s * nc + i] = res[r][pp];
-              }
-          }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// w_p = A v_p (w, v: [B][n]) for the listed problems
-template <int ST>
-__device__ void mapply_A(const BArgs& A, unsigned mask, int* plist, cg::grid_group& grid, float2* w, const float2* v,
-                         float2* sm) {
-  const CGArgs& a = A.a;
-  if (a.eo) {
-    msites<kStF32>(A, mask, plist, a.A, nullptr, a.half, 8, false, a.half, a.nsites, A.tB, A.nfull, v, A.n, nullptr, 0,
-                   sm);
-    grid.sync();
-    msites<ST>(A, mask, plist, a.Y, a.Ys, 0, 8, true, 0, a.half, w, A.n, A.tB, A.nfull, v, A.n, sm);
-  } else {
-    msites<kStF32>(A, mask, plist, a.A, nullptr, 0, 9, false, 0, a.nsites, w, A.n, v, A.n, nullptr, 0, sm);
-  }
-}
-
-template <int ST>
-__global__ void __launch_bounds__(kThreads) k_coarse_gcr_batch(BArgs A) {
-  cg::grid_group grid = cg::this_grid();
-  extern __shared__ __align__(16) double dsm[];
-  double* sred = dsm;                        // [8][8]
-  double* tot = sred + 64;                   // own totals [kNR]
-  double* allv = tot + kNR;                  // per-problem values [kMaxBatch]
-  double* stol = allv + kMaxBatch;           // per-problem absolute tolerances [kMaxBatch]
-  double* cc = stol + kMaxBatch;             // own back-substitution coefficients [2 kMaxRestart]
-  int* slist = reinterpret_cast<int*>(cc + 2 * kMaxRestart);        // [kMaxBatch]
-  float2* sm = reinterpret_cast<float2*>(cc + 2 * kMaxRestart + kMaxBatch / 2);   // [B * 9 nc] gather
-  const CGArgs& a = A.a;
-  const int B = A.B, m = a.m;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  // this CTA's problem group (element-wise phases)
-  const int myp = blockIdx.x / A.Gp, gi = blockIdx.x % A.Gp;
-  const bool mine = myp < B;
-  const size_t n = A.n;
-  const size_t chunk = (n + A.Gp - 1) / A.Gp;
-  const size_t e0 = mine ? (size_t)gi * chunk : 0;
-  const size_t e1 = mine ? (e0 + chunk < n ? e0 + chunk : n) : 0;
-  double* beta = A.scal + (mine ? myp : 0) * A.nscal;
-  double* alpha = beta + 2 * (size_t)m * m;
-  double* gam = alpha + 2 * m;
-  const unsigned allm = B >= 32 ? 0xffffffffu : ((1u << B) - 1u);
-  unsigned act = allm, run = 0u;   // bit p: problem p active / running in this cycle
-  long long its_total = 0;
-  double v[4];
-
-  // ---- ||b_p|| (full vectors) and the reduced right-hand sides
-  {
-    const size_t nf = A.nfull;
-    const size_t cf = (nf + A.Gp - 1) / A.Gp;
-    const size_t f0 = mine ? (size_t)gi * cf : 0, f1 = mine ? (f0 + cf < nf ? f0 + cf : nf) : 0;
-    v[0] = 0.0;
-    for (size_t e = f0 + threadIdx.x; e < f1; e += blockDim.x) {
-      const float2 q = A.b[myp * nf + e];
-      v[0] += (double)q.x * q.x + (double)q.y * q.y;
-    }
-    if (mine) own_partials(A, v, 1, RD, myp, gi, sred);
-  }
-  const float2* rhs = A.b;
-  size_t rstride = A.nfull;
-  if (a.eo) {
-    msite_mul(A, act, slist, a.Xinv, a.half, a.nsites, A.tB, A.nfull, A.b, A.nfull, sm);   // t_o = X_o^{-1} b_o
-    grid.sync();
-    msites<ST>(A, act, slist, a.Y, a.Ys, 0, 8, true, 0, a.half, A.br, n, A.tB, A.nfull, A.b, A.nfull, sm);
-    rhs = A.br;
-    rstride = n;
-  }
-  grid.sync();
-  all_totals(A, RD, allv);
-  act = 0u;
-  for (int p = 0; p < B; p++)
-    if (allv[p] > 0.0) act |= 1u << p;
-  if (threadIdx.x < B) stol[threadIdx.x] = a.tol_rel * sqrt(allv[threadIdx.x]);
-  __syncthreads();
-  if (mine)
-    for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      A.y[myp * n + e] = make_float2(0.f, 0.f);
-      A.r[myp * n + e] = rhs[myp * rstride + e];
-    }
-  long long its = 0;
-  grid.sync();
-  while (act && its < a.maxit) {
-    int k = 0, kmy = 0;
-    run = act;
-    while (k < m && its < a.maxit && run) {
-      const bool me = mine && ((run >> myp) & 1u);
-      float2* Wk = A.W + (size_t)k * B * n;
-      float2* Zk = A.Z + (size_t)k * B * n;
-      if (me)
-        for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) Zk[myp * n + e] = A.r[myp * n + e];
-      mapply_A<ST>(A, run, slist, grid, Wk, A.r, sm);
-      grid.sync();
-      // beta_j = <w_j, w> for this CTA's problem: warp wid owns j = wid + u*nw (u < 4)
-      if (me)
-        for (int jb = wid; jb < k; jb += 4 * nw) {
-          double re[4] = {0.0, 0.0, 0.0, 0.0}, im[4] = {0.0, 0.0, 0.0, 0.0};
-          for (size_t e = e0 + lane; e < e1; e += 32) {
-            const float2 x = Wk[myp * n + e];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-              const int j = jb + u * nw;
-              const float2 q = j < k ? A.W[((size_t)j * B + myp) * n + e] : make_float2(0.f, 0.f);
-              re[u] += (double)q.x * x.x + (double)q.y * x.y;
-              im[u] += (double)q.x * x.y - (double)q.y * x.x;
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 4; u++) {
-            const int j = jb + u * nw;
-            const double sr = wsum(re[u]), si = wsum(im[u]);
-            if (lane == 0 && j < k) {
-              A.partials[((size_t)(RA + 2 * j) * B + myp) * A.Gp + gi] = sr;
-              A.partials[((size_t)(RA + 2 * j + 1) * B + myp) * A.Gp + gi] = si;
-            }
-          }
-        }
-      grid.sync();
-      if (me && k) own_totals(A, RA, 2 * k, myp, tot);
-      // w -= sum_j beta_j w_j, then ||w||^2 and <w, r>
-      if (me) {
-        v[0] = v[1] = v[2] = 0.0;
-        for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-          float2 x = Wk[myp * n + e];
-          for (int j = 0; j < k; j++) {
-            const float2 q = A.W[((size_t)j * B + myp) * n + e];
-            const float br = (float)tot[2 * j], bi = (float)tot[2 * j + 1];
-            x.x -= br * q.x - bi * q.y;
-            x.y -= br * q.y + bi * q.x;
-          }
-          Wk[myp * n + e] = x;
-          const float2 rr = A.r[myp * n + e];
-          v[0] += (double)x.x * x.x + (double)x.y * x.y;
-          v[1] += (double)x.x * rr.x + (double)x.y * rr.y;
-          v[2] += (double)x.x * rr.y - (double)x.y * rr.x;
-        }
-        if (gi == 0)
-          for (int j = threadIdx.x; j < k; j += blockDim.x) {
-            beta[(j + (size_t)m * k) * 2] = tot[2 * j];
-            beta[(j + (size_t)m * k) * 2 + 1] = tot[2 * j + 1];
-          }
-        own_partials(A, v, 3, RB, myp, gi, sred);
-      }
-      grid.sync();
-      if (me) {
-        own_totals(A, RB, 3, myp, tot);
-        const double g = tot[0] > 0 ? sqrt(tot[0]) : 1.0;
-        const double ar = tot[1] / g, ai = tot[2] / g;
-        if (gi == 0 && threadIdx.x == 0) {
-          alpha[2 * k] = ar;
-          alpha[2 * k + 1] = ai;
-          gam[k] = g;
-        }
-        const float ig = (float)(1.0 / g), far = (float)ar, fai = (float)ai;
-        v[0] = 0.0;
-        for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-          float2 x = Wk[myp * n + e];
-          x.x *= ig;
-          x.y *= ig;
-          Wk[myp * n + e] = x;
-          float2 rr = A.r[myp * n + e];
-          rr.x -= far * x.x - fai * x.y;
-          rr.y -= far * x.y + fai * x.x;
-          A.r[myp * n + e] = rr;
-          v[0] += (double)rr.x * rr.x + (double)rr.y * rr.y;
-        }
-        own_partials(A, v, 1, RC, myp, gi, sred);
-      }
-      grid.sync();
-      all_totals(A, RC, allv);
-      k++;
-      its++;
-      if (me) kmy = k;
-      its_total += __popc(run);
-      unsigned next = run;
-      for (int p = 0; p < B; p++) {
-        if (!((run >> p) & 1u)) continue;
-        const double rn = sqrt(allv[p]);
-        if (!(rn == rn)) {
-          if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&a.flags[FLAG_NAN], 1);
-          next &= ~(1u << p);
-          act &= ~(1u << p);
-        } else if (rn <= stol[p]) {
-          next &= ~(1u << p);
-        }
-      }
-      run = next;
-    }
-    // back substitution of this CTA's problem and y += sum c_j z_j
-    if (mine && kmy > 0) {
-      if (threadIdx.x == 0) {
-        for (int j = kmy - 1; j >= 0; j--) {
-          double re = alpha[2 * j], im = alpha[2 * j + 1];
-          for (int l = j + 1; l < kmy; l++) {
-            const double br = beta[(j + (size_t)m * l) * 2], bi = beta[(j + (size_t)m * l) * 2 + 1];
-            re -= br * cc[2 * l] - bi * cc[2 * l + 1];
-            im -= br * cc[2 * l + 1] + bi * cc[2 * l];
-          }
-          cc[2 * j] = re / gam[j];
-          cc[2 * j + 1] = im / gam[j];
-        }
-      }
-      __syncthreads();
-      for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        float2 yy = A.y[myp * n + e];
-        double re = yy.x, im = yy.y;
-        for (int j = 0; j < kmy; j++) {
-          const float2 z = A.Z[((size_t)j * B + myp) * n + e];
-          re += cc[2 * j] * z.x - cc[2 * j + 1] * z.y;
-          im += cc[2 * j] * z.y + cc[2 * j + 1] * z.x;
-        }
-        A.y[myp * n + e] = make_float2((float)re, (float)im);
-      }
-    }
-    grid.sync();
-    // true residuals r_p = rhs_p - A y_p of the problems still active
-    mapply_A<ST>(A, act, slist, grid, A.r, A.y, sm);
-    grid.sync();
-    if (mine && ((act >> myp) & 1u)) {
-      v[0] = 0.0;
-      for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const float2 ay = A.r[myp * n + e], bb = rhs[myp * rstride + e];
-        const float2 rr = make_float2(bb.x - ay.x, bb.y - ay.y);
-        A.r[myp * n + e] = rr;
-        v[0] += (double)rr.x * rr.x + (double)rr.y * rr.y;
-      }
-      own_partials(A, v, 1, RD, myp, gi, sred);
-    }
-    grid.sync();
-    all_totals(A, RD, allv);
-    unsigned next = act;
-    for (int p = 0; p < B; p++) {
-      if (!((act >> p) & 1u)) continue;
-      const double rn = sqrt(allv[p]);
-      if (rn <= stol[p] || !(rn == rn)) next &= ~(1u << p);
-    }
-    act = next;
-  }
-  // reconstruction of every problem
-  if (a.eo) {
-    msite_mul(A, allm, slist, a.Xinv, 0, a.half, A.x, A.nfull, A.y, n, sm);                 // x_e = X_e^{-1} y_e
-    grid.sync();
-    msites<ST>(A, allm, slist, a.Y, a.Ys, 0, 8, true, a.half, a.nsites, A.tB, A.nfull, A.x, A.nfull, A.b, A.nfull, sm);
-    grid.sync();                                                                               // t_o = b_o - Y_oe x_e
-    msite_mul(A, allm, slist, a.Xinv, a.half, a.nsites, A.x, A.nfull, A.tB, A.nfull, sm);   // x_o = X_o^{-1} t_o
-  } else if (mine) {
-    for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) A.x[myp * A.nfull + e] = A.y[myp * n + e];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.iters += its_total;
-}
-
-size_t batch_smem(int nc, int nb) {
-  return sizeof(double) * (64 + kNR + 2 * kMaxBatch + 2 * kMaxRestart + kMaxBatch / 2) +
-         sizeof(float2) * (size_t)nb * 9 * nc;
-}
-
 }  // namespace
 
 size_t coarse_gcr_scalars(int m) { return 2 * (size_t)m * m + 5 * (size_t)m + 16; }
@@ -968,94 +531,6 @@ void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuff
                      : C.store == STORE_BF16 ? (const void*)k_coarse_gcr<kStBF16>
                                              : (const void*)k_coarse_gcr<kStF32>;
   MG_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), params, smem, s));
-  MG_LAUNCH();
-}
-
-int coarse_gcr_batch_max() { return kMaxBatch; }
-
-void coarse_gcr_solve_batch(const LevelGeom& G, const CoarseOp& C, CoarseGCRBuffers& Bf, int m, int maxit,
-                            double tol_rel, int nb, const float* b, float* x, long long* d_iters, int* flags,
-                            cudaStream_t s) {
-  if (m > kMaxRestart) raise(MG_ERR_ARG, "coarse restart too long for the persistent solver");
-  if (nb < 1 || nb > kMaxBatch) raise(MG_ERR_ARG, "coarse batch size out of range");
-  const int nc = C.nc;
-  const size_t nfull = (size_t)G.nsites * nc;
-  const size_t n = G.eo ? (size_t)G.half * nc : nfull;
-  const size_t smem = batch_smem(nc, nb);
-  const void* kern = C.store == STORE_F16    ? (const void*)k_coarse_gcr_batch<kStF16>
-                     : C.store == STORE_BF16 ? (const void*)k_coarse_gcr_batch<kStBF16>
-                                             : (const void*)k_coarse_gcr_batch<kStF32>;
-  if (Bf.bcap < nb || Bf.bm != m || Bf.bnb != nb) {
-    // the co-resident grid of the batched kernel for this batch size
-    int dev = 0, sms = 0, per = 0;
-    MG_CUDA(cudaGetDevice(&dev));
-    MG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    MG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kThreads, smem));
-    if (per < 1) raise(MG_ERR_CUDA, "batched coarse GCR cannot be resident");
-    const int most = sms * (per < 4 ? per : 4);
-    // every problem group gets the same number of CTAs
-    int grid = most;
-    const long long sites = G.eo ? G.half : G.nsites;
-    if (sites < grid) grid = (int)(sites > sms ? sites : sms);
-    if (grid > most) grid = most;
-    Bf.bGp = grid / nb;
-    if (Bf.bGp < 1) raise(MG_ERR_ARG, "batch larger than the co-resident grid");
-    Bf.bgrid = grid;
-    Bf.bnb = nb;
-    if (Bf.bcap < nb || Bf.bm != m) {
-      Bf.bnscal = coarse_gcr_scalars(m);
-      Bf.bcap = nb;
-      Bf.bm = m;
-      Bf.bx_r.alloc(sizeof(float2) * n * nb);
-      Bf.bx_y.alloc(sizeof(float2) * n * nb);
-      Bf.bx_br.alloc(sizeof(float2) * n * nb);
-      Bf.bx_tB.alloc(sizeof(float2) * nfull * nb);
-      MG_CUDA(cudaMemset(Bf.bx_tB.get(), 0, sizeof(float2) * nfull * nb));
-      Bf.bx_W.alloc(sizeof(float2) * n * nb * m);
-      Bf.bx_Z.alloc(sizeof(float2) * n * nb * m);
-      Bf.bx_scal.alloc(sizeof(double) * Bf.bnscal * nb);
-    }
-    Bf.bx_part.alloc(sizeof(double) * (size_t)kNR * nb * Bf.bGp);
-  }
-  BArgs A;
-  CGArgs& a = A.a;
-  std::memset(&a, 0, sizeof(a));
-  a.nc = nc;
-  a.half = G.half;
-  a.nsites = G.nsites;
-  a.m = m;
-  a.maxit = maxit;
-  a.eo = G.eo ? 1 : 0;
-  a.tol_rel = tol_rel;
-  a.nbr = G.d_nbr.as<int>();
-  a.Y = C.Y.get();
-  a.Ys = C.Yscale.as<float>();
-  a.X = C.X.as<float2>();
-  a.Xinv = C.Xinv.as<float2>();
-  a.A = C.A.as<float2>();
-  if (!a.A) raise(MG_ERR_STATE, "folded coarse links missing");
-  a.nsplit = 1;
-  a.iters = d_iters;
-  a.flags = flags;
-  A.B = nb;
-  A.Gp = Bf.bGp;
-  A.nfull = nfull;
-  A.n = n;
-  A.b = reinterpret_cast<const float2*>(b);
-  A.x = reinterpret_cast<float2*>(x);
-  A.r = Bf.bx_r.as<float2>();
-  A.y = Bf.bx_y.as<float2>();
-  A.br = Bf.bx_br.as<float2>();
-  A.tB = Bf.bx_tB.as<float2>();
-  A.W = Bf.bx_W.as<float2>();
-  A.Z = Bf.bx_Z.as<float2>();
-  A.partials = Bf.bx_part.as<double>();
-  A.scal = Bf.bx_scal.as<double>();
-  A.nscal = Bf.bnscal;
-  void* params[] = {&A};
-  MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  MG_CUDA(cudaLaunchCooperativeKernel(kern, dim3(Bf.bgrid), dim3(kThreads), params, smem, s));
   MG_LAUNCH();
 }
 

@@ -310,6 +310,16 @@ int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int m
 // nb right-hand sides (ABI vectors, consecutive) solved together by
 // lock-step multigrid-preconditioned FGCR (block.cu)
 int solve_fine_block(Ctx* c, double* psi_abi, const double* eta_abi, int nb, double tol, mg_solve_info* info);
+// right-hand sides of several contexts (lattices) solved together, their
+// coarsest-level solves sharing persistent launches (block.cu)
+struct BlockPart {
+  Ctx* c;
+  int nb;
+  const double* eta;   // nb ABI vectors on the device
+  double* psi;
+  mg_solve_info* info;
+};
+int solve_multi_block(const std::vector<BlockPart>& parts, double tol);
 
 // --------------------------------------------------------------------------- gauge derivative (force.cu)
 // gamma_5 in place on ABI fine vectors (`sites` sites of 12 complex128)
@@ -325,6 +335,12 @@ void mg_destroy_hierarchy(Ctx* c);
 void mg_precondition(Ctx* c, float* z_e, const float* r_e);
 // the same for nb right-hand sides (packed half vectors, stride 24 Vh floats)
 void mg_precondition_batch(Ctx* c, float* z_e, const float* r_e, int nb);
+// mg_precondition_batch in three steps around the coarsest solve, so that
+// several contexts can share one coarsest launch (see multigrid.cu)
+void mg_batch_pre(Ctx* c, float* z_e, const float* r_e, int nb);
+void mg_batch_coarse(Ctx* c, int nb);
+void mg_batch_post(Ctx* c, float* z_e, const float* r_e, int nb);
+bool mg_batch_joinable(Ctx* c);
 // MG_OP_CYCLE of level 0 for nb ABI vectors through mg_precondition_batch
 void mg_cycle_batch(Ctx* c, double* out_abi, const double* in_abi, int nb);
 void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in_abi);

@@ -525,75 +525,123 @@ void mg_build(Ctx* c, mg_setup_info* info) {
 // The cycle of level 0 for nb right-hand sides at once (packed half vectors,
 // stride 24 Vh floats): multi-RHS D_r in the smoother, all coarsest-level
 // solves in one persistent launch per group of up to coarse_gcr_batch_max().
-// Each rhs gets exactly the arithmetic of mg_precondition.
-void mg_precondition_batch(Ctx* c, float* z, const float* r, int nb) {
-  if (!c->mg) raise(MG_ERR_STATE, "multigrid not set up");
-  Hierarchy& H = *c->mg;
-  const mg_params& p = c->params;
-  cudaStream_t s = c->stream;
-  const size_t n = half_n(H, 0), hs = 2 * n;
-  const size_t nfc = full_n(H, 1), cs = 2 * nfc;
-  const TransferOp& T = H.tr[0];
-  BatchWork& bw = H.bw;
-  if (bw.cap < nb) {
-    bw.rc.alloc(sizeof(float) * cs * nb);
-    bw.ec.alloc(sizeof(float) * cs * nb);
-    for (DBuf* d : {&bw.res, &bw.w, &bw.e, &bw.z0}) d->alloc(sizeof(float) * hs * nb);
-    bw.scr.alloc(sizeof(double) * 4 * nb);
-    bw.cap = nb;
-  }
-  float* rc = bw.rc.as<float>();
-  float* ec = bw.ec.as<float>();
-  float* res = bw.res.as<float>();
-  float* w = bw.w.as<float>();
-  float* e = bw.e.as<float>();
-  double* scr = bw.scr.as<double>();
-  auto Drm = [&](float* o, const float* i) { H.F32->Dr_multi(o, i, nb, hs); };
-  auto mr = [&](float* ev, float* rv, int nu) {   // ev = MR_nu(D_r, rv), rv consumed
-    blas_zero<float>(ev, n * nb, s);
-    for (int it = 0; it < nu; it++) {
-      Drm(w, rv);
-      for (int q = 0; q < nb; q++) {
-        blas_dot2<float>(w + q * hs, rv + q * hs, n, scr + 4 * q, c->ws, s);
-        blas_mr_update<float>(ev + q * hs, rv + q * hs, w + q * hs, scr + 4 * q, n, s);
-      }
+// Each rhs gets exactly the arithmetic of mg_precondition.  It is split around
+// the coarsest solve so that several contexts can share that launch:
+// mg_batch_pre (pre-smoothing, restriction to bw.rc), the coarse solve
+// (bw.rc -> bw.ec), mg_batch_post (prolongation, post-smoothing).
+namespace {
+struct BatchCtx {
+  Hierarchy& H;
+  const mg_params& p;
+  cudaStream_t s;
+  size_t n, hs, nfc, cs;
+  BatchCtx(Ctx* c, int nb) : H(*c->mg), p(c->params), s(c->stream) {
+    n = half_n(H, 0);
+    hs = 2 * n;
+    nfc = full_n(H, 1);
+    cs = 2 * nfc;
+    BatchWork& bw = H.bw;
+    if (bw.cap < nb) {
+      bw.rc.alloc(sizeof(float) * cs * nb);
+      bw.ec.alloc(sizeof(float) * cs * nb);
+      for (DBuf* d : {&bw.res, &bw.w, &bw.e, &bw.z0}) d->alloc(sizeof(float) * hs * nb);
+      bw.scr.alloc(sizeof(double) * 4 * nb);
+      bw.cap = nb;
     }
-  };
+  }
+};
+
+// e = MR_nu(D_r, r) for nb rhs (r consumed)
+void batch_mr(Ctx* c, BatchCtx& b, float* ev, float* rv, int nu, int nb) {
+  float* w = b.H.bw.w.as<float>();
+  double* scr = b.H.bw.scr.as<double>();
+  blas_zero<float>(ev, b.n * nb, b.s);
+  for (int it = 0; it < nu; it++) {
+    b.H.F32->Dr_multi(w, rv, nb, b.hs);
+    for (int q = 0; q < nb; q++) {
+      blas_dot2<float>(w + q * b.hs, rv + q * b.hs, b.n, scr + 4 * q, c->ws, b.s);
+      blas_mr_update<float>(ev + q * b.hs, rv + q * b.hs, w + q * b.hs, scr + 4 * q, b.n, b.s);
+    }
+  }
+}
+}  // namespace
+
+void mg_batch_pre(Ctx* c, float* z, const float* r, int nb) {
+  if (!c->mg) raise(MG_ERR_STATE, "multigrid not set up");
+  BatchCtx b(c, nb);
+  BatchWork& bw = b.H.bw;
+  float* res = bw.res.as<float>();
   const float* rin = r;
-  if (p.nu_pre > 0) {
-    blas_convert<float, float>(res, r, n * nb, s);
-    mr(z, res, p.nu_pre);
-    Drm(w, z);
-    blas_convert<float, float>(res, r, n * nb, s);
-    blas_axpby<float>(-1.0, w, 1.0, res, n * nb, s);
+  if (b.p.nu_pre > 0) {
+    float* w = bw.w.as<float>();
+    blas_convert<float, float>(res, r, b.n * nb, b.s);
+    batch_mr(c, b, z, res, b.p.nu_pre, nb);
+    b.H.F32->Dr_multi(w, z, nb, b.hs);
+    blas_convert<float, float>(res, r, b.n * nb, b.s);
+    blas_axpby<float>(-1.0, w, 1.0, res, b.n * nb, b.s);
     rin = res;
   }
-  for (int q = 0; q < nb; q++) restrict_vec(T, rc + q * cs, rin + q * hs, true, s);
-  if (H.L == 2) {
-    const int restart = p.restart_coarse > 0 ? p.restart_coarse : 32;
+  for (int q = 0; q < nb; q++) restrict_vec(b.H.tr[0], bw.rc.as<float>() + q * b.cs, rin + q * b.hs, true, b.s);
+}
+
+bool mg_batch_joinable(Ctx* c) { return c->mg && c->mg->L == 2; }
+
+void mg_batch_systems(Ctx* c, int nb, std::vector<CoarseSystem>& out) {
+  if (!mg_batch_joinable(c)) raise(MG_ERR_STATE, "only 2-level hierarchies join a shared coarsest solve");
+  Hierarchy& H = *c->mg;
+  const size_t cs = 2 * full_n(H, 1);
+  for (int q = 0; q < nb; q++)
+    out.push_back(CoarseSystem{&H.geo[1], &H.cop[1], H.bw.rc.as<float>() + q * cs, H.bw.ec.as<float>() + q * cs,
+                               c->params.tol_coarse, H.d_iters.as<long long>() + 1});
+}
+
+CoarseGCRBuffers& mg_batch_buffers(Ctx* c) { return c->mg->work[1].cg; }
+
+void mg_batch_coarse(Ctx* c, int nb) {
+  BatchCtx b(c, nb);
+  if (b.H.L == 2) {
+    const int restart = b.p.restart_coarse > 0 ? b.p.restart_coarse : 32;
     const int gmax = coarse_gcr_batch_max();
+    std::vector<CoarseSystem> sys;
+    mg_batch_systems(c, nb, sys);
     for (int q0 = 0; q0 < nb; q0 += gmax) {
-      const int g = nb - q0 < gmax ? nb - q0 : gmax;
-      coarse_gcr_solve_batch(H.geo[1], H.cop[1], H.work[1].cg, restart, p.maxit_coarse, p.tol_coarse, g,
-                             rc + q0 * cs, ec + q0 * cs, H.d_iters.as<long long>() + 1, c->ws.flags.as<int>(), s);
+      std::vector<CoarseSystem> part(sys.begin() + q0, sys.begin() + std::min(nb, q0 + gmax));
+      coarse_gcr_solve_multi(part, b.H.work[1].cg, restart, b.p.maxit_coarse, c->ws.flags.as<int>(), b.s);
     }
   } else {
-    for (int q = 0; q < nb; q++) coarse_solve(c, H, 1, ec + q * cs, rc + q * cs);
+    for (int q = 0; q < nb; q++)
+      coarse_solve(c, b.H, 1, b.H.bw.ec.as<float>() + q * b.cs, b.H.bw.rc.as<float>() + q * b.cs);
   }
-  if (p.nu_pre > 0) {
+}
+
+void mg_batch_post(Ctx* c, float* z, const float* r, int nb) {
+  BatchCtx b(c, nb);
+  BatchWork& bw = b.H.bw;
+  const TransferOp& T = b.H.tr[0];
+  float* ec = bw.ec.as<float>();
+  if (b.p.nu_pre > 0) {
     float* z0 = bw.z0.as<float>();
-    for (int q = 0; q < nb; q++) prolong_vec(T, z0 + q * hs, ec + q * cs, true, s);
-    blas_axpby<float>(1.0, z0, 1.0, z, n * nb, s);
+    for (int q = 0; q < nb; q++) prolong_vec(T, z0 + q * b.hs, ec + q * b.cs, true, b.s);
+    blas_axpby<float>(1.0, z0, 1.0, z, b.n * nb, b.s);
   } else {
-    for (int q = 0; q < nb; q++) prolong_vec(T, z + q * hs, ec + q * cs, true, s);
+    for (int q = 0; q < nb; q++) prolong_vec(T, z + q * b.hs, ec + q * b.cs, true, b.s);
   }
-  if (p.nu_post > 0) {
-    Drm(w, z);
-    blas_convert<float, float>(res, r, n * nb, s);
-    blas_axpby<float>(-1.0, w, 1.0, res, n * nb, s);
-    mr(e, res, p.nu_post);
-    blas_axpby<float>(1.0, e, 1.0, z, n * nb, s);
+  if (b.p.nu_post > 0) {
+    float* w = bw.w.as<float>();
+    float* res = bw.res.as<float>();
+    float* e = bw.e.as<float>();
+    b.H.F32->Dr_multi(w, z, nb, b.hs);
+    blas_convert<float, float>(res, r, b.n * nb, b.s);
+    blas_axpby<float>(-1.0, w, 1.0, res, b.n * nb, b.s);
+    batch_mr(c, b, e, res, b.p.nu_post, nb);
+    blas_axpby<float>(1.0, e, 1.0, z, b.n * nb, b.s);
   }
+}
+
+void mg_precondition_batch(Ctx* c, float* z, const float* r, int nb) {
+  mg_batch_pre(c, z, r, nb);
+  mg_batch_coarse(c, nb);
+  mg_batch_post(c, z, r, nb);
 }
 
 void mg_cycle_batch(Ctx* c, double* out_abi, const double* in_abi, int nb) {

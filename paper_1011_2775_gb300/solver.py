@@ -11,6 +11,17 @@ import numpy as np
 from . import binding as B
 
 
+def solve_batch(solvers, etas, tol: float = 1e-10, outs=None):
+    """Solve several lattices together (``mg_solve_batch``): ``etas[i]`` holds the
+    right-hand sides of ``solvers[i]`` (shape ``(nrhs_i, Lt, Lz, Ly, Lx, 4, 3)``
+    or a single source).  Returns ``(outs, infos)``."""
+    if outs is None:
+        outs = [e.new_zeros(e.shape) if not isinstance(e, np.ndarray) else np.zeros_like(e) for e in etas]
+    nrhs = [1 if e.ndim == 6 else e.shape[0] for e in etas]
+    st, infos = B.mg_solve_batch([s.ctx for s in solvers], outs, etas, nrhs, tol)
+    return outs, infos
+
+
 class Solver:
     """``[D(U) + m] psi = eta`` on one lattice ``dims = (Lx, Ly, Lz, Lt)``."""
 

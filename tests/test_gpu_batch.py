@@ -9,6 +9,9 @@
 * The lock-step block solve (mg_solve, rhs_block > 1): every right-hand side
   reaches ||eta - D psi|| / ||eta|| <= 1e-10 with the oracle's D, including a
   zero right-hand side, and agrees with one-at-a-time solves.
+* mg_solve_batch: several lattices of uneven size solved together, their
+  coarsest-level solves sharing persistent launches; every solution against
+  the oracle's D of its lattice and against that context's own mg_solve.
 * The multi-RHS benchmark entry point reports its byte model.
 """
 import numpy as np
@@ -99,8 +102,7 @@ def test_block_solve_matches_sequential_and_oracle():
         res = eta[q].reshape(W.shape + (12,)) - W.D(psi[q].reshape(W.shape + (12,)))
         assert np.sqrt(norm2(res) / norm2(eta[q])) <= 1e-10, q
     assert info.true_residual <= 1e-10
-    S.set_params(rhs_block=1)                     # one after another (invalidates the setup)
-    S.setup()
+    S.set_params(rhs_block=1)                     # one after another (the setup is kept)
     seq, sinfo = S.solve(eta, 1e-10, B.MG_MODE_MG)
     for q in (0, 1, 3):
         assert np.linalg.norm((psi[q] - seq[q]).ravel()) / np.linalg.norm(seq[q].ravel()) < 1e-7, q
@@ -139,4 +141,55 @@ def test_multi_rhs_benchmark_byte_model():
         for nrhs in (1, 4):
             ms, by = B.mg_benchmark_kernel_nrhs(S.ctx, k, B.MG_FP32, nrhs, 2, 5)
             assert ms > 0 and by == per(nrhs) * 4 * vh
+    S.close()
+
+
+def test_solve_batch_several_lattices():
+    """mg_solve_batch: three lattices of uneven size (one with odd coarse extents,
+    so its coarsest solves take a launch of their own) and 18 right-hand sides in
+    all (two groups of up to 16); every solution reaches the tolerance with the
+    oracle's D of its lattice and agrees with that context's own mg_solve."""
+    from paper_1011_2775_gb300 import binding as B
+    from paper_1011_2775_gb300.solver import solve_batch
+    specs = [((8, 8, 8, 8), (2, 2, 2, 2), 8, 9, 0.3, -0.1, 7501),
+             ((8, 8, 8, 16), (4, 4, 4, 4), 12, 5, 1.0, -0.6, 7502),
+             ((6, 4, 4, 8), (2, 2, 2, 2), 8, 4, 0.4, -0.15, 7503)]
+    solvers, etas, ops = [], [], []
+    for dims, blk, nv, nrhs, eps, m0, seed in specs:
+        ape = 5 if eps >= 1.0 else 1
+        U = I.make_gauge(dims, eps, ape, 0.5, seed)
+        S = _solver(dims, U, 1.0, m0)
+        S.set_params(levels=2, blocks=[blk], nv=[nv], seed=seed + 1, maxit_fine=2000)
+        S.setup()
+        solvers.append(S)
+        etas.append(I.gaussian_source(dims, seed + 2, nrhs=nrhs))
+        ops.append(WilsonClover(U, 1.0, m0))
+    outs, infos = solve_batch(solvers, etas, 1e-10)
+    for S, eta, psi, W, info in zip(solvers, etas, outs, ops, infos):
+        for q in range(eta.shape[0]):
+            res = eta[q].reshape(W.shape + (12,)) - W.D(psi[q].reshape(W.shape + (12,)))
+            assert np.sqrt(norm2(res) / norm2(eta[q])) <= 1e-10
+        assert info.true_residual <= 1e-10 and info.coarse_iterations[1] > 0
+        own, _ = S.solve(eta, 1e-10, B.MG_MODE_MG)
+        for q in range(eta.shape[0]):
+            assert np.linalg.norm((psi[q] - own[q]).ravel()) / np.linalg.norm(own[q].ravel()) < 1e-7
+    for S in solvers:
+        S.close()
+
+
+def test_solve_batch_rejects_bad_input():
+    from paper_1011_2775_gb300 import binding as B
+    dims = (4, 4, 4, 4)
+    U = I.make_gauge(dims, 0.3, 0, 0.5, 7601)
+    S = _solver(dims, U, 1.0, -0.1)
+    eta = I.gaussian_source(dims, 7602)
+    psi = np.zeros_like(eta)
+    with pytest.raises(B.MGError) as e:          # no setup
+        B.mg_solve_batch([S.ctx], [psi], [eta], [1], 1e-10)
+    assert e.value.status == B.MG_ERR_STATE
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[8])
+    S.setup()
+    with pytest.raises(B.MGError) as e:          # the same context twice
+        B.mg_solve_batch([S.ctx, S.ctx], [psi, psi.copy()], [eta, eta], [1, 1], 1e-10)
+    assert e.value.status == B.MG_ERR_ARG
     S.close()
