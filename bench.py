@@ -405,6 +405,17 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
                                                    "FP64 hop and clover link derivative"}
     del eta_d, U_d, chi_d, psi, lam, loss
 
+    # ---- the 2-level cycle replayed as a CUDA graph (default) against direct launches
+    e_g = torch.from_numpy(eta).to(f"cuda:{dev}")
+    p_g = torch.zeros_like(e_g)
+    tg = {}
+    for flag in (0, 1):
+        S.set_params(cuda_graphs=flag)
+        S.solve(e_g, TOL, B.MG_MODE_MG, out=p_g)     # warm-up (and capture)
+        tg[flag] = statistics.median(timed(lambda: S.solve(e_g, TOL, B.MG_MODE_MG, out=p_g))[0] for _ in range(3))
+    out["cuda_graph"] = {"graph_ms": tg[1], "direct_launch_ms": tg[0], "speedup": tg[0] / tg[1]}
+    del e_g, p_g
+
     # ---- FP16 storage of P and the coarse links
     Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
     Q.load_gauge(U)
@@ -424,6 +435,75 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     return out
 
 
+# Batched sources on lattices of uneven size (the batching workload): 12 point
+# sources on 32^3x64, 8 Gaussian sources each on 16^3x32 and 24^3x48, the same
+# gauge construction, m0 = -0.3, 2-level MG with 4^4 blocks and Nv = 24.
+MULTI = [((32, 32, 32, 64), "point", 12), ((16, 16, 16, 32), "gauss", 8), ((24, 24, 24, 48), "gauss", 8)]
+MULTI_M0 = -0.3
+
+
+def run_multi(dev: int) -> dict:
+    """All 28 right-hand sides through mg_solve_batch (lock-step, shared coarsest
+    launches) against each lattice's own block solve and against 28 solves one
+    after another; every time is CUDA events on the one stream all contexts use."""
+    import numpy as np
+    import torch
+    from paper_1011_2775_gb300 import binding as B
+    from paper_1011_2775_gb300 import inputs as I
+    from paper_1011_2775_gb300.solver import Solver, solve_batch
+
+    stream = torch.cuda.current_stream(dev)
+    solvers, etas, outs, setup_ms = [], [], [], []
+    for k, (dims, kind, nrhs) in enumerate(MULTI):
+        U = I.make_gauge(dims, EPS, APE, ALPHA, 4001 + 10 * k)
+        S = Solver(dims, device=dev, stream=stream.cuda_stream)
+        S.load_gauge(U)
+        del U
+        S.set_clover(CSW, MULTI_M0)
+        S.set_params(seed=4003 + 10 * k, maxit_fine=2000, **MG)
+        t0 = time.perf_counter()
+        S.setup()
+        setup_ms.append(1e3 * (time.perf_counter() - t0))
+        if kind == "point":
+            e = np.stack([I.point_source(dims, a) for a in range(nrhs)])
+        else:
+            e = I.gaussian_source(dims, 4002 + 10 * k, nrhs=nrhs)
+        etas.append(torch.from_numpy(e).to(f"cuda:{dev}"))
+        outs.append(torch.zeros_like(etas[-1]))
+        solvers.append(S)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    solve_batch(solvers, etas, TOL, outs)                        # warm-up (allocations, autotuning)
+    t_all, (_, infos) = timed(lambda: solve_batch(solvers, etas, TOL, outs))
+    t_lat = []
+    for S, e, o in zip(solvers, etas, outs):
+        t, _ = timed(lambda: S.solve(e, TOL, B.MG_MODE_MG, out=o))
+        t_lat.append(t)
+    t_seq = []
+    for S, e, o in zip(solvers, etas, outs):
+        S.set_params(rhs_block=1)
+        t, (_, si) = timed(lambda: S.solve(e, TOL, B.MG_MODE_MG, out=o))
+        t_seq.append(t)
+        S.set_params(rhs_block=16)
+    out = {"lattices": [f"{d[0]}^3x{d[3]} x{n} {kind}" for d, kind, n in MULTI], "m0": MULTI_M0,
+           "all_in_one_ms": t_all, "per_lattice_block_ms": t_lat, "one_at_a_time_ms": t_seq,
+           "speedup_vs_one_at_a_time": sum(t_seq) / t_all, "speedup_vs_per_lattice_blocks": sum(t_lat) / t_all,
+           "outer_iterations": [i.outer_iterations for i in infos],
+           "true_residual_max": max(i.true_residual for i in infos), "setup_ms": setup_ms}
+    for S in solvers:
+        S.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -434,6 +514,8 @@ def main():
     ap.add_argument("--no-eo", action="store_true", help="skip the plain EO-GCR comparison")
     ap.add_argument("--eo-maxit", type=int, default=20000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--multi", action="store_true",
+                    help="also solve the batched sources on three lattices of uneven size (about a minute)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FP16-storage, gradient and multi-RHS D_r measurements")
     ap.add_argument("--profile", choices=["solve", "block", "dslash", "dslash_mrhs"],
@@ -477,6 +559,8 @@ def main():
         return
 
     r = run_gpu(args, dist)
+    if args.multi:
+        r["extra"]["multi_lattice"] = run_multi(dist.local)
     info = r["info"]
     dr_per_solve = info.dslash_launches / 2.0
     k = r["kern"]["dslash_clover_fp32"]

@@ -125,6 +125,8 @@ typedef struct {
   uint64_t seed;                  /* Philox4x32-10 key of the setup's random start vectors       */
   int rhs_block;                  /* mg_solve (MG mode): right-hand sides solved together in      */
                                   /* lock-step, 1..16 (1: one after another)                      */
+  int cuda_graphs;                /* 1: replay the 2-level cycle of a single-rhs solve as a        */
+                                  /* captured CUDA graph (0: launch its kernels one by one)        */
 } mg_params;
 
 typedef struct {
@@ -163,7 +165,7 @@ MG_API const char* mg_last_error(void);
 /* Fill `p` with the defaults: 2 levels, 4^4 blocks, Nv = 24, 20 passes of 8
  * GCR iterations, RQ tolerance 0.05, nu_post = 4, coarse tolerance 0.1,
  * coarse restart 32 / cap 50, outer restart 16 / cap 500, FP32 storage,
- * Galerkin projection of D_p, seed 3, rhs_block 16. */
+ * Galerkin projection of D_p, seed 3, rhs_block 16, cuda_graphs 1. */
 MG_API int mg_default_params(mg_params* p);
 
 /* Create a context for a lattice of `dims` on CUDA device `device`; kernels
@@ -244,7 +246,9 @@ MG_API int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol,
  * 2-level contexts into shared persistent launches (up to 16 systems and 8
  * lattices each; contexts whose hierarchy is deeper, or whose coarse storage,
  * restart or cap differ from the first's, solve their own).  Right-hand sides
- * are taken in context order in groups of the first context's rhs_block.
+ * are taken in context order in groups of at most the first context's
+ * rhs_block (a context's right-hand sides are not split when they fit in a
+ * fresh group).
  * The contexts need the same restart_fine.  `where` applies to every buffer;
  * infos (may be NULL) receives one mg_solve_info per context, solve_ms and
  * kernel_launches being those of the whole call.  An extension of the paper's

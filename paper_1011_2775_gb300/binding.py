@@ -59,7 +59,8 @@ class mg_params(ctypes.Structure):
                 ("storage", ctypes.c_int),
                 ("coarse_op", ctypes.c_int),
                 ("seed", ctypes.c_uint64),
-                ("rhs_block", ctypes.c_int)]
+                ("rhs_block", ctypes.c_int),
+                ("cuda_graphs", ctypes.c_int)]
 
 
 class mg_setup_info(ctypes.Structure):

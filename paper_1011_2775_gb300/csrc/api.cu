@@ -184,6 +184,7 @@ int mg_default_params(mg_params* p) {
   p->coarse_op = MG_COARSE_DP;
   p->seed = 3;
   p->rhs_block = 16;
+  p->cuda_graphs = 1;
   return MG_OK;
 }
 
@@ -282,6 +283,7 @@ int mg_set_params(void* ctx, const mg_params* p) {
     if (p->storage < MG_STORE_FP32 || p->storage > MG_STORE_BF16) mg::raise(MG_ERR_ARG, "bad storage");
     if (p->coarse_op != MG_COARSE_DP && p->coarse_op != MG_COARSE_D) mg::raise(MG_ERR_ARG, "bad coarse_op");
     if (p->rhs_block < 1 || p->rhs_block > 16) mg::raise(MG_ERR_ARG, "rhs_block must be in [1, 16]");
+    if (p->cuda_graphs != 0 && p->cuda_graphs != 1) mg::raise(MG_ERR_ARG, "cuda_graphs must be 0 or 1");
     int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
     int ndof = 12;
     for (int l = 0; l + 1 < p->levels; l++) {
@@ -444,6 +446,8 @@ int mg_solve_batch(void* const* ctxs, int nctx, void* const* psi, const void* co
     };
     for (int i = 0; i < nctx; i++) {
       int q = 0;
+      // a context's right-hand sides stay in one group when they fit in a fresh one
+      if (used > 0 && used + nrhs[i] > cap && nrhs[i] <= cap) flush();
       while (q < nrhs[i]) {
         const int take = std::min(nrhs[i] - q, cap - used);
         mg::Ctx* c = cs[i];

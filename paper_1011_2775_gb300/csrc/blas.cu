@@ -182,6 +182,71 @@ __global__ void k_dot2(const cx<T>* __restrict__ w, const cx<T>* __restrict__ r,
   double v[3] = {(double)s0, (double)s1, (double)s2};
   grid_reduce<3>(v, partials, counter, out);
 }
+// nrhs pairs (w_q, r_q) at `stride` complex apart: d_out[4q .. 4q+2] per pair,
+// one launch (blockIdx.y = q, a separate reduction per pair)
+template <typename T>
+__global__ void k_dot2_multi(const cx<T>* __restrict__ w, const cx<T>* __restrict__ r, size_t n, size_t stride,
+                             double* partials, unsigned* counters, double* out) {
+  const int q = blockIdx.y;
+  w += q * stride;
+  r += q * stride;
+  acc_t<T> s0 = 0, s1 = 0, s2 = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    cx<T> a = w[i], b = r[i];
+    s0 = fma((acc_t<T>)a.re, (acc_t<T>)a.re, s0);
+    s0 = fma((acc_t<T>)a.im, (acc_t<T>)a.im, s0);
+    s1 = fma((acc_t<T>)a.re, (acc_t<T>)b.re, s1);
+    s1 = fma((acc_t<T>)a.im, (acc_t<T>)b.im, s1);
+    s2 = fma((acc_t<T>)a.re, (acc_t<T>)b.im, s2);
+    s2 = fma(-(acc_t<T>)a.im, (acc_t<T>)b.re, s2);
+  }
+  double v[3] = {(double)s0, (double)s1, (double)s2};
+  grid_reduce<3>(v, partials + (size_t)q * gridDim.x * 3, counters + q, out + 4 * q);
+}
+template <typename T>
+void blas_dot2_multi(const T* w, const T* r, size_t n, size_t stride, int nrhs, double* d_out, Workspace& ws,
+                     cudaStream_t s) {
+  if (nrhs > Workspace::kMultiCounters) raise(MG_ERR_ARG, "too many vectors for one multi-reduction");
+  int g = red_grid(n);
+  const int cap = Workspace::kMaxBlocks * Workspace::kMaxResults / (3 * nrhs);
+  if (g > cap) g = cap;
+  k_dot2_multi<T><<<dim3(g, nrhs), kBS, 0, s>>>((const cx<T>*)w, (const cx<T>*)r, n, stride / 2,
+                                                 ws.partials.as<double>(), ws.mcounters.as<unsigned>(), d_out);
+  MG_LAUNCH();
+}
+
+template <typename T>
+__global__ void k_mr_update_multi(cx<T>* e, cx<T>* r, const cx<T>* __restrict__ w, const double* __restrict__ in,
+                                  size_t n, size_t stride) {
+  const int q = blockIdx.y;
+  e += q * stride;
+  r += q * stride;
+  w += q * stride;
+  in += 4 * q;
+  const double ww = in[0] > 0 ? in[0] : 1.0;
+  const T ar = (T)(in[1] / ww), ai = (T)(in[2] / ww);
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    cx<T> rv = r[i], wv = w[i], ev = e[i];
+    ev.re += ar * rv.re - ai * rv.im;
+    ev.im += ar * rv.im + ai * rv.re;
+    rv.re -= ar * wv.re - ai * wv.im;
+    rv.im -= ar * wv.im + ai * wv.re;
+    e[i] = ev;
+    r[i] = rv;
+  }
+}
+template <typename T>
+void blas_mr_update_multi(T* e, T* r, const T* w, const double* d_in, size_t n, size_t stride, int nrhs,
+                          cudaStream_t s) {
+  int g = ew_grid(n);
+  if (g * nrhs > 152 * 16) g = (152 * 16 + nrhs - 1) / nrhs;
+  k_mr_update_multi<T><<<dim3(g, nrhs), kBS, 0, s>>>((cx<T>*)e, (cx<T>*)r, (const cx<T>*)w, d_in, n, stride / 2);
+  MG_LAUNCH();
+}
+template void blas_dot2_multi<float>(const float*, const float*, size_t, size_t, int, double*, Workspace&, cudaStream_t);
+template void blas_mr_update_multi<float>(float*, float*, const float*, const double*, size_t, size_t, int,
+                                          cudaStream_t);
+
 template <typename T>
 void blas_dot2(const T* w, const T* r, size_t n, double* d_out, Workspace& ws, cudaStream_t s) {
   k_dot2<T><<<red_grid(n), kBS, 0, s>>>((const cx<T>*)w, (const cx<T>*)r, n, ws.partials.as<double>(),

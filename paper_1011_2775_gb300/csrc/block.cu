@@ -120,9 +120,9 @@ void read_norms(Run& R, const double* ve, const double* vo, const std::vector<ch
 
 // the cycle for every run, with the coarsest solves of the joinable runs in
 // shared launches (the others solve their own)
-void precondition_all(std::vector<Run>& runs, int k) {
+void precondition_all(std::vector<Run*>& runs, int k) {
   std::vector<Run*> joint, own;
-  for (Run& R : runs) (mg_batch_joinable(R.c) ? joint : own).push_back(&R);
+  for (Run* R : runs) (mg_batch_joinable(R->c) ? joint : own).push_back(R);
   // runs that can share a launch: same device, coarse storage, restart, cap and even-odd structure
   std::vector<Run*> shared, alone = own;
   for (Run* R : joint) {
@@ -136,11 +136,11 @@ void precondition_all(std::vector<Run>& runs, int k) {
                     a.restart_coarse == b.restart_coarse && a.maxit_coarse == b.maxit_coarse;
     (ok ? shared : alone).push_back(R);
   }
-  for (Run& R : runs) {
-    float* zk = R.B->Z[k].as<float>();
-    float* r32 = R.B->r32.as<float>();
-    blas_convert<double, float>(r32, R.B->r.as<double>(), R.n * R.nb, R.c->stream);
-    mg_batch_pre(R.c, zk, r32, R.nb);
+  for (Run* R : runs) {
+    float* zk = R->B->Z[k].as<float>();
+    float* r32 = R->B->r32.as<float>();
+    blas_convert<double, float>(r32, R->B->r.as<double>(), R->n * R->nb, R->c->stream);
+    mg_batch_pre(R->c, zk, r32, R->nb);
   }
   for (Run* R : alone) mg_batch_coarse(R->c, R->nb);
   if (!shared.empty()) {
@@ -189,7 +189,7 @@ void precondition_all(std::vector<Run>& runs, int k) {
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
     cudaEventDestroy(done);
   }
-  for (Run& R : runs) mg_batch_post(R.c, R.B->Z[k].as<float>(), R.B->r32.as<float>(), R.nb);
+  for (Run* R : runs) mg_batch_post(R->c, R->B->Z[k].as<float>(), R->B->r32.as<float>(), R->nb);
 }
 
 int solve_runs(std::vector<Run>& runs, double tol) {
@@ -242,8 +242,13 @@ int solve_runs(std::vector<Run>& runs, double tol) {
         if (it >= R.maxit) std::fill(R.run.begin(), R.run.end(), 0);
       }
       while (k < m && it < maxit && any_running()) {
-        precondition_all(runs, k);
-        for (Run& R : runs) {
+        // contexts whose right-hand sides have all stopped drop out of the iteration
+        std::vector<Run*> live;
+        for (Run& R : runs)
+          if (any_of(R.run)) live.push_back(&R);
+        precondition_all(live, k);
+        for (Run* Rp : live) {
+          Run& R = *Rp;
           BlockBuffers& B = *R.B;
           Ctx* c = R.c;
           double* wk = B.W[k].as<double>();
@@ -262,7 +267,8 @@ int solve_runs(std::vector<Run>& runs, double tol) {
                                   B.rn2.as<double>() + 2 * q, c->ws, c->stream);
           }
         }
-        for (Run& R : runs) {
+        for (Run* Rp : live) {
+          Run& R = *Rp;
           MG_CUDA(cudaMemcpyAsync(R.h.data(), R.B->rn2.as<double>(), sizeof(double) * 2 * R.nb,
                                   cudaMemcpyDeviceToHost, R.c->stream));
           R.c->sync();
@@ -279,6 +285,7 @@ int solve_runs(std::vector<Run>& runs, double tol) {
         it++;
       }
       for (Run& R : runs) {
+        if (!any_of(R.active)) continue;   // nothing changed since its last check
         BlockBuffers& B = *R.B;
         Ctx* c = R.c;
         double* y = B.y.as<double>();

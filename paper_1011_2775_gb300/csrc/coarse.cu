@@ -123,9 +123,12 @@ __device__ __forceinline__ float warp_sumf(float v) {
 // in flight at a time.  Per-warp sums are combined in FP64 at the end.
 template <int ST>
 __global__ void __launch_bounds__(256) k_restrict(TArgs a, float* __restrict__ out, const float* __restrict__ v,
-                                                  int even_only) {
+                                                  int even_only, int nrhs, size_t vstride, size_t cstride) {
   extern __shared__ float2 sacc[];  // [nwarps][2 nv]
-  const int cc = blockIdx.x;
+  // one CTA per (coarse site, rhs), rhs fastest: the CTAs of a site share its P rows in L2
+  const int cc = blockIdx.x / nrhs, rq = blockIdx.x % nrhs;
+  v += rq * vstride;
+  out += rq * cstride;
   const int nv = a.nv, hd = a.ndof / 2;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   float acc[2][2][2] = {};  // [k-half][chirality][re, im]
@@ -172,22 +175,31 @@ __global__ void __launch_bounds__(256) k_restrict(TArgs a, float* __restrict__ o
   }
 }
 
-void restrict_vec(const TransferOp& T, float* out_c, const float* v, bool even_only, cudaStream_t s) {
+void restrict_vec_multi(const TransferOp& T, int nrhs, float* out_c, size_t cstride, const float* v, size_t vstride,
+                        bool even_only, cudaStream_t s) {
   TArgs a = targs(T);
   const size_t sm = sizeof(float2) * (kBS / 32) * 2 * (size_t)T.nv;
+  const unsigned grid = (unsigned)((size_t)T.ncoarse * nrhs);
   switch (T.store) {
-    case STORE_F32: k_restrict<STORE_F32><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
-    case STORE_F16: k_restrict<STORE_F16><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
-    default: k_restrict<STORE_BF16><<<T.ncoarse, kBS, sm, s>>>(a, out_c, v, even_only); break;
+    case STORE_F32: k_restrict<STORE_F32><<<grid, kBS, sm, s>>>(a, out_c, v, even_only, nrhs, vstride, cstride); break;
+    case STORE_F16: k_restrict<STORE_F16><<<grid, kBS, sm, s>>>(a, out_c, v, even_only, nrhs, vstride, cstride); break;
+    default: k_restrict<STORE_BF16><<<grid, kBS, sm, s>>>(a, out_c, v, even_only, nrhs, vstride, cstride); break;
   }
   MG_LAUNCH();
 }
 
+void restrict_vec(const TransferOp& T, float* out_c, const float* v, bool even_only, cudaStream_t s) {
+  restrict_vec_multi(T, 1, out_c, 0, v, 0, even_only, s);
+}
+
 // --------------------------------------------------------------------------- prolongation
 template <int ST>
-__global__ void k_prolong(TArgs a, float* __restrict__ v, const float* __restrict__ in_c, int even_only) {
+__global__ void k_prolong(TArgs a, float* __restrict__ v, const float* __restrict__ in_c, int even_only, int nrhs,
+                          size_t vstride, size_t cstride) {
   extern __shared__ float2 svc[];  // [2 nv]
-  const int cc = blockIdx.x;
+  const int cc = blockIdx.x / nrhs, rq = blockIdx.x % nrhs;   // (coarse site, rhs), rhs fastest
+  v += rq * vstride;
+  in_c += rq * cstride;
   const int nv = a.nv, hd = a.ndof / 2;
   for (int t = threadIdx.x; t < 2 * nv; t += blockDim.x)
     svc[t] = reinterpret_cast<const float2*>(in_c)[(size_t)cc * 2 * nv + t];
@@ -211,15 +223,21 @@ __global__ void k_prolong(TArgs a, float* __restrict__ v, const float* __restric
   }
 }
 
-void prolong_vec(const TransferOp& T, float* v, const float* in_c, bool even_only, cudaStream_t s) {
+void prolong_vec_multi(const TransferOp& T, int nrhs, float* v, size_t vstride, const float* in_c, size_t cstride,
+                       bool even_only, cudaStream_t s) {
   TArgs a = targs(T);
   const size_t sm = sizeof(float2) * 2 * T.nv;
+  const unsigned grid = (unsigned)((size_t)T.ncoarse * nrhs);
   switch (T.store) {
-    case STORE_F32: k_prolong<STORE_F32><<<T.ncoarse, kBS, sm, s>>>(a, v, in_c, even_only); break;
-    case STORE_F16: k_prolong<STORE_F16><<<T.ncoarse, kBS, sm, s>>>(a, v, in_c, even_only); break;
-    default: k_prolong<STORE_BF16><<<T.ncoarse, kBS, sm, s>>>(a, v, in_c, even_only); break;
+    case STORE_F32: k_prolong<STORE_F32><<<grid, kBS, sm, s>>>(a, v, in_c, even_only, nrhs, vstride, cstride); break;
+    case STORE_F16: k_prolong<STORE_F16><<<grid, kBS, sm, s>>>(a, v, in_c, even_only, nrhs, vstride, cstride); break;
+    default: k_prolong<STORE_BF16><<<grid, kBS, sm, s>>>(a, v, in_c, even_only, nrhs, vstride, cstride); break;
   }
   MG_LAUNCH();
+}
+
+void prolong_vec(const TransferOp& T, float* v, const float* in_c, bool even_only, cudaStream_t s) {
+  prolong_vec_multi(T, 1, v, 0, in_c, 0, even_only, s);
 }
 
 // --------------------------------------------------------------------------- column extraction

@@ -90,6 +90,11 @@ void coarse_fold_links(const LevelGeom& G, CoarseOp& C, cudaStream_t s);
 void restrict_vec(const TransferOp& T, float* out_c, const float* v, bool even_only, cudaStream_t s);
 // v = P in_c; even_only: only even sites of v are written
 void prolong_vec(const TransferOp& T, float* v, const float* in_c, bool even_only, cudaStream_t s);
+// the same for nrhs vectors (strides in floats), one launch
+void restrict_vec_multi(const TransferOp& T, int nrhs, float* out_c, size_t cstride, const float* v, size_t vstride,
+                        bool even_only, cudaStream_t s);
+void prolong_vec_multi(const TransferOp& T, int nrhs, float* v, size_t vstride, const float* in_c, size_t cstride,
+                       bool even_only, cudaStream_t s);
 // p = column (chir, k) of P as a whole-lattice vector of the fine level
 void extract_column(const TransferOp& T, float* p, int chir, int k, cudaStream_t s);
 // Galerkin accumulation of one column: W[0..7] directional hops of u = M^{-1} p,

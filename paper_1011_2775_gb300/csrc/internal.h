@@ -27,6 +27,8 @@ void cuda_check(cudaError_t e, const char* expr, const char* file, int line);
 // only; no sync)
 void launch_check(const char* file, int line);
 long long launches_so_far();
+// adjusts the launch count (kernels a CUDA-graph replay runs, or captured ones that did not run)
+void add_launches(long long n);
 #define MG_CUDA(expr) ::mg::cuda_check((expr), #expr, __FILE__, __LINE__)
 #define MG_LAUNCH() ::mg::launch_check(__FILE__, __LINE__)
 
@@ -68,6 +70,8 @@ struct Workspace {
   DBuf counter;                                // unsigned, self-resetting
   DBuf scalars;                                // doubles
   DBuf flags;                                  // int[16]
+  static constexpr int kMultiCounters = 64;    // separate reductions in one launch (multi-RHS)
+  DBuf mcounters;                              // unsigned[kMultiCounters], self-resetting
   double* host = nullptr;                      // pinned mirror of the first scalars
   void init();
   ~Workspace();
@@ -156,6 +160,14 @@ void blas_normalize(T* x, const double* d_norm2, size_t n, cudaStream_t s);
 // {<w,w>, Re<w,r>, Im<w,r>} -> d_out
 template <typename T>
 void blas_dot2(const T* w, const T* r, size_t n, double* d_out, Workspace& ws, cudaStream_t s);
+// the same for nrhs pairs at `stride` reals apart: d_out[4q .. 4q+2] (one launch)
+template <typename T>
+void blas_dot2_multi(const T* w, const T* r, size_t n, size_t stride, int nrhs, double* d_out, Workspace& ws,
+                     cudaStream_t s);
+// blas_mr_update for nrhs triples at `stride` reals apart with d_in[4q ..] (one launch)
+template <typename T>
+void blas_mr_update_multi(T* e, T* r, const T* w, const double* d_in, size_t n, size_t stride, int nrhs,
+                          cudaStream_t s);
 
 // --------------------------------------------------------------------------- autotuner (tune.cu)
 struct TuneKey {
@@ -333,6 +345,9 @@ void mg_build(Ctx* c, mg_setup_info* info);
 void mg_destroy_hierarchy(Ctx* c);
 // preconditioner of the fine D_r in FP32 (z_e, r_e half vectors)
 void mg_precondition(Ctx* c, float* z_e, const float* r_e);
+// the same from an FP64 residual through a captured CUDA graph (r32: FP32
+// staging); false when graphs are off or unavailable (see multigrid.cu)
+bool mg_precondition_graph(Ctx* c, float* z_e, const double* r_e, float* r32);
 // the same for nb right-hand sides (packed half vectors, stride 24 Vh floats)
 void mg_precondition_batch(Ctx* c, float* z_e, const float* r_e, int nb);
 // mg_precondition_batch in three steps around the coarsest solve, so that

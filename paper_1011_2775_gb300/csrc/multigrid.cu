@@ -97,8 +97,24 @@ struct BatchWork {
   DBuf rc, ec, res, w, e, z0, scr;
 };
 
+// The 2-level cycle of level 0 as a captured CUDA graph (see mg_precondition_graph)
+struct CycleGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;   // private stream the capture runs on
+  const double* r = nullptr;    // the input the graph was captured for
+  float* r32 = nullptr;
+  bool failed = false;
+  long long dslash = 0, kernels = 0;   // launches one replay executes (for the statistics)
+  DBuf zc;                      // the graph's output
+  ~CycleGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
 struct Hierarchy {
   BatchWork bw;
+  CycleGraph graph;
   int L = 0;
   std::vector<LevelGeom> geo;
   std::vector<CoarseOp> cop;
@@ -558,10 +574,8 @@ void batch_mr(Ctx* c, BatchCtx& b, float* ev, float* rv, int nu, int nb) {
   blas_zero<float>(ev, b.n * nb, b.s);
   for (int it = 0; it < nu; it++) {
     b.H.F32->Dr_multi(w, rv, nb, b.hs);
-    for (int q = 0; q < nb; q++) {
-      blas_dot2<float>(w + q * b.hs, rv + q * b.hs, b.n, scr + 4 * q, c->ws, b.s);
-      blas_mr_update<float>(ev + q * b.hs, rv + q * b.hs, w + q * b.hs, scr + 4 * q, b.n, b.s);
-    }
+    blas_dot2_multi<float>(w, rv, b.n, b.hs, nb, scr, c->ws, b.s);
+    blas_mr_update_multi<float>(ev, rv, w, scr, b.n, b.hs, nb, b.s);
   }
 }
 }  // namespace
@@ -581,7 +595,7 @@ void mg_batch_pre(Ctx* c, float* z, const float* r, int nb) {
     blas_axpby<float>(-1.0, w, 1.0, res, b.n * nb, b.s);
     rin = res;
   }
-  for (int q = 0; q < nb; q++) restrict_vec(b.H.tr[0], bw.rc.as<float>() + q * b.cs, rin + q * b.hs, true, b.s);
+  restrict_vec_multi(b.H.tr[0], nb, bw.rc.as<float>(), b.cs, rin, b.hs, true, b.s);
 }
 
 bool mg_batch_joinable(Ctx* c) { return c->mg && c->mg->L == 2; }
@@ -621,10 +635,10 @@ void mg_batch_post(Ctx* c, float* z, const float* r, int nb) {
   float* ec = bw.ec.as<float>();
   if (b.p.nu_pre > 0) {
     float* z0 = bw.z0.as<float>();
-    for (int q = 0; q < nb; q++) prolong_vec(T, z0 + q * b.hs, ec + q * b.cs, true, b.s);
+    prolong_vec_multi(T, nb, z0, b.hs, ec, b.cs, true, b.s);
     blas_axpby<float>(1.0, z0, 1.0, z, b.n * nb, b.s);
   } else {
-    for (int q = 0; q < nb; q++) prolong_vec(T, z + q * b.hs, ec + q * b.cs, true, b.s);
+    prolong_vec_multi(T, nb, z, b.hs, ec, b.cs, true, b.s);
   }
   if (b.p.nu_post > 0) {
     float* w = bw.w.as<float>();
@@ -659,6 +673,67 @@ void mg_cycle_batch(Ctx* c, double* out_abi, const double* in_abi, int nb) {
   mg_precondition_batch(c, oe, ie, nb);
   for (int q = 0; q < nb; q++) unpack_spinor(c->g, oe + q * hs, oo + q * hs, true, out_abi + (size_t)q * 24 * c->V, s);
   c->sync();
+}
+
+// z_e = K(r_e) for an FP64 residual: the conversion to FP32 and the whole
+// 2-level cycle (restriction, persistent coarsest solve, prolongation, MR
+// smoothing: ~30 launches, no host synchronisation) are captured once into a
+// CUDA graph on a private stream and replayed with one launch; the output is
+// copied to z_e.  Returns false (nothing launched) when graphs are off or
+// unavailable -- deeper hierarchies (their intermediate GCRs test convergence
+// on the host), before the autotuner has chosen the coarsest solver (it
+// synchronises), or after a failed capture -- and the caller runs the cycle
+// directly.
+bool mg_precondition_graph(Ctx* c, float* z_e, const double* r_e, float* r32) {
+  if (!c->mg || !c->params.cuda_graphs) return false;
+  Hierarchy& H = *c->mg;
+  CycleGraph& G = H.graph;
+  if (H.L != 2 || G.failed || H.work[1].coarse_impl < 0) return false;
+  const size_t n = half_n(H, 0);
+  if (!G.exec || G.r != r_e || G.r32 != r32) {
+    if (G.exec) {
+      cudaGraphExecDestroy(G.exec);
+      G.exec = nullptr;
+    }
+    if (!G.zc.get()) G.zc.alloc(sizeof(float) * 2 * n);
+    if (!G.cap) MG_CUDA(cudaStreamCreateWithFlags(&G.cap, cudaStreamNonBlocking));
+    MG_CUDA(cudaStreamSynchronize(c->stream));
+    cudaStream_t saved = c->stream;
+    c->stream = G.cap;
+    const long long d0 = c->dslash_launches, k0 = launches_so_far();
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(G.cap, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    if (ok) {
+      try {
+        blas_convert<double, float>(r32, r_e, n, G.cap);
+        cycle(c, H, 0, G.zc.as<float>(), r32);
+      } catch (const Error&) {
+        ok = false;
+      }
+      ok = cudaStreamEndCapture(G.cap, &graph) == cudaSuccess && ok && graph;
+    }
+    c->stream = saved;
+    // the captured launches did not run: count them when a replay runs them
+    G.dslash = c->dslash_launches - d0;
+    G.kernels = launches_so_far() - k0;
+    c->dslash_launches = d0;
+    add_launches(-G.kernels);
+    if (ok) ok = cudaGraphInstantiate(&G.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      G.exec = nullptr;
+      G.failed = true;
+      (void)cudaGetLastError();   // clear the capture error; run the cycle directly from now on
+      return false;
+    }
+    G.r = r_e;
+    G.r32 = r32;
+  }
+  MG_CUDA(cudaGraphLaunch(G.exec, c->stream));
+  c->dslash_launches += G.dslash;
+  add_launches(G.kernels);
+  MG_CUDA(cudaMemcpyAsync(z_e, G.zc.get(), sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, c->stream));
+  return true;
 }
 
 void mg_precondition(Ctx* c, float* z_e, const float* r_e) {

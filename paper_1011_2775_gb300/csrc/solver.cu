@@ -38,6 +38,8 @@ void launch_check(const char* file, int line) {
 
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
 void DBuf::alloc(size_t bytes) {
   release();
   if (bytes == 0) return;
@@ -59,6 +61,8 @@ void Workspace::init() {
   MG_CUDA(cudaMemset(scalars.get(), 0, sizeof(double) * kScalars));
   flags.alloc(sizeof(int) * FLAG_COUNT);
   MG_CUDA(cudaMemset(flags.get(), 0, sizeof(int) * FLAG_COUNT));
+  mcounters.alloc(sizeof(unsigned) * kMultiCounters);
+  MG_CUDA(cudaMemset(mcounters.get(), 0, sizeof(unsigned) * kMultiCounters));
   if (!host) MG_CUDA(cudaMallocHost((void**)&host, sizeof(double) * 256));
 }
 
@@ -445,6 +449,7 @@ int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int m
       if (!B->gcr_mg) B->gcr_mg.reset(new GCR<double, float>(c, n, restart));
       float* r32 = B->r32.as<float>();
       GCR<double, float>::Pre pre = [&](float* z, const double* r) {
+        if (mg_precondition_graph(c, z, r, r32)) return;
         blas_convert<double, float>(r32, r, n, s);
         mg_precondition(c, z, r32);
       };

@@ -249,3 +249,25 @@ def test_mg_iterations_match_oracle(qcdlike):
     assert _true_residual(W, psi, eta) <= 1e-10
     assert abs(info.outer_iterations - oinfo.outer_iterations) <= max(3, 0.2 * oinfo.outer_iterations)
     S.close()
+
+
+def test_cycle_graph_replay_matches_direct_launches():
+    """The single-rhs solve replays its 2-level cycle as a captured CUDA graph
+    (mg_params.cuda_graphs = 1, the default); the same kernels launched one by
+    one give the same solution and iteration count."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (8, 8, 8, 16)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 5001)
+    W = WilsonClover(U, 1.0, -0.6)
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(levels=2, blocks=[(4, 4, 4, 4)], nv=[12], seed=5101)
+    S.setup()
+    eta = I.gaussian_source(dims, 5102)
+    psi_g, info_g = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    psi_g2, info_g2 = S.solve(eta, 1e-10, B.MG_MODE_MG)   # graph captured by now: pure replay
+    S.set_params(cuda_graphs=0)
+    psi_d, info_d = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _true_residual(W, psi_g2, eta) <= 1e-10
+    assert info_g2.outer_iterations == info_d.outer_iterations
+    assert np.abs(psi_g2 - psi_d).max() <= 1e-13 * np.abs(psi_d).max()
+    S.close()
