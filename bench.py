@@ -416,6 +416,26 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     out["cuda_graph"] = {"graph_ms": tg[1], "direct_launch_ms": tg[0], "speedup": tg[0] / tg[1]}
     del e_g, p_g
 
+    # ---- the mass sweep of the workload: MG-GCR, and plain EO-GCR capped at SWEEP_EO_CAP iterations
+    sweep = []
+    for m0 in MASSES:
+        Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
+        Q.load_gauge(U)
+        Q.set_clover(CSW, m0)
+        Q.set_params(seed=NULLVEC_SEED, maxit_fine=2000, **MG)
+        Q.setup()
+        e_d = torch.from_numpy(eta).to(f"cuda:{dev}")
+        p_d = torch.zeros_like(e_d)
+        Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
+        t_mg, (_, mi) = timed(lambda: Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
+        Q.set_params(maxit_fine=SWEEP_EO_CAP)
+        t_eo, (st, ei) = timed(lambda: B.mg_solve(Q.ctx, p_d, e_d, 1, TOL, B.MG_MODE_EO_GCR, allow_not_converged=True))
+        sweep.append({"m0": m0, "mg_ms": t_mg, "mg_outer_iterations": mi.outer_iterations,
+                      "mg_true_residual": mi.true_residual, "eo_gcr_ms": t_eo, "eo_gcr_iterations": ei.outer_iterations,
+                      "eo_gcr_true_residual": ei.true_residual, "eo_gcr_converged": st == B.MG_OK})
+        Q.close()
+    out["mass_sweep"] = sweep
+
     # ---- FP16 storage of P and the coarse links
     Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
     Q.load_gauge(U)
@@ -440,6 +460,56 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
 # gauge construction, m0 = -0.3, 2-level MG with 4^4 blocks and Nv = 24.
 MULTI = [((32, 32, 32, 64), "point", 12), ((16, 16, 16, 32), "gauss", 8), ((24, 24, 24, 48), "gauss", 8)]
 MULTI_M0 = -0.3
+SWEEP_EO_CAP = 2000                  # EO-GCR iteration cap in the mass sweep
+
+# The 3-level configuration: 24^3x64, same gauge construction, m0 = -0.35,
+# 4^4 blocks (Nv = 24) then 2^4 blocks (Nv = 32) onto a 3^3x8 coarsest lattice
+# (odd extent: no even-odd there), 16-bit storage of P and coarse links.
+CONFIG3_DIMS = (24, 24, 24, 64)
+CONFIG3_MG = dict(levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 32])
+
+
+def run_config3(dev: int) -> dict:
+    """The 3-level solve on 24^3x64 with BF16 and with FP32 storage, and the FP32
+    dslash on this lattice (467 MB per launch, beyond L2)."""
+    import torch
+    from paper_1011_2775_gb300 import binding as B
+    from paper_1011_2775_gb300 import inputs as I
+    from paper_1011_2775_gb300.solver import Solver
+
+    stream = torch.cuda.current_stream(dev)
+    U = I.make_gauge(CONFIG3_DIMS, EPS, APE, ALPHA, 3001)
+    eta = torch.from_numpy(I.gaussian_source(CONFIG3_DIMS, 3002)).to(f"cuda:{dev}")
+    psi = torch.zeros_like(eta)
+    out = {"lattice": "24^3x64", "m0": -0.35, "mg": "3-level: 4^4 (Nv=24) then 2^4 (Nv=32), coarsest 3^3x8"}
+    for name, store, mg in (("bf16", B.MG_STORE_BF16, CONFIG3_MG), ("fp32", B.MG_STORE_FP32, CONFIG3_MG),
+                            ("two_level_fp32", B.MG_STORE_FP32, MG)):
+        S = Solver(CONFIG3_DIMS, device=dev, stream=stream.cuda_stream)
+        S.load_gauge(U)
+        S.set_clover(CSW, -0.35)
+        S.set_params(seed=3003, maxit_fine=2000, storage=store, **mg)
+        t0 = time.perf_counter()
+        S.setup()
+        setup_ms = 1e3 * (time.perf_counter() - t0)
+        S.solve(eta, TOL, B.MG_MODE_MG, out=psi)
+        ts = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, info = S.solve(eta, TOL, B.MG_MODE_MG, out=psi)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        out[name] = {"solve_ms": min(ts), "setup_ms": setup_ms, "outer_iterations": info.outer_iterations,
+                     "level1_iterations": info.coarse_iterations[1], "level2_iterations": info.coarse_iterations[2],
+                     "true_residual": info.true_residual, "levels": mg["levels"]}
+        if name == "fp32":
+            ms_k, by = B.mg_benchmark_kernel(S.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, warmup=10, iters=50)
+            out["dslash_clover_fp32"] = {"ms": ms_k, "bytes": by, "gbs": by / ms_k / 1e6}
+        S.close()
+    return out
 
 
 def run_multi(dev: int) -> dict:
@@ -514,6 +584,8 @@ def main():
     ap.add_argument("--no-eo", action="store_true", help="skip the plain EO-GCR comparison")
     ap.add_argument("--eo-maxit", type=int, default=20000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--config3", action="store_true",
+                    help="also run the 3-level 24^3x64 solve with BF16 and FP32 storage (about a minute)")
     ap.add_argument("--multi", action="store_true",
                     help="also solve the batched sources on three lattices of uneven size (about a minute)")
     ap.add_argument("--no-extra", action="store_true",
@@ -561,6 +633,8 @@ def main():
     r = run_gpu(args, dist)
     if args.multi:
         r["extra"]["multi_lattice"] = run_multi(dist.local)
+    if args.config3:
+        r["extra"]["three_level_24x64"] = run_config3(dist.local)
     info = r["info"]
     dr_per_solve = info.dslash_launches / 2.0
     k = r["kern"]["dslash_clover_fp32"]

@@ -440,8 +440,8 @@ __global__ void __launch_bounds__(128) k_dslash(Geom g, int par, T* out, const T
 // into registers and applied to the NR
 // neighbour spinors, so link bytes are paid once per site and NR rhs while
 // the spinor loads stay coalesced over consecutive sites.
-template <typename T, int EPI, int NR, int BS>
-__global__ void __launch_bounds__(BS) k_dslash_mrhs(Geom g, int par, int nrhs, size_t stride, T* out,
+template <typename T, int EPI, int NR, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_dslash_mrhs(Geom g, int par, int nrhs, size_t stride, T* out,
                                                     const T* __restrict__ in, const T* __restrict__ gauge,
                                                     const T* __restrict__ clov, const T* __restrict__ x, T a,
                                                     int dirmask) {
@@ -549,22 +549,24 @@ void dslash_mrhs_y(const Geom& g, Epilogue epi, int parity, int nrhs, size_t str
   MG_LAUNCH();
 }
 
-template <typename T, int NR, int BS>
+template <typename T, int NR, int BS, int MINB = 1>
 void dslash_mrhs_cfg(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
                      const T* gauge, const T* clov, const T* x, double a, int dirmask, cudaStream_t s) {
   const dim3 grid((unsigned)(((g.Vh + BS - 1) / BS) * ((nrhs + NR - 1) / NR)));
   switch (epi) {
-    case EPI_H: k_dslash_mrhs<T, EPI_H, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_CH: k_dslash_mrhs<T, EPI_CH, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_XPAY: k_dslash_mrhs<T, EPI_XPAY, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_CX_PAY: k_dslash_mrhs<T, EPI_CX_PAY, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
-    case EPI_C_XPAY: k_dslash_mrhs<T, EPI_C_XPAY, NR, BS><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_H: k_dslash_mrhs<T, EPI_H, NR, BS, MINB><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CH: k_dslash_mrhs<T, EPI_CH, NR, BS, MINB><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_XPAY: k_dslash_mrhs<T, EPI_XPAY, NR, BS, MINB><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_CX_PAY: k_dslash_mrhs<T, EPI_CX_PAY, NR, BS, MINB><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
+    case EPI_C_XPAY: k_dslash_mrhs<T, EPI_C_XPAY, NR, BS, MINB><<<grid, BS, 0, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (T)a, dirmask); break;
   }
   MG_LAUNCH();
 }
 
 // config = NR * 1000 + CTA size (NR right-hand sides per thread; FP32: NR in
-// {2, 4}, FP64: NR in {1, 2}), or 100000 + NY (rhs in threadIdx.y, NY in {4, 8})
+// {2, 4}, FP64: NR in {1, 2}) [+ 10000, FP32 only: register cap for more
+// resident CTAs, __launch_bounds__ minimum of 4 (NR = 2) or 3 (NR = 4) CTAs of 128], or
+// 100000 + NY (rhs in threadIdx.y, NY in {4, 8})
 template <typename T>
 void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
                  const T* gauge, const T* clov, const T* x, double a, int dirmask, int config, cudaStream_t s) {
@@ -578,6 +580,15 @@ void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t strid
   }
   constexpr bool f32 = std::is_same<T, float>::value;
   constexpr int NA = f32 ? 2 : 1, NB = f32 ? 4 : 2;
+  if constexpr (f32) {
+    if (config >= 10000) {   // register-capped variants (FP32 only: FP64 would spill), CTA of 128
+      if ((config - 10000) / 1000 == 4)
+        dslash_mrhs_cfg<T, 4, 128, 3>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
+      else
+        dslash_mrhs_cfg<T, 2, 128, 4>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
+      return;
+    }
+  }
   const int nr = config / 1000, bs = config % 1000;
   if (nr == NB) {
     if (bs == 64)
@@ -597,7 +608,7 @@ template void dslash_mrhs<double>(const Geom&, Epilogue, int, int, size_t, doubl
                                   const double*, const double*, double, int, int, cudaStream_t);
 
 std::vector<int> dslash_mrhs_configs(bool fp32) {
-  return fp32 ? std::vector<int>{2064, 2128, 4064, 4128, 100004, 100008}
+  return fp32 ? std::vector<int>{2064, 2128, 4064, 4128, 12128, 14128, 100004, 100008}
               : std::vector<int>{1064, 1128, 2064, 2128, 100004, 100008};
 }
 int dslash_mrhs_default(bool fp32) { (void)fp32; return 100004; }
