@@ -436,6 +436,41 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
         Q.close()
     out["mass_sweep"] = sweep
 
+    # ---- setup reuse: rebuild for the next mass of the sweep from the current null vectors, and
+    #      the setup effort (inverse-iteration passes) against the solve it buys
+    reuse = {}
+    Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
+    Q.load_gauge(U)
+    Q.set_clover(CSW, MASSES[-1])
+    Q.set_params(seed=NULLVEC_SEED, maxit_fine=2000, **MG)
+    Q.setup()
+    e_d = torch.from_numpy(eta).to(f"cuda:{dev}")
+    p_d = torch.zeros_like(e_d)
+    ui = Q.update_mass(MASSES[-2])
+    Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
+    t_u, (_, qi) = timed(lambda: Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
+    reuse["update_mass"] = {"from_m0": MASSES[-1], "to_m0": MASSES[-2], "rebuild_ms": ui.setup_ms, "solve_ms": t_u,
+                            "outer_iterations": qi.outer_iterations, "true_residual": qi.true_residual}
+    Q.close()
+    effort = []
+    for iters in (2, 5, 20):
+        Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
+        Q.load_gauge(U)
+        Q.set_clover(CSW, MASSES[-1])
+        Q.set_params(seed=NULLVEC_SEED, maxit_fine=2000, setup_iters=iters, **MG)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        si_ = Q.setup()
+        t_setup = 1e3 * (time.perf_counter() - t0)
+        Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
+        t_s, (_, qi) = timed(lambda: Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
+        effort.append({"setup_iters": iters, "setup_passes": si_.passes[0], "setup_ms": t_setup, "solve_ms": t_s,
+                       "outer_iterations": qi.outer_iterations})
+        Q.close()
+    reuse["setup_effort"] = effort
+    out["setup_reuse"] = reuse
+    del e_d, p_d
+
     # ---- FP16 storage of P and the coarse links
     Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
     Q.load_gauge(U)

@@ -195,6 +195,10 @@ MG_API int mg_set_clover(void* ctx, double csw, double m0);
  * below the coarsest has an odd extent), MG_ERR_NV. */
 MG_API int mg_set_params(void* ctx, const mg_params* p);
 
+/* Copy out the context's current parameters (the defaults until
+ * mg_set_params or mg_load_setup set them).  Errors: MG_ERR_ARG. */
+MG_API int mg_get_params(void* ctx, mg_params* p);
+
 /* Run the setup ("Setup procedure"): for every transfer l, find nv[l]
  * near-null vectors of level l's D_p by inverse iteration (unless injected by
  * mg_set_null_vectors), split them by chirality, block-orthonormalise them
@@ -210,7 +214,28 @@ MG_API int mg_setup(void* ctx, mg_setup_info* info);
 MG_API int mg_set_null_vectors(void* ctx, int level, const void* V, int nv, int where);
 MG_API int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where);
 
-/* Read the coarse operator of level `level` (1 .. levels-1) after mg_setup,
+/* Setup reuse.  The paper keeps the null vectors and coarse operators of a
+ * setup for later use; here the raw null vectors of every transfer are the
+ * saved state, and P and the coarse operators are rebuilt from them (block
+ * Gram-Schmidt and Galerkin links: no inverse iteration) for the current
+ * gauge field, clover and mass.
+ *   mg_save_setup:  writes the multigrid parameters, csw, m0 and the null
+ *                   vectors (complex128) of the current setup to `path`.
+ *   mg_load_setup:  reads such a file for a context with the same lattice
+ *                   (gauge field and clover already set), applies its
+ *                   parameters and rebuilds the hierarchy; `info` (may be
+ *                   NULL) as mg_setup, setup_ms being the whole call.
+ *   mg_update_mass: sets a new bare mass (same csw) and rebuilds the
+ *                   hierarchy from the current null vectors -- setup reuse
+ *                   across masses.
+ * Errors: MG_ERR_ARG (unreadable or foreign file), MG_ERR_DIMS (another
+ * lattice), MG_ERR_STATE (no setup / no clover), MG_ERR_GS_BREAKDOWN,
+ * MG_ERR_SINGULAR_CLOVER, MG_ERR_CUDA. */
+MG_API int mg_save_setup(void* ctx, const char* path);
+MG_API int mg_load_setup(void* ctx, const char* path, mg_setup_info* info);
+MG_API int mg_update_mass(void* ctx, double m0, mg_setup_info* info);
+
+/* Read the coarse operator of level `level` (1 .. levels-1) after mg_setup,/* Read the coarse operator of level `level` (1 .. levels-1) after mg_setup,
  * as the solver applies it: the Galerkin links of section "Implementation"
  * (D_hat v(x) = X(x) v(x) + sum_d Y_d(x) v(x + d), d < 4: from x + mu,
  * d >= 4: from x - mu), dequantised from their storage format (FP16/BF16

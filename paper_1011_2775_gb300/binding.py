@@ -37,8 +37,9 @@ MG_FORCE_SU3, MG_FORCE_WIRTINGER = 0, 1
 MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_DR = range(4)
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
-            "mg_set_clover", "mg_set_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_get_coarse_links", "mg_solve", "mg_solve_batch", "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
+            "mg_set_clover", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
+            "mg_get_coarse_links", "mg_save_setup", "mg_load_setup", "mg_update_mass", "mg_solve", "mg_solve_batch",
+            "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
             "mg_level_info"]
 
 
@@ -110,6 +111,7 @@ def lib() -> ctypes.CDLL:
             "mg_load_gauge": [vp, vp, ip],
             "mg_set_clover": [vp, dp, dp],
             "mg_set_params": [vp, ctypes.POINTER(mg_params)],
+            "mg_get_params": [vp, ctypes.POINTER(mg_params)],
             "mg_setup": [vp, ctypes.POINTER(mg_setup_info)],
             "mg_set_null_vectors": [vp, ip, vp, ip, ip],
             "mg_get_null_vectors": [vp, ip, vp, ip, ip],
@@ -117,6 +119,9 @@ def lib() -> ctypes.CDLL:
             "mg_solve_dagger": [vp, vp, vp, ip, dp, ip, ip, ctypes.POINTER(mg_solve_info)],
             "mg_force": [vp, vp, vp, vp, ip, ip],
             "mg_get_coarse_links": [vp, ip, vp, vp, ip],
+            "mg_save_setup": [vp, ctypes.c_char_p],
+            "mg_load_setup": [vp, ctypes.c_char_p, ctypes.POINTER(mg_setup_info)],
+            "mg_update_mass": [vp, dp, ctypes.POINTER(mg_setup_info)],
             "mg_solve_batch": [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ip), dp,
                                ip, ctypes.POINTER(mg_solve_info)],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
@@ -197,6 +202,12 @@ def mg_set_params(ctx, params: mg_params) -> None:
     _check(lib().mg_set_params(ctx, ctypes.byref(params)), "mg_set_params")
 
 
+def mg_get_params(ctx) -> mg_params:
+    p = mg_params()
+    _check(lib().mg_get_params(ctx, ctypes.byref(p)), "mg_get_params")
+    return p
+
+
 def mg_setup(ctx) -> mg_setup_info:
     info = mg_setup_info()
     _check(lib().mg_setup(ctx, ctypes.byref(info)), "mg_setup")
@@ -253,6 +264,22 @@ def mg_solve_dagger(ctx, psi, eta, nrhs: int, tol: float, mode: int = MG_MODE_MG
     st = lib().mg_solve_dagger(ctx, pp, pe, int(nrhs), float(tol), int(mode), wp, ctypes.byref(info))
     _check(st, "mg_solve_dagger", allow=(MG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
     return st, info
+
+
+def mg_save_setup(ctx, path: str) -> None:
+    _check(lib().mg_save_setup(ctx, os.fsencode(path)), "mg_save_setup")
+
+
+def mg_load_setup(ctx, path: str) -> mg_setup_info:
+    info = mg_setup_info()
+    _check(lib().mg_load_setup(ctx, os.fsencode(path), ctypes.byref(info)), "mg_load_setup")
+    return info
+
+
+def mg_update_mass(ctx, m0: float) -> mg_setup_info:
+    info = mg_setup_info()
+    _check(lib().mg_update_mass(ctx, float(m0), ctypes.byref(info)), "mg_update_mass")
+    return info
 
 
 def mg_get_coarse_links(ctx, level: int, Y, X) -> None:

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <vector>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
@@ -329,6 +330,15 @@ int mg_set_params(void* ctx, const mg_params* p) {
   });
 }
 
+int mg_get_params(void* ctx, mg_params* p) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!p) mg::raise(MG_ERR_ARG, "null params");
+    *p = c->params;
+    return MG_OK;
+  });
+}
+
 int mg_setup(void* ctx, mg_setup_info* info) {
   return guarded([&]() {
     mg::Ctx* c = as_ctx(ctx);
@@ -372,6 +382,121 @@ int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where) {
     mg::mg_get_vectors(c, level, st.ptr, nv);
     stage_out_finish(c, st, V, bytes, where);
     return MG_OK;
+  });
+}
+
+// ---- setup reuse (the paper saves null vectors and coarse operators for later use)
+namespace {
+constexpr char kSetupMagic[8] = {'M', 'G', 'C', 'L', 'S', 'E', 'T', '1'};
+
+struct SetupHeader {
+  char magic[8];
+  int32_t dims[4];
+  mg_params params;
+  double csw, m0;
+  int32_t levels;
+};
+
+// the raw null vectors of every transfer of the current setup, complex128 on the host
+std::vector<std::vector<double>> current_vectors(mg::Ctx* c) {
+  std::vector<std::vector<double>> out;
+  for (int l = 0; l + 1 < c->params.levels; l++) {
+    const int nv = c->params.nv[l];
+    const size_t n = level_vec_complex(c, l, nullptr) * nv;
+    mg::DBuf d(sizeof(double) * 2 * n);
+    mg::mg_get_vectors(c, l, d.as<double>(), nv);
+    out.emplace_back(2 * n);
+    MG_CUDA(cudaMemcpy(out.back().data(), d.get(), sizeof(double) * 2 * n, cudaMemcpyDeviceToHost));
+  }
+  return out;
+}
+
+// rebuild the hierarchy from given null vectors (no inverse iteration)
+void rebuild_from(mg::Ctx* c, std::vector<std::vector<double>>& vecs, mg_setup_info* info) {
+  c->injected.assign(MG_MAX_LEVELS, std::vector<double>());
+  for (size_t l = 0; l < vecs.size(); l++) c->injected[l] = vecs[l];
+  if (info) std::memset(info, 0, sizeof(*info));
+  mg::mg_build(c, info);
+}
+}  // namespace
+
+int mg_save_setup(void* ctx, const char* path) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!path) mg::raise(MG_ERR_ARG, "null path");
+    if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    SetupHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kSetupMagic, 8);
+    for (int m = 0; m < 4; m++) h.dims[m] = c->dims[m];
+    h.params = c->params;
+    h.csw = c->csw;
+    h.m0 = c->m0;
+    h.levels = c->params.levels;
+    std::vector<std::vector<double>> vecs = current_vectors(c);
+    std::FILE* f = std::fopen(path, "wb");
+    if (!f) mg::raise(MG_ERR_ARG, std::string("cannot open ") + path + " for writing");
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
+    for (const auto& v : vecs) ok = ok && std::fwrite(v.data(), sizeof(double), v.size(), f) == v.size();
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) mg::raise(MG_ERR_ARG, std::string("writing ") + path + " failed");
+    return MG_OK;
+  });
+}
+
+int mg_load_setup(void* ctx, const char* path, mg_setup_info* info) {
+  return guarded([&]() {
+    const auto t0 = std::chrono::steady_clock::now();
+    mg::Ctx* c = as_ctx(ctx);
+    if (!path) mg::raise(MG_ERR_ARG, "null path");
+    if (!c->have_clover) mg::raise(MG_ERR_STATE, "load the gauge field and set the clover first");
+    std::FILE* f = std::fopen(path, "rb");
+    if (!f) mg::raise(MG_ERR_ARG, std::string("cannot open ") + path);
+    SetupHeader h;
+    const bool hdr = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, kSetupMagic, 8) == 0;
+    if (!hdr) {
+      std::fclose(f);
+      mg::raise(MG_ERR_ARG, std::string(path) + " is not a saved multigrid setup");
+    }
+    for (int m = 0; m < 4; m++)
+      if (h.dims[m] != c->dims[m]) {
+        std::fclose(f);
+        mg::raise(MG_ERR_DIMS, "the saved setup belongs to another lattice");
+      }
+    const int st = mg_set_params(ctx, &h.params);
+    if (st != MG_OK) {
+      std::fclose(f);
+      return st;
+    }
+    std::vector<std::vector<double>> vecs;
+    bool ok = true;
+    for (int l = 0; l + 1 < h.params.levels && ok; l++) {
+      const size_t n = 2 * level_vec_complex(c, l, nullptr) * h.params.nv[l];
+      vecs.emplace_back(n);
+      ok = std::fread(vecs.back().data(), sizeof(double), n, f) == n;
+    }
+    std::fclose(f);
+    if (!ok) mg::raise(MG_ERR_ARG, std::string(path) + " is truncated");
+    rebuild_from(c, vecs, info);
+    if (info)
+      info->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return (int)MG_OK;
+  });
+}
+
+int mg_update_mass(void* ctx, double m0, mg_setup_info* info) {
+  return guarded([&]() {
+    const auto t0 = std::chrono::steady_clock::now();
+    mg::Ctx* c = as_ctx(ctx);
+    if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    if (!std::isfinite(m0)) mg::raise(MG_ERR_ARG, "non-finite m0");
+    std::vector<std::vector<double>> vecs = current_vectors(c);
+    const int st = mg_set_clover(ctx, c->csw, m0);
+    if (st != MG_OK) return st;
+    rebuild_from(c, vecs, info);
+    if (info)
+      info->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return (int)MG_OK;
   });
 }
 

@@ -72,11 +72,6 @@ __device__ __forceinline__ double wsum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ float wsumf(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // Block-reduce nq values (one per thread-slot array v[q]) and store the block's
 // partial sums in partials[q0 + q][blockIdx.x] (slot-major, so that the

@@ -96,6 +96,19 @@ class Solver:
         B.mg_get_coarse_links(self.ctx, level, Y, X)
         return Y, X
 
+    def save_setup(self, path: str):
+        B.mg_save_setup(self.ctx, path)
+
+    def load_setup(self, path: str):
+        """Parameters and null vectors from a saved setup; the hierarchy is rebuilt for the current field."""
+        info = B.mg_load_setup(self.ctx, path)
+        self.params = B.mg_get_params(self.ctx)
+        return info
+
+    def update_mass(self, m0: float):
+        """New bare mass, hierarchy rebuilt from the current null vectors (no inverse iteration)."""
+        return B.mg_update_mass(self.ctx, m0)
+
     def setup(self):
         return B.mg_setup(self.ctx)
 
