@@ -271,3 +271,23 @@ def test_cycle_graph_replay_matches_direct_launches():
     assert info_g2.outer_iterations == info_d.outer_iterations
     assert np.abs(psi_g2 - psi_d).max() <= 1e-13 * np.abs(psi_d).max()
     S.close()
+
+
+def test_four_level_solve():
+    """Four levels (16^4 -> 8^4 -> 4^4 -> 2^4, 2^4 blocks, Nv = 8 each): the
+    recursive cycle with two intermediate GCR levels reaches the tolerance with
+    the oracle's D, and every coarse level iterates."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (16, 16, 16, 16)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 5601)
+    W = WilsonClover(U, 1.0, -0.5)
+    S = _solver(dims, U, 1.0, -0.5)
+    S.set_params(levels=4, blocks=[(2, 2, 2, 2)] * 3, nv=[8, 8, 8], seed=5602, maxit_fine=2000, setup_iters=6)
+    info = S.setup()
+    assert info.coarse_sites[0] == 4096 and info.coarse_sites[2] == 16
+    assert S.level_info(3) == ((2, 2, 2, 2), 16)
+    eta = I.gaussian_source(dims, 5603)
+    psi, si = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _true_residual(W, psi, eta) <= 1e-10
+    assert si.coarse_iterations[1] > 0 and si.coarse_iterations[2] > 0 and si.coarse_iterations[3] > 0
+    S.close()
