@@ -467,6 +467,21 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
         effort.append({"setup_iters": iters, "setup_passes": si_.passes[0], "setup_ms": t_setup, "solve_ms": t_s,
                        "outer_iterations": qi.outer_iterations})
         Q.close()
+    # a weak setup (2 passes per vector) refined by one adaptive pass
+    Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
+    Q.load_gauge(U)
+    Q.set_clover(CSW, MASSES[-1])
+    Q.set_params(seed=NULLVEC_SEED, maxit_fine=2000, setup_iters=2, **MG)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Q.setup()
+    ai = Q.adapt_setup(passes=1, relax=2)
+    t_setup = 1e3 * (time.perf_counter() - t0)
+    Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
+    t_s, (_, qi) = timed(lambda: Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
+    effort.append({"setup_iters": 2, "adaptive_passes": 1, "adaptive_relax": 2, "setup_ms": t_setup,
+                   "adaptive_ms": ai.setup_ms, "solve_ms": t_s, "outer_iterations": qi.outer_iterations})
+    Q.close()
     reuse["setup_effort"] = effort
     out["setup_reuse"] = reuse
     del e_d, p_d

@@ -38,7 +38,7 @@ MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_D
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
-            "mg_get_coarse_links", "mg_save_setup", "mg_load_setup", "mg_update_mass", "mg_solve", "mg_solve_batch",
+            "mg_get_coarse_links", "mg_save_setup", "mg_load_setup", "mg_update_mass", "mg_adapt_setup", "mg_solve", "mg_solve_batch",
             "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
             "mg_level_info"]
 
@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "mg_save_setup": [vp, ctypes.c_char_p],
             "mg_load_setup": [vp, ctypes.c_char_p, ctypes.POINTER(mg_setup_info)],
             "mg_update_mass": [vp, dp, ctypes.POINTER(mg_setup_info)],
+            "mg_adapt_setup": [vp, ip, ip, ctypes.POINTER(mg_setup_info)],
             "mg_solve_batch": [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ip), dp,
                                ip, ctypes.POINTER(mg_solve_info)],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
@@ -279,6 +280,12 @@ def mg_load_setup(ctx, path: str) -> mg_setup_info:
 def mg_update_mass(ctx, m0: float) -> mg_setup_info:
     info = mg_setup_info()
     _check(lib().mg_update_mass(ctx, float(m0), ctypes.byref(info)), "mg_update_mass")
+    return info
+
+
+def mg_adapt_setup(ctx, passes: int = 1, relax: int = 2) -> mg_setup_info:
+    info = mg_setup_info()
+    _check(lib().mg_adapt_setup(ctx, int(passes), int(relax), ctypes.byref(info)), "mg_adapt_setup")
     return info
 
 

@@ -484,6 +484,23 @@ int mg_load_setup(void* ctx, const char* path, mg_setup_info* info) {
   });
 }
 
+int mg_adapt_setup(void* ctx, int passes, int relax, mg_setup_info* info) {
+  return guarded([&]() {
+    const auto t0 = std::chrono::steady_clock::now();
+    mg::Ctx* c = as_ctx(ctx);
+    if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    if (passes < 1 || relax < 1) mg::raise(MG_ERR_ARG, "passes and relax must be positive");
+    for (int p = 0; p < passes; p++) {
+      mg::mg_relax_null_vectors(c, relax);
+      std::vector<std::vector<double>> vecs = current_vectors(c);
+      rebuild_from(c, vecs, info);
+    }
+    if (info)
+      info->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return (int)MG_OK;
+  });
+}
+
 int mg_update_mass(void* ctx, double m0, mg_setup_info* info) {
   return guarded([&]() {
     const auto t0 = std::chrono::steady_clock::now();

@@ -799,6 +799,47 @@ void mg_get_links(Ctx* c, int level, double* Y_abi, double* X_abi) {
   coarse_links_abi(H.geo[level], H.cop[level], Y_abi, X_abi, c->stream);
 }
 
+// Adaptive refinement of the fine-level null vectors (the alpha-SA idea the
+// paper plans for the clover case, section "Setup procedure"): every vector v
+// is relaxed on the homogeneous system D_p v = 0 with the current multigrid
+// solver, v <- v - M D_p v, normalised after each step, where M ~ D_p^{-1} is
+// the even-odd form of the current cycle K ~ D_r^{-1}: with D_p = [[1, X],
+// [Y, 1]] (X = H_eo A_o^{-1}, Y = H_oe A_e^{-1}, D_r = 1 - X Y),
+//   u_e = K (f_e - X f_o),   u_o = f_o - Y u_e   solves D_p u = f when K = D_r^{-1}.
+// Components the current coarse space represents well are removed; what is
+// left is rich in the modes the solver resolves poorly.  The caller rebuilds
+// the hierarchy from the relaxed vectors.
+void mg_relax_null_vectors(Ctx* c, int relax) {
+  if (!c->mg || c->mg->L < 2) raise(MG_ERR_STATE, "multigrid not set up");
+  Hierarchy& H = *c->mg;
+  const size_t nf = full_n(H, 0), nh = half_n(H, 0), hs = 2 * nh;
+  cudaStream_t s = c->stream;
+  FineOps<float>& F = *H.F32;
+  DBuf tb(sizeof(float) * 2 * nf), ub(sizeof(float) * 2 * nf), gb(sizeof(float) * hs), sb(sizeof(float) * hs);
+  float* te = tb.as<float>();
+  float* to = te + hs;
+  float* ue = ub.as<float>();
+  float* uo = ue + hs;
+  float* ge = gb.as<float>();
+  float* se = sb.as<float>();
+  double* scr = c->ws.scalars.as<double>() + 1024;
+  for (int k = 0; k < H.tr[0].nv; k++) {
+    float* ve = H.nullvecs[0].as<float>() + (size_t)k * 2 * nf;
+    float* vo = ve + hs;
+    for (int it = 0; it < relax; it++) {
+      F.Dp(te, to, ve, vo);                                                  // t = D_p v
+      F.br(ge, te, to);                                                      // g_e = t_e - X t_o
+      mg_precondition(c, ue, ge);                                            // u_e = K g_e
+      clover_apply<float>(c->g, se, ue, c->Ainv<float>(0), s);              // A_e^{-1} u_e
+      dslash<float>(c->g, EPI_XPAY, 1, uo, se, c->gauge<float>(), nullptr, to, -1.0, 0xff, s);  // u_o = t_o - Y u_e
+      blas_axpby<float>(-1.0, ue, 1.0, ve, nf, s);                         // v -= u (both halves)
+      blas_norm2<float>(ve, nf, scr, c->ws, s);
+      blas_normalize<float>(ve, scr, nf, s);
+    }
+  }
+  c->sync();
+}
+
 void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv) {
   if (!c->mg || level + 1 >= c->mg->L) raise(MG_ERR_STATE, "transfer not set up");
   Hierarchy& H = *c->mg;

@@ -109,3 +109,24 @@ def test_update_mass_reuses_null_vectors():
     assert si.outer_iterations <= 1.5 * fi.outer_iterations + 3
     S.close()
     F.close()
+
+
+def test_adaptive_setup_improves_a_weak_setup():
+    """mg_adapt_setup (alpha-SA style refinement): after a deliberately weak setup
+    (one inverse-iteration pass per vector), one adaptive pass -- relaxing each
+    null vector with the current solver and rebuilding -- lowers the outer
+    iteration count, and the solve still reaches 1e-10 with the oracle's D."""
+    from paper_1011_2775_gb300 import binding as B
+    U = I.make_gauge(DIMS, 1.0, 5, 0.5, 8401)
+    W = WilsonClover(U, 1.0, -0.6)
+    eta = I.gaussian_source(DIMS, 8402)
+    S = _solver(U, -0.6)
+    S.set_params(levels=2, blocks=[(4, 4, 4, 4)], nv=[12], seed=8403, setup_iters=1, maxit_fine=4000)
+    S.setup()
+    _, weak = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    info = S.adapt_setup(passes=1, relax=3)
+    assert info.vectors[0] == 12
+    psi, adapted = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _res(W, psi, eta) <= 1e-10
+    assert adapted.outer_iterations < weak.outer_iterations
+    S.close()
