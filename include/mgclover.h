@@ -235,19 +235,23 @@ MG_API int mg_save_setup(void* ctx, const char* path);
 MG_API int mg_load_setup(void* ctx, const char* path, mg_setup_info* info);
 MG_API int mg_update_mass(void* ctx, double m0, mg_setup_info* info);
 
-/* Adaptive refinement of a setup -- the adaptive smooth-aggregation idea the
- * paper plans for the clover case (section "Setup procedure"): `passes` times,
- * relax every fine-level null vector `relax` times on the homogeneous system
- * D_p v = 0 with the current multigrid solver (v <- v - M D_p v, normalised,
- * M the even-odd form of the current cycle), then rebuild P and the coarse
- * operators from the relaxed vectors.  What survives the relaxation is the
- * part of the near-null space the current coarse space misses.  Coarser
- * levels keep their null vectors.  `info` (may be NULL) as mg_setup, setup_ms
- * being the whole call.  Errors: MG_ERR_ARG, MG_ERR_STATE, MG_ERR_GS_BREAKDOWN,
+/* Adaptive refinement of a setup -- the adaptive idea the paper plans for the
+ * clover case (section "Setup procedure"), with the current multigrid solver
+ * as the approximate inverse: `passes` times, and for each of the `transfers`
+ * finest transfers (0: all), from the finest down, take each of its null
+ * vectors through `relax` steps of inverse subspace iteration on its level,
+ * v_k <- M v_k (M ~ D_p^{-1}: the even-odd reduction of the level and one of
+ * its cycles), Gram-Schmidt against v_0 .. v_{k-1} and normalised; then
+ * rebuild P and the coarse operators, the transfers below that level being
+ * set up afresh (inverse iteration, as mg_setup) on the refined coarse
+ * operator.  `info` (may be NULL) as mg_setup, setup_ms being the whole call.
+ * Errors: MG_ERR_ARG (passes or relax < 1, transfers < 0), MG_ERR_STATE,
+ * MG_ERR_DIMS (a relaxed coarse level with an odd extent),
+ * MG_ERR_GS_BREAKDOWN (a vector lost in the iteration or in a block),
  * MG_ERR_CUDA. */
-MG_API int mg_adapt_setup(void* ctx, int passes, int relax, mg_setup_info* info);
+MG_API int mg_adapt_setup(void* ctx, int passes, int relax, int transfers, mg_setup_info* info);
 
-/* Read the coarse operator of level `level` (1 .. levels-1) after mg_setup,/* Read the coarse operator of level `level` (1 .. levels-1) after mg_setup,
+/* Read the coarse operator of level `level` (1 .. levels-1) after mg_setup,
  * as the solver applies it: the Galerkin links of section "Implementation"
  * (D_hat v(x) = X(x) v(x) + sum_d Y_d(x) v(x + d), d < 4: from x + mu,
  * d >= 4: from x - mu), dequantised from their storage format (FP16/BF16

@@ -122,7 +122,7 @@ def lib() -> ctypes.CDLL:
             "mg_save_setup": [vp, ctypes.c_char_p],
             "mg_load_setup": [vp, ctypes.c_char_p, ctypes.POINTER(mg_setup_info)],
             "mg_update_mass": [vp, dp, ctypes.POINTER(mg_setup_info)],
-            "mg_adapt_setup": [vp, ip, ip, ctypes.POINTER(mg_setup_info)],
+            "mg_adapt_setup": [vp, ip, ip, ip, ctypes.POINTER(mg_setup_info)],
             "mg_solve_batch": [ctypes.POINTER(vp), ip, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ip), dp,
                                ip, ctypes.POINTER(mg_solve_info)],
             "mg_apply": [vp, ip, ip, vp, vp, ip, ip, ip],
@@ -283,9 +283,9 @@ def mg_update_mass(ctx, m0: float) -> mg_setup_info:
     return info
 
 
-def mg_adapt_setup(ctx, passes: int = 1, relax: int = 2) -> mg_setup_info:
+def mg_adapt_setup(ctx, passes: int = 1, relax: int = 2, transfers: int = 1) -> mg_setup_info:
     info = mg_setup_info()
-    _check(lib().mg_adapt_setup(ctx, int(passes), int(relax), ctypes.byref(info)), "mg_adapt_setup")
+    _check(lib().mg_adapt_setup(ctx, int(passes), int(relax), int(transfers), ctypes.byref(info)), "mg_adapt_setup")
     return info
 
 

@@ -484,17 +484,23 @@ int mg_load_setup(void* ctx, const char* path, mg_setup_info* info) {
   });
 }
 
-int mg_adapt_setup(void* ctx, int passes, int relax, mg_setup_info* info) {
+int mg_adapt_setup(void* ctx, int passes, int relax, int transfers, mg_setup_info* info) {
   return guarded([&]() {
     const auto t0 = std::chrono::steady_clock::now();
     mg::Ctx* c = as_ctx(ctx);
     if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
-    if (passes < 1 || relax < 1) mg::raise(MG_ERR_ARG, "passes and relax must be positive");
-    for (int p = 0; p < passes; p++) {
-      mg::mg_relax_null_vectors(c, relax);
-      std::vector<std::vector<double>> vecs = current_vectors(c);
-      rebuild_from(c, vecs, info);
-    }
+    if (passes < 1 || relax < 1 || transfers < 0) mg::raise(MG_ERR_ARG, "passes and relax must be positive");
+    const int nt = transfers == 0 ? c->params.levels - 1 : std::min(transfers, c->params.levels - 1);
+    // every pass refines the transfers from the finest down; after each, the
+    // coarser transfers are set up afresh (inverse iteration) on the refined
+    // coarse operator, whose near-null space their old vectors no longer span
+    for (int p = 0; p < passes; p++)
+      for (int l = 0; l < nt; l++) {
+        mg::mg_relax_null_vectors(c, l, relax);
+        std::vector<std::vector<double>> vecs = current_vectors(c);
+        vecs.resize(l + 1);
+        rebuild_from(c, vecs, info);
+      }
     if (info)
       info->setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return (int)MG_OK;

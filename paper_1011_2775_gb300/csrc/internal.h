@@ -360,8 +360,8 @@ bool mg_batch_joinable(Ctx* c);
 void mg_cycle_batch(Ctx* c, double* out_abi, const double* in_abi, int nb);
 void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in_abi);
 void mg_get_vectors(Ctx* c, int level, double* V_abi, int nv);
-// relaxes the fine-level null vectors with the current solver (multigrid.cu)
-void mg_relax_null_vectors(Ctx* c, int relax);
+// relaxes the null vectors of transfer `level` with the current solver (multigrid.cu)
+void mg_relax_null_vectors(Ctx* c, int level, int relax);
 // dequantised coarse links of level >= 1 (ABI layouts, see mg_get_coarse_links)
 void mg_get_links(Ctx* c, int level, double* Y_abi, double* X_abi);
 void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof);

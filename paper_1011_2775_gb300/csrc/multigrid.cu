@@ -799,7 +799,7 @@ void mg_get_links(Ctx* c, int level, double* Y_abi, double* X_abi) {
   coarse_links_abi(H.geo[level], H.cop[level], Y_abi, X_abi, c->stream);
 }
 
-// Adaptive refinement of the fine-level null vectors (the alpha-SA idea the
+// Adaptive refinement of the null vectors of transfer `level` (the alpha-SA idea the
 // paper plans for the clover case, section "Setup procedure"): every vector v
 // is relaxed on the homogeneous system D_p v = 0 with the current multigrid
 // solver, v <- v - M D_p v, normalised after each step, where M ~ D_p^{-1} is
@@ -809,32 +809,55 @@ void mg_get_links(Ctx* c, int level, double* Y_abi, double* X_abi) {
 // Components the current coarse space represents well are removed; what is
 // left is rich in the modes the solver resolves poorly.  The caller rebuilds
 // the hierarchy from the relaxed vectors.
-void mg_relax_null_vectors(Ctx* c, int relax) {
-  if (!c->mg || c->mg->L < 2) raise(MG_ERR_STATE, "multigrid not set up");
+void mg_relax_null_vectors(Ctx* c, int level, int relax) {
+  if (!c->mg || level < 0 || level + 1 >= c->mg->L) raise(MG_ERR_STATE, "no transfer from this level");
   Hierarchy& H = *c->mg;
-  const size_t nf = full_n(H, 0), nh = half_n(H, 0), hs = 2 * nh;
+  const int l = level;
+  const size_t nf = full_n(H, l), nh = half_n(H, l), hs = 2 * nh;
   cudaStream_t s = c->stream;
-  FineOps<float>& F = *H.F32;
-  DBuf tb(sizeof(float) * 2 * nf), ub(sizeof(float) * 2 * nf), gb(sizeof(float) * hs), sb(sizeof(float) * hs);
-  float* te = tb.as<float>();
-  float* to = te + hs;
+  if (l > 0 && !H.geo[l].eo) raise(MG_ERR_DIMS, "level has an odd extent");
+  DBuf ub(sizeof(float) * 2 * nf), gb(sizeof(float) * 2 * nf), sb(sizeof(float) * 2 * nf);
   float* ue = ub.as<float>();
   float* uo = ue + hs;
   float* ge = gb.as<float>();
   float* se = sb.as<float>();
   double* scr = c->ws.scalars.as<double>() + 1024;
-  for (int k = 0; k < H.tr[0].nv; k++) {
-    float* ve = H.nullvecs[0].as<float>() + (size_t)k * 2 * nf;
+  const int nv = H.tr[l].nv;
+  float* base = H.nullvecs[l].as<float>();
+  std::vector<const float*> prev(nv);
+  for (int k = 0; k < nv; k++) prev[k] = base + (size_t)k * 2 * nf;
+  // inverse subspace iteration with the current solver of the level as the
+  // approximate inverse: v_k <- M v_k, M = D_p^{-1} through the even-odd
+  // reduction and one cycle, then Gram-Schmidt against v_0 .. v_{k-1}
+  for (int k = 0; k < nv; k++) {
+    float* ve = base + (size_t)k * 2 * nf;
     float* vo = ve + hs;
     for (int it = 0; it < relax; it++) {
-      F.Dp(te, to, ve, vo);                                                  // t = D_p v
-      F.br(ge, te, to);                                                      // g_e = t_e - X t_o
-      mg_precondition(c, ue, ge);                                            // u_e = K g_e
-      clover_apply<float>(c->g, se, ue, c->Ainv<float>(0), s);              // A_e^{-1} u_e
-      dslash<float>(c->g, EPI_XPAY, 1, uo, se, c->gauge<float>(), nullptr, to, -1.0, 0xff, s);  // u_o = t_o - Y u_e
-      blas_axpby<float>(-1.0, ue, 1.0, ve, nf, s);                         // v -= u (both halves)
-      blas_norm2<float>(ve, nf, scr, c->ws, s);
-      blas_normalize<float>(ve, scr, nf, s);
+      if (l == 0) {
+        FineOps<float>& F = *H.F32;
+        F.br(ge, ve, vo);                                                    // g_e = v_e - X v_o
+        cycle(c, H, 0, ue, ge);                                              // u_e = K g_e
+        clover_apply<float>(c->g, se, ue, c->Ainv<float>(0), s);            // A_e^{-1} u_e
+        dslash<float>(c->g, EPI_XPAY, 1, uo, se, c->gauge<float>(), nullptr, vo, -1.0, 0xff, s);  // u_o = v_o - Y u_e
+      } else {
+        // the same on a coarse level: vectors are full coarse vectors, even sites first
+        const LevelGeom& G = H.geo[l];
+        const CoarseOp& C = H.cop[l];
+        br_level(c, H, l, ge, ve);                                           // g_e = v_e - Y_eo X_o^{-1} v_o
+        blas_zero<float>(ue, nf, s);
+        cycle(c, H, l, ue, ge);                                              // u_e = K g_e
+        coarse_site_mul(G, C, true, 0, G.half, se, ue, s);                   // X_e^{-1} u_e
+        coarse_hop(G, C, EPI_XPAY, false, G.half, G.nsites, ue, se, ve, -1.f, 0xff, s);  // u_o = v_o - Y_oe .
+      }
+      blas_convert<float, float>(ve, ue, nf, s);                            // v = M v
+      for (int rep = 0; rep < 2 && k > 0; rep++) {
+        blas_multidot<float>(prev.data(), k, ve, nf, scr, c->ws, s);
+        blas_lincomb<float, float>(ve, prev.data(), scr, k, -1.0, nf, s);
+      }
+      blas_norm2<float>(ve, nf, scr + 512, c->ws, s);
+      const double nn = c->read_scalar(scr + 512);
+      if (!std::isfinite(nn) || nn == 0.0) raise(MG_ERR_GS_BREAKDOWN, "null vector lost in the adaptive iteration");
+      blas_normalize<float>(ve, scr + 512, nf, s);
     }
   }
   c->sync();

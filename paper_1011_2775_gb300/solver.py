@@ -109,9 +109,10 @@ class Solver:
         """New bare mass, hierarchy rebuilt from the current null vectors (no inverse iteration)."""
         return B.mg_update_mass(self.ctx, m0)
 
-    def adapt_setup(self, passes: int = 1, relax: int = 2):
-        """Adaptive refinement: relax the null vectors with the current solver and rebuild."""
-        return B.mg_adapt_setup(self.ctx, passes, relax)
+    def adapt_setup(self, passes: int = 1, relax: int = 2, transfers: int = 1):
+        """Adaptive refinement: relax the null vectors of the `transfers` finest transfers (0: all)
+        with the current solver and rebuild."""
+        return B.mg_adapt_setup(self.ctx, passes, relax, transfers)
 
     def setup(self):
         return B.mg_setup(self.ctx)

@@ -112,9 +112,9 @@ def test_update_mass_reuses_null_vectors():
 
 
 def test_adaptive_setup_improves_a_weak_setup():
-    """mg_adapt_setup (alpha-SA style refinement): after a deliberately weak setup
-    (one inverse-iteration pass per vector), one adaptive pass -- relaxing each
-    null vector with the current solver and rebuilding -- lowers the outer
+    """mg_adapt_setup: after a deliberately weak setup (one inverse-iteration
+    pass per vector), one adaptive pass -- inverse subspace iteration of the
+    null vectors with the current solver, then a rebuild -- lowers the outer
     iteration count, and the solve still reaches 1e-10 with the oracle's D."""
     from paper_1011_2775_gb300 import binding as B
     U = I.make_gauge(DIMS, 1.0, 5, 0.5, 8401)
@@ -129,4 +129,46 @@ def test_adaptive_setup_improves_a_weak_setup():
     psi, adapted = S.solve(eta, 1e-10, B.MG_MODE_MG)
     assert _res(W, psi, eta) <= 1e-10
     assert adapted.outer_iterations < weak.outer_iterations
+    S.close()
+
+
+def test_adaptive_setup_three_levels():
+    """On three levels the adaptive pass refines both transfers (the level-1
+    vectors iterated with the level-1 cycle); the solve still reaches 1e-10 and
+    needs fewer outer iterations than the weak setup it started from."""
+    from paper_1011_2775_gb300 import binding as B
+    U = I.make_gauge(DIMS, 1.0, 5, 0.5, 8501)
+    W = WilsonClover(U, 1.0, -0.6)
+    eta = I.gaussian_source(DIMS, 8502)
+    S = _solver(U, -0.6)
+    S.set_params(levels=3, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 8], seed=8503, setup_iters=1,
+                 maxit_fine=4000)
+    S.setup()
+    _, weak = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    S.adapt_setup(passes=1, relax=3, transfers=0)
+    psi, adapted = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _res(W, psi, eta) <= 1e-10
+    assert adapted.outer_iterations < weak.outer_iterations
+    S.close()
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_adaptive_setup_keeps_a_good_setup(levels):
+    """The refinement must not undo a converged setup: the inverse iteration
+    keeps the low modes the coarse space already holds (replacing v by the
+    error propagator's (1 - M D_p) v would remove exactly those)."""
+    from paper_1011_2775_gb300 import binding as B
+    U = I.make_gauge(DIMS, 1.0, 5, 0.5, 8601)
+    W = WilsonClover(U, 1.0, -0.6)
+    eta = I.gaussian_source(DIMS, 8602)
+    S = _solver(U, -0.6)
+    blocks = [(4, 4, 4, 4)] if levels == 2 else [(2, 2, 2, 2), (2, 2, 2, 2)]
+    S.set_params(levels=levels, blocks=blocks, nv=[12] if levels == 2 else [8, 8], seed=8603, setup_iters=6,
+                 maxit_fine=4000)
+    S.setup()
+    _, good = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    S.adapt_setup(passes=1, relax=2, transfers=0)
+    psi, adapted = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _res(W, psi, eta) <= 1e-10
+    assert adapted.outer_iterations <= good.outer_iterations + 2
     S.close()
