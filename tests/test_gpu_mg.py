@@ -93,6 +93,89 @@ def test_coarse_operator_parity(injected3, level, op):
     assert rel(got, ref) <= TOL32
 
 
+@pytest.fixture(scope="module")
+def injected3_odd():
+    """3 levels on 12x8x8x8 whose coarsest lattice (3x2x2x2) has an odd extent,
+    so it is solved without even-odd: blocks 2^4 (Nv = 8) then 2^4 (Nv = 6),
+    vectors injected; coarse solves to 1e-6 so that the cycles can be compared."""
+    dims = (12, 8, 8, 8)
+    U = I.make_gauge(dims, 0.4, 1, 0.5, 3101)
+    W = WilsonClover(U, 1.0, -0.2)
+    V0 = _vectors(79, 0, 8, W.shape, 12)
+    V1 = _vectors(80, 1, 6, (4, 4, 4, 6), 16)
+    cp = dict(tol_coarse=1e-6, maxit_coarse=400, restart_coarse=64, nu_post=2)
+    mg = Multigrid(W, MGParams(blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 6], **cp), null_vectors=[V0, V1])
+    S = _solver(dims, U, 1.0, -0.2)
+    S.set_params(levels=3, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 6], **cp)
+    S.set_null_vectors(0, np.ascontiguousarray(np.stack(V0)))
+    S.set_null_vectors(1, np.ascontiguousarray(np.stack(V1)))
+    S.setup()
+    yield dims, W, mg, S
+    S.close()
+
+
+@pytest.mark.parametrize("level,op", [(1, "D"), (1, "DP"), (1, "DR"), (1, "BR"), (1, "MINV"), (2, "D"), (2, "DP"),
+                                      (2, "M"), (2, "MINV"), (2, "HOP")])
+def test_odd_coarsest_operator_parity(injected3_odd, level, op):
+    from paper_1011_2775_gb300 import binding as B
+    dims, W, mg, S = injected3_odd
+    assert S.level_info(2) == ((3, 2, 2, 2), 12)
+    C = mg.levels[level]
+    rng = np.random.default_rng(20 + level)
+    v = rng.standard_normal(C.shape + (C.ndof,)) + 1j * rng.standard_normal(C.shape + (C.ndof,))
+    ref = {"D": C.D, "DP": C.Dp, "DR": lambda x: C.Dr(x * C.even), "BR": C.b_r, "M": C.M, "MINV": C.Minv,
+           "HOP": C.hop}[op](v)
+    got = S.apply(getattr(B, "MG_OP_" + op), np.ascontiguousarray(v), level=level)
+    assert rel(got, ref) <= TOL32
+
+
+def test_odd_coarsest_rejects_even_odd_ops(injected3_odd):
+    from paper_1011_2775_gb300 import binding as B
+    dims, W, mg, S = injected3_odd
+    C = mg.levels[2]
+    v = np.ones(C.shape + (C.ndof,), dtype=np.complex128)
+    for op in (B.MG_OP_DR, B.MG_OP_BR):
+        with pytest.raises(B.MGError) as e:
+            S.apply(op, v, level=2)
+        assert e.value.status == B.MG_ERR_DIMS
+
+
+@pytest.mark.parametrize("level", [1, 0])
+def test_odd_coarsest_cycle_parity(injected3_odd, level):
+    """The K-cycle of level 1 (its coarse solve: GCR on the full coarsest D)
+    and of the fine level (a level-1 GCR preconditioned by that cycle) against
+    the oracle's, on even-site input."""
+    from paper_1011_2775_gb300 import binding as B
+    dims, W, mg, S = injected3_odd
+    lev = mg.levels[level]
+    rng = np.random.default_rng(30 + level)
+    r = rng.standard_normal(lev.shape + (lev.ndof,)) + 1j * rng.standard_normal(lev.shape + (lev.ndof,))
+    ref = mg.cycle(level, r * lev.even)
+    got = S.apply(B.MG_OP_CYCLE, np.ascontiguousarray(r), level=level)
+    assert rel(got, ref) <= 1e-4
+
+
+def test_odd_coarsest_solve_and_adaptive_refinement():
+    """A 3-level solve whose coarsest lattice has an odd extent reaches 1e-10
+    with the oracle's D, before and after refining both transfers."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (12, 8, 8, 16)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 5101)
+    W = WilsonClover(U, 1.0, -0.6)
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(levels=3, blocks=[(2, 2, 2, 2), (2, 2, 2, 2)], nv=[8, 8], setup_iters=6, maxit_fine=3000)
+    S.setup()
+    assert S.level_info(2)[0] == (3, 2, 2, 4)
+    eta = I.gaussian_source(dims, 5102)
+    psi, good = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _true_residual(W, psi, eta) <= 1e-10
+    S.adapt_setup(passes=1, relax=2, transfers=0)
+    psi, adapted = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert _true_residual(W, psi, eta) <= 1e-10
+    assert adapted.outer_iterations <= good.outer_iterations + 2
+    S.close()
+
+
 def test_setup_P_orthonormal_and_chiral():
     """Setup without injection: R P = I on coarse vectors (P^dag P = I) and
     gamma_5 P = P gamma_5c."""
