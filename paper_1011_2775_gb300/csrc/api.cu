@@ -323,6 +323,8 @@ int mg_set_params(void* ctx, const mg_params* p) {
     if (setup_changed) {
       c->mg.reset();
       c->injected.assign(MG_MAX_LEVELS, std::vector<double>());
+    } else {
+      mg::mg_solve_params_changed(c);
     }
     c->solve_work.reset();
     c->block_work.reset();

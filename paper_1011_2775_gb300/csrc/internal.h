@@ -348,6 +348,8 @@ void mg_precondition(Ctx* c, float* z_e, const float* r_e);
 // the same from an FP64 residual through a captured CUDA graph (r32: FP32
 // staging); false when graphs are off or unavailable (see multigrid.cu)
 bool mg_precondition_graph(Ctx* c, float* z_e, const double* r_e, float* r32);
+// solve parameters changed with the setup kept: drop what was captured with the old ones
+void mg_solve_params_changed(Ctx* c);
 // the same for nb right-hand sides (packed half vectors, stride 24 Vh floats)
 void mg_precondition_batch(Ctx* c, float* z_e, const float* r_e, int nb);
 // mg_precondition_batch in three steps around the coarsest solve, so that

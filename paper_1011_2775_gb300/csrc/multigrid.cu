@@ -106,6 +106,15 @@ struct CycleGraph {
   bool failed = false;
   long long dslash = 0, kernels = 0;   // launches one replay executes (for the statistics)
   DBuf zc;                      // the graph's output
+  // the captured cycle bakes in the smoothing steps, coarse tolerance and caps:
+  // drop it when they change so that the next solve captures it afresh
+  void drop() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    r = nullptr;
+    r32 = nullptr;
+    failed = false;
+  }
   ~CycleGraph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (cap) cudaStreamDestroy(cap);
@@ -734,6 +743,12 @@ bool mg_precondition_graph(Ctx* c, float* z_e, const double* r_e, float* r32) {
   add_launches(G.kernels);
   MG_CUDA(cudaMemcpyAsync(z_e, G.zc.get(), sizeof(float) * 2 * n, cudaMemcpyDeviceToDevice, c->stream));
   return true;
+}
+
+void mg_solve_params_changed(Ctx* c) {
+  if (!c->mg || !c->mg->graph.exec) return;
+  MG_CUDA(cudaStreamSynchronize(c->stream));   // no replay in flight
+  c->mg->graph.drop();
 }
 
 void mg_precondition(Ctx* c, float* z_e, const float* r_e) {

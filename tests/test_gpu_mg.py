@@ -176,6 +176,34 @@ def test_odd_coarsest_solve_and_adaptive_refinement():
     S.close()
 
 
+def test_changed_solve_params_take_effect_with_graphs():
+    """Smoothing steps and the coarse tolerance changed between solves (setup
+    kept) reach the captured cycle graph: the solve then iterates exactly as a
+    context set up with those parameters from the start."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (8, 8, 8, 16)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 5301)
+    eta = I.gaussian_source(dims, 5302)
+    mg = dict(levels=2, blocks=[(4, 4, 4, 4)], nv=[12], seed=5303, maxit_fine=3000)
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(nu_post=4, tol_coarse=0.1, **mg)
+    S.setup()
+    _, a = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    _, a2 = S.solve(eta, 1e-10, B.MG_MODE_MG)            # graph replays
+    assert a2.outer_iterations == a.outer_iterations
+    S.set_params(nu_post=1, tol_coarse=0.5)
+    _, b = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    F = _solver(dims, U, 1.0, -0.6)
+    F.set_params(nu_post=1, tol_coarse=0.5, **mg)
+    F.setup()
+    _, c = F.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert b.outer_iterations == c.outer_iterations
+    assert b.coarse_iterations[1] == c.coarse_iterations[1]
+    assert b.outer_iterations != a.outer_iterations
+    S.close()
+    F.close()
+
+
 def test_setup_P_orthonormal_and_chiral():
     """Setup without injection: R P = I on coarse vectors (P^dag P = I) and
     gamma_5 P = P gamma_5c."""
