@@ -436,7 +436,8 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     out["cuda_graph"] = {"graph_ms": tg[1], "direct_launch_ms": tg[0], "speedup": tg[0] / tg[1]}
     del e_g, p_g
 
-    # ---- the mass sweep of the workload: MG-GCR, and plain EO-GCR capped at SWEEP_EO_CAP iterations
+    # ---- the mass sweep of the workload: MG-GCR, and plain EO-GCR and mixed-precision BiCGStab
+    #      capped at SWEEP_EO_CAP iterations
     sweep = []
     for m0 in MASSES:
         Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
@@ -450,9 +451,14 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
         t_mg, (_, mi) = timed(lambda: Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
         Q.set_params(maxit_fine=SWEEP_EO_CAP)
         t_eo, (st, ei) = timed(lambda: B.mg_solve(Q.ctx, p_d, e_d, 1, TOL, B.MG_MODE_EO_GCR, allow_not_converged=True))
+        B.mg_solve(Q.ctx, p_d, e_d, 1, 1e-2, B.MG_MODE_BICGSTAB_MP, allow_not_converged=True)   # buffers
+        t_bi, (sb, bi) = timed(lambda: B.mg_solve(Q.ctx, p_d, e_d, 1, TOL, B.MG_MODE_BICGSTAB_MP,
+                                                  allow_not_converged=True))
         sweep.append({"m0": m0, "mg_ms": t_mg, "mg_outer_iterations": mi.outer_iterations,
                       "mg_true_residual": mi.true_residual, "eo_gcr_ms": t_eo, "eo_gcr_iterations": ei.outer_iterations,
-                      "eo_gcr_true_residual": ei.true_residual, "eo_gcr_converged": st == B.MG_OK})
+                      "eo_gcr_true_residual": ei.true_residual, "eo_gcr_converged": st == B.MG_OK,
+                      "bicgstab_mixed_ms": t_bi, "bicgstab_mixed_iterations": bi.outer_iterations,
+                      "bicgstab_mixed_true_residual": bi.true_residual, "bicgstab_mixed_converged": sb == B.MG_OK})
         Q.close()
     out["mass_sweep"] = sweep
 
@@ -526,6 +532,96 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     out["fp16_storage"] = {"ms": statistics.median(ts), "outer_iterations": qi.outer_iterations,
                            "coarse_iterations": qi.coarse_iterations[1], "true_residual": qi.true_residual}
     Q.close()
+    out["krylov"] = run_krylov(dev, flush, stream)
+    return out
+
+
+# The Krylov comparison (the paper's time-to-solution vs. mass, speedup vs.
+# tolerance and error/residual axes) on a rougher ensemble of the same shape,
+# eps = 1.0 + 5 APE, whose critical mass lies below -0.65: the masses swept
+# toward it stay subcritical there, so the plain Krylov solvers converge.
+KRYLOV_EPS = 1.0
+KRYLOV_MASSES = (-0.35, -0.5, -0.65)
+KRYLOV_MAXIT = 10000                 # iteration cap of the comparison solvers
+KRYLOV_TOLS = (1e-6, 1e-8, 1e-10)
+ERROR_TOLS = (1e-4, 1e-6, 1e-8, 1e-10)
+
+
+def run_krylov(dev: int, flush, stream) -> dict:
+    """MG-GCR against BiCGStab (FP64 and mixed precision), CGNR and EO-GCR per
+    mass; MG against mixed-precision BiCGStab per tolerance at the lightest
+    mass; and the error/residual ratio of MG and BiCGStab for a manufactured
+    solution b = D x0 (x0 = an approximate solution for a point source)."""
+    import numpy as np
+    import torch
+    from paper_1011_2775_gb300 import binding as B
+    from paper_1011_2775_gb300 import inputs as I
+    from paper_1011_2775_gb300.solver import Solver
+
+    def timed(fn):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), res
+
+    U = I.make_gauge(DIMS, KRYLOV_EPS, APE, ALPHA, GAUGE_SEED)
+    eta_d = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED)).to(f"cuda:{dev}")
+    psi_d = torch.zeros_like(eta_d)
+    modes = [("mg", B.MG_MODE_MG), ("bicgstab", B.MG_MODE_BICGSTAB), ("bicgstab_mixed", B.MG_MODE_BICGSTAB_MP),
+             ("cgnr", B.MG_MODE_CGNR), ("eo_gcr", B.MG_MODE_EO_GCR)]
+    out = {"ensemble": f"{DIMS[0]}^3x{DIMS[3]}, eps={KRYLOV_EPS}+{APE} APE(alpha={ALPHA}), csw={CSW}",
+           "iteration_cap": KRYLOV_MAXIT, "masses": []}
+
+    def solve_row(S, mode, tol):
+        S.solve(eta_d, 1e-2, mode, out=psi_d, allow_not_converged=True)     # buffers allocated outside the timing
+        ms, (st, info) = timed(lambda: B.mg_solve(S.ctx, psi_d, eta_d, 1, tol, mode, allow_not_converged=True))
+        return {"ms": ms, "iterations": info.outer_iterations, "converged": st == B.MG_OK,
+                "true_residual": info.true_residual}
+
+    S = None
+    for m0 in KRYLOV_MASSES:
+        S = Solver(DIMS, device=dev, stream=stream.cuda_stream)
+        S.load_gauge(U)
+        S.set_clover(CSW, m0)
+        S.set_params(seed=NULLVEC_SEED, maxit_fine=KRYLOV_MAXIT, **MG)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S.setup()
+        row = {"m0": m0, "mg_setup_ms": 1e3 * (time.perf_counter() - t0)}
+        for name, mode in modes:
+            row[name] = solve_row(S, mode, TOL)
+        out["masses"].append(row)
+        if m0 != KRYLOV_MASSES[-1]:
+            S.close()
+    # speedup vs. requested tolerance at the lightest mass (S is still set up there)
+    out["tolerance"] = []
+    for tol in KRYLOV_TOLS:
+        mg_r = solve_row(S, B.MG_MODE_MG, tol)
+        bi_r = solve_row(S, B.MG_MODE_BICGSTAB_MP, tol)
+        out["tolerance"].append({"tol": tol, "mg_ms": mg_r["ms"], "bicgstab_mixed_ms": bi_r["ms"],
+                                 "speedup": bi_r["ms"] / mg_r["ms"], "mg_iterations": mg_r["iterations"],
+                                 "bicgstab_mixed_iterations": bi_r["iterations"]})
+    # error / residual with a manufactured solution
+    p = I.point_source(DIMS, 0, (0, 0, 0, 0))
+    x0, _ = S.solve(p, 1e-6, B.MG_MODE_MG)
+    b = S.apply(B.MG_OP_D, x0, prec=B.MG_FP64)
+    nb, nx = float(np.linalg.norm(b.ravel())), float(np.linalg.norm(x0.ravel()))
+    out["error_vs_residual"] = []
+    for tol in ERROR_TOLS:
+        for name, mode in (("mg", B.MG_MODE_MG), ("bicgstab", B.MG_MODE_BICGSTAB)):
+            x = np.zeros_like(b)
+            st, info = B.mg_solve(S.ctx, x, b, 1, tol, mode, allow_not_converged=True)
+            err = float(np.linalg.norm((x - x0).ravel()))
+            res = info.true_residual * nb
+            out["error_vs_residual"].append({"tol": tol, "solver": name, "residual": res, "error": err,
+                                             "error_over_residual": err / res if res > 0 else None,
+                                             "relative_error": err / nx})
+    S.close()
     return out
 
 
@@ -534,7 +630,7 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
 # gauge construction, m0 = -0.3, 2-level MG with 4^4 blocks and Nv = 24.
 MULTI = [((32, 32, 32, 64), "point", 12), ((16, 16, 16, 32), "gauss", 8), ((24, 24, 24, 48), "gauss", 8)]
 MULTI_M0 = -0.3
-SWEEP_EO_CAP = 2000                  # EO-GCR iteration cap in the mass sweep
+SWEEP_EO_CAP = 2000                  # EO-GCR and BiCGStab iteration cap in the mass sweep
 
 # The 3-level configuration: 24^3x64, same gauge construction, m0 = -0.35,
 # 4^4 blocks (Nv = 24) then 2^4 blocks (Nv = 32) onto a 3^3x8 coarsest lattice

@@ -89,14 +89,31 @@ enum mg_op {
   MG_OP_HOP = 6,        /* hopping term H alone                                            */
   MG_OP_R = 7,          /* restriction R = P^dag: level l vector -> level l+1 vector       */
   MG_OP_P = 8,          /* prolongation P: level l+1 vector -> level l vector              */
-  MG_OP_CYCLE = 9       /* one multigrid cycle K_l (the preconditioner of D_r on level l): */
+  MG_OP_CYCLE = 9,      /* one multigrid cycle K_l (the preconditioner of D_r on level l): */
                         /* reads the even sites of `in`, writes z_e ~ D_r^{-1} r_e to the  */
                         /* even sites of `out` and zeros its odd sites (FP32 arithmetic)   */
+  MG_OP_DR_DAG = 10     /* D_r^dag = gamma_5 M_e^{-1} D_r M_e gamma_5, fine level only (the */
+                        /* operator of CGNR); even sites as MG_OP_DR                        */
 };
 
 enum mg_prec { MG_FP64 = 0, MG_FP32 = 1 };
 enum mg_storage { MG_STORE_FP32 = 0, MG_STORE_FP16 = 1, MG_STORE_BF16 = 2 };
-enum mg_mode { MG_MODE_MG = 0, MG_MODE_EO_GCR = 1 };
+/* Solvers of the reduced system D_r y_e = b_r (section "Results" compares
+ * multigrid with the Krylov solvers in use):
+ *   MG_MODE_MG           multigrid-preconditioned FGCR (FP64 outer, FP32 cycle)
+ *   MG_MODE_EO_GCR       plain FP64 GCR(restart_fine)
+ *   MG_MODE_BICGSTAB     FP64 BiCGStab
+ *   MG_MODE_CGNR         FP64 CG on D_r^dag D_r y = D_r^dag b_r
+ *   MG_MODE_BICGSTAB_MP  mixed precision by iterative refinement: FP64
+ *                        residual, FP32 BiCGStab reducing it by 1e-4 per step
+ * All stop on the FP64 true residual of the full system (mg_solve). */
+enum mg_mode {
+  MG_MODE_MG = 0,
+  MG_MODE_EO_GCR = 1,
+  MG_MODE_BICGSTAB = 2,
+  MG_MODE_CGNR = 3,
+  MG_MODE_BICGSTAB_MP = 4
+};
 enum mg_coarse_op { MG_COARSE_DP = 0, MG_COARSE_D = 1 };
 /* Output of mg_force. */
 enum mg_force_kind {
@@ -264,7 +281,11 @@ MG_API int mg_get_coarse_links(void* ctx, int level, void* Y, void* X, int where
 
 /* Solve D psi = eta for nrhs right-hand sides (layout above) to
  * ||eta - D psi|| / ||eta|| <= tol, in MG_MODE_MG (multigrid-preconditioned
- * FGCR; needs mg_setup) or MG_MODE_EO_GCR (plain FP64 even-odd GCR).  In
+ * FGCR; needs mg_setup) or one of the unpreconditioned modes of enum mg_mode
+ * (maxit_fine caps the iterations of every mode; an iteration applies D_r
+ * once in GCR, twice in BiCGStab, D_r and D_r^dag in CGNR, and is one inner
+ * FP32 BiCGStab iteration in the mixed-precision mode, whose refinement steps
+ * are counted in info->restarts).  In
  * MG mode groups of up to mg_params.rhs_block right-hand sides are solved
  * together: one FGCR per right-hand side, run in lock-step so that every
  * iteration applies D_r to all of them in one multi-RHS launch and the

@@ -27,10 +27,10 @@ MG_ERR_CUDA, MG_ERR_ALLOC = -9, -10
 # where
 MG_HOST, MG_DEVICE = 0, 1
 # operators
-MG_OP_D, MG_OP_DP, MG_OP_DR, MG_OP_BR, MG_OP_M, MG_OP_MINV, MG_OP_HOP, MG_OP_R, MG_OP_P, MG_OP_CYCLE = range(10)
+MG_OP_D, MG_OP_DP, MG_OP_DR, MG_OP_BR, MG_OP_M, MG_OP_MINV, MG_OP_HOP, MG_OP_R, MG_OP_P, MG_OP_CYCLE, MG_OP_DR_DAG = range(11)
 MG_FP64, MG_FP32 = 0, 1
 MG_STORE_FP32, MG_STORE_FP16, MG_STORE_BF16 = 0, 1, 2
-MG_MODE_MG, MG_MODE_EO_GCR = 0, 1
+MG_MODE_MG, MG_MODE_EO_GCR, MG_MODE_BICGSTAB, MG_MODE_CGNR, MG_MODE_BICGSTAB_MP = range(5)
 MG_COARSE_DP, MG_COARSE_D = 0, 1
 MG_FORCE_SU3, MG_FORCE_WIRTINGER = 0, 1
 

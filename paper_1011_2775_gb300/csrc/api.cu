@@ -96,7 +96,7 @@ int solve_impl(void* ctx, void* psi, const void* eta, int nrhs, double tol, int 
   mg::Ctx* c = as_ctx(ctx);
   check_where(where);
   if (!psi || !eta || nrhs < 1 || !(tol > 0)) mg::raise(MG_ERR_ARG, "bad solve arguments");
-  if (mode != MG_MODE_MG && mode != MG_MODE_EO_GCR) mg::raise(MG_ERR_ARG, "bad mode");
+  if (mode < MG_MODE_MG || mode > MG_MODE_BICGSTAB_MP) mg::raise(MG_ERR_ARG, "bad mode");
   if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
   if (mode == MG_MODE_MG && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
   mg_solve_info local;
@@ -648,9 +648,10 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
     check_where(where);
     if (!out || !in || nrhs < 1) mg::raise(MG_ERR_ARG, "bad apply arguments");
     if (prec != MG_FP64 && prec != MG_FP32) mg::raise(MG_ERR_ARG, "bad precision");
-    if (op < MG_OP_D || op > MG_OP_CYCLE) mg::raise(MG_ERR_ARG, "bad operator");
+    if (op < MG_OP_D || op > MG_OP_DR_DAG) mg::raise(MG_ERR_ARG, "bad operator");
     if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
     if (level < 0 || level >= c->params.levels) mg::raise(MG_ERR_ARG, "level out of range");
+    if (op == MG_OP_DR_DAG && level != 0) mg::raise(MG_ERR_ARG, "D_r^dag is a fine-level operator");
     if ((level > 0 || op == MG_OP_R || op == MG_OP_P || op == MG_OP_CYCLE) && !c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
     if (op == MG_OP_CYCLE && level + 1 >= c->params.levels) mg::raise(MG_ERR_ARG, "no coarser level to cycle to");
     int ndof_in, ndof_out;
@@ -684,6 +685,11 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
         using T = std::remove_pointer_t<decltype(tag)>;
         mg::FineOps<T> F(c);
         T *ie_ = (T*)ie, *io_ = (T*)io, *oe_ = (T*)oe, *oo_ = (T*)oo;
+        if (op == MG_OP_DR_DAG) {
+          mg::DBuf tmp(sizeof(T) * half);
+          for (int r = 0; r < nrhs; r++) mg::dr_dagger<T>(c, F, oe_ + half * r, ie_ + half * r, tmp.as<T>());
+          return;
+        }
         if (nrhs == 1) {
           switch (op) {
             case MG_OP_D: F.D(oe_, oo_, ie_, io_); break;

@@ -5,7 +5,9 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <complex>
 #include <functional>
+#include <initializer_list>
 #include <memory>
 #include <string>
 #include <vector>
@@ -310,6 +312,43 @@ class GCR {
   DBuf r_, tmp_;
   DBuf scal_;
   double* s_;  // device scalars: beta[m*m*2], alpha[m*2], gamma[m], c[m*2], misc
+};
+
+// --------------------------------------------------------------------------- comparison Krylov solvers (krylov.cu)
+// D_r^dag in = gamma_5 A_e^{-1} D_r A_e gamma_5 in on even half vectors (tmp: one half vector)
+template <typename T>
+void dr_dagger(Ctx* c, FineOps<T>& F, T* out, const T* in, T* tmp);
+
+// BiCGStab and CGNR on n complex unknowns; the iteration scalars go through
+// the host (a few synchronisations per iteration)
+template <typename T>
+class Krylov {
+ public:
+  using Op = std::function<void(T* out, const T* in)>;
+  struct Result {
+    int iterations = 0;
+    int restarts = 0;
+    double rnorm = 0;
+    bool converged = false;
+  };
+  Krylov(Ctx* c, size_t n);
+  ~Krylov();
+  Krylov(const Krylov&) = delete;
+  Krylov& operator=(const Krylov&) = delete;
+  // A x = b from x = 0 (x0_zero) or from x, until ||b - A x|| <= tol_abs
+  // (recursive residual) or maxit iterations (two applications of A each)
+  Result bicgstab(const Op& A, T* x, const T* b, bool x0_zero, double tol_abs, int maxit);
+  // CG on A^dag A x = A^dag b until ||b - A x|| <= tol_abs or maxit
+  // iterations (one application of A and one of A^dag each)
+  Result cgnr(const Op& A, const Op& Adag, T* x, const T* b, bool x0_zero, double tol_abs, int maxit);
+
+ private:
+  const double* coefs(std::initializer_list<std::complex<double>> z);
+  Ctx* c_;
+  size_t n_;
+  DBuf r_, rh_, p_, v_, s_, t_, q_;
+  DBuf sc_, coef_;
+  double* hcoef_ = nullptr;  // pinned staging of lincomb coefficients
 };
 
 // MR smoothing: e = MR_nu(A, r) from e = 0 (r is consumed as scratch)

@@ -8,6 +8,7 @@
 // cycle (back substitution of the triangular system).  In exact arithmetic
 // this is the textbook flexible GCR; deferring the update lets the
 // preconditioned directions z_j stay in the preconditioner's precision.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -392,8 +393,16 @@ struct SolveBuffers {
   std::unique_ptr<FineOps<double>> F64;
   std::unique_ptr<GCR<double, float>> gcr_mg;
   std::unique_ptr<GCR<double, double>> gcr_eo;
+  std::unique_ptr<FineOps<float>> F32;      // the comparison solvers' FP32 operator
+  std::unique_ptr<Krylov<double>> kry64;
+  std::unique_ptr<Krylov<float>> kry32;
+  DBuf dag;                                 // D_r^dag temporary
   int restart = 0;
 };
+
+// inner solve of the mixed-precision BiCGStab: residual reduction per
+// refinement step (FP32 BiCGStab)
+constexpr double kMixedInnerTol = 1e-4;
 }  // namespace
 
 
@@ -456,11 +465,52 @@ int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int m
       auto res = B->gcr_mg->solve(Aop, &pre, y, br, first, tol_r, maxit - used, true);
       used += res.iterations;
       restarts += res.restarts;
-    } else {
+    } else if (mode == MG_MODE_EO_GCR) {
       if (!B->gcr_eo) B->gcr_eo.reset(new GCR<double, double>(c, n, restart));
       auto res = B->gcr_eo->solve(Aop, nullptr, y, br, first, tol_r, maxit - used, true);
       used += res.iterations;
       restarts += res.restarts;
+    } else if (mode == MG_MODE_BICGSTAB || mode == MG_MODE_CGNR) {
+      if (!B->kry64) B->kry64.reset(new Krylov<double>(c, n));
+      Krylov<double>::Result res;
+      if (mode == MG_MODE_BICGSTAB) {
+        res = B->kry64->bicgstab(Aop, y, br, first, tol_r, maxit - used);
+      } else {
+        if (!B->dag.get()) B->dag.alloc(sizeof(double) * 2 * n);
+        auto Adag = [&](double* out, const double* in) { dr_dagger<double>(c, F, out, in, B->dag.as<double>()); };
+        res = B->kry64->cgnr(Aop, Adag, y, br, first, tol_r, maxit - used);
+      }
+      used += res.iterations;
+      restarts += res.restarts;
+    } else {
+      // mixed precision by iterative refinement: FP64 residual r = b_r - D_r y,
+      // FP32 BiCGStab for D_r e = r to kMixedInnerTol ||r||, y += e
+      if (!B->F32) B->F32.reset(new FineOps<float>(c));
+      if (!B->kry32) B->kry32.reset(new Krylov<float>(c, n));
+      FineOps<float>& F32 = *B->F32;
+      auto A32 = [&](float* out, const float* in) { F32.Dr(out, in); };
+      float* r32 = B->r32.as<float>();
+      float* e32 = B->z32.as<float>();
+      double* r = to;
+      if (first) blas_zero<double>(y, n, s);
+      while (used < maxit) {
+        F.Dr(te, y);
+        blas_convert<double, double>(r, br, n, s);
+        blas_axpby<double>(-1.0, te, 1.0, r, n, s);  // r = b_r - D_r y
+        blas_norm2<double>(r, n, d_scr, c->ws, s);
+        const double rn = std::sqrt(c->read_scalar(d_scr));
+        if (!std::isfinite(rn)) raise(MG_ERR_NAN, "non-finite residual in the refinement");
+        if (rn <= tol_r) break;
+        blas_convert<double, float>(r32, r, n, s);
+        auto res = B->kry32->bicgstab(A32, e32, r32, true, std::max(kMixedInnerTol * rn, tol_r), maxit - used);
+        used += res.iterations;
+        restarts++;
+        if (res.iterations == 0) break;
+        const float* Z[1] = {e32};
+        const double one[2] = {1.0, 0.0};
+        MG_CUDA(cudaMemcpyAsync(d_scr + 8, one, sizeof(one), cudaMemcpyHostToDevice, s));
+        blas_lincomb<double, float>(y, Z, d_scr + 8, 1, 1.0, n, s);  // y += e
+      }
     }
     first = false;
     F.reconstruct(xe, xo, y, bo);
