@@ -124,8 +124,14 @@ struct CoarseGCRBuffers {
 // x = D_hat^{-1} b to ||b - D_hat x|| <= tol_rel ||b|| (or maxit iterations) by
 // GCR(m) on the reduced even-odd system (or on D_hat itself when the level has
 // an odd extent); adds the iterations run to *d_iters (device)
+// (grid: blocks of the cooperative launch, 0 for B.grid; at most B.grid)
 void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuffers& B, int m, int maxit,
-                      double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s);
+                      double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s,
+                      int grid = 0);
+// smaller grids worth timing against B.grid: the fewest blocks that keep the
+// largest number of stencil sites per block, and one more site per block
+// (fewer blocks at every grid barrier)
+std::vector<int> coarse_gcr_smaller_grids(const LevelGeom& G, const CoarseGCRBuffers& B);
 
 // ---- batched coarsest solves (coarse_batch.cu)
 // One coarse system: the lattice and operator (a level of some context), its

@@ -487,8 +487,20 @@ int coarse_gcr_grid(int nc) {
   return sms * (per < 4 ? per : 4);
 }
 
+std::vector<int> coarse_gcr_smaller_grids(const LevelGeom& G, const CoarseGCRBuffers& B) {
+  const int target = G.eo ? G.half : G.nsites;
+  const int per = (target + B.grid - 1) / B.grid;  // sites per block on the full grid
+  std::vector<int> out;
+  for (int k = per; k <= per + 1; k++) {
+    const int g = (target + k - 1) / k;
+    if (g >= 1 && g < B.grid && (out.empty() || g < out.back())) out.push_back(g);
+  }
+  return out;
+}
+
 void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuffers& B, int m, int maxit,
-                      double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s) {
+                      double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s,
+                      int grid_blocks) {
   if (m > kMaxRestart) raise(MG_ERR_ARG, "coarse restart too long for the persistent solver");
   CGArgs a;
   a.nc = C.nc;
@@ -520,7 +532,7 @@ void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuff
   a.iters = d_iters;
   a.flags = flags;
   const size_t smem = sizeof(double) * (kNR * 8 + kNR) + sizeof(float2) * 10 * (size_t)C.nc;
-  const int grid = B.grid;
+  const int grid = grid_blocks > 0 && grid_blocks < B.grid ? grid_blocks : B.grid;
   void* params[] = {&a};
   const void* kern = C.store == STORE_F16    ? (const void*)k_coarse_gcr<kStF16>
                      : C.store == STORE_BF16 ? (const void*)k_coarse_gcr<kStBF16>

@@ -252,23 +252,29 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
   cudaStream_t s = c->stream;
   if (l + 1 == H.L) {
     // coarsest level: one persistent kernel, no host round trip.  Two
-    // implementations of the same GCR: the single-system kernel, and the
+    // implementations of the same GCR: the single-system kernel (on the full
+    // grid, or on a smaller one whose grid barriers have fewer blocks), and the
     // batched kernel with one system (row-blocked GEMV: fewer registers, more
-    // co-resident CTAs).  The autotuner times both on the first solve of this
+    // co-resident CTAs).  The autotuner times them on the first solve of this
     // lattice (the tuning runs do not count towards the iteration statistics).
     const int restart = p.restart_coarse > 0 ? p.restart_coarse : 32;
     long long* d_it = H.d_iters.as<long long>() + l;
+    const std::vector<int> smaller = coarse_gcr_smaller_grids(G, W.cg);
     auto run = [&](int which, long long* it) {
       if (which == 1)
         coarse_gcr_solve_batch(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, 1, b, x, it,
                                c->ws.flags.as<int>(), s);
       else
-        coarse_gcr_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, b, x, it, c->ws.flags.as<int>(), s);
+        coarse_gcr_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, b, x, it, c->ws.flags.as<int>(), s,
+                         which >= 2 ? smaller[which - 2] : 0);
     };
     if (W.coarse_impl < 0) {
       if (!W.tune_iters.get()) W.tune_iters.alloc(sizeof(long long));
       TuneKey key{"coarse_gcr", {G.L[0], G.L[1], G.L[2], G.L[3]}, H.cop[l].nc, H.cop[l].store};
-      W.coarse_impl = tuned_block(key, {0, 1}, [&](int which) { run(which, W.tune_iters.as<long long>()); }, s);
+      std::vector<int> cands = {0, 1};
+      for (size_t k = 0; k < smaller.size(); k++) cands.push_back(2 + (int)k);
+      W.coarse_impl = tuned_block(key, cands, [&](int which) { run(which, W.tune_iters.as<long long>()); }, s);
+      if (W.coarse_impl >= 2 + (int)smaller.size()) W.coarse_impl = 0;  // a cached choice from other grids
     }
     run(W.coarse_impl, d_it);
     return;
