@@ -63,3 +63,31 @@ def test_no_gpu_fails_cleanly(libpath):
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 4)(4, 4, 4, 4)
     assert B.lib().mg_create(ctypes.byref(h), d, 0, None) == B.MG_ERR_CUDA
+
+
+def _enumerators():
+    """Every `NAME = value` enumerator of the header's enums (values as written),
+    and the members of enums whose values are implicit (counted from the last)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for body in re.findall(r"enum\s+\w+\s*\{(.*?)\}", src, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            m = re.match(r"(MG_\w+)\s*(?:=\s*(-?\d+))?$", item)
+            assert m, item
+            val = int(m.group(2)) if m.group(2) is not None else nxt
+            out[m.group(1)] = val
+            nxt = val + 1
+    return out
+
+
+def test_binding_constants_match_the_header_enums():
+    from paper_1011_2775_gb300 import binding
+    enums = _enumerators()
+    assert len(enums) > 30
+    for name, val in enums.items():
+        assert hasattr(binding, name), name
+        assert getattr(binding, name) == val, name
