@@ -69,7 +69,8 @@ const double* Krylov<T>::coefs(std::initializer_list<cplx> z) {
 }
 
 // BiCGStab (van der Vorst) on A x = b.  Restarts (rh = r, p = v = 0) when
-// <rh, r> or <rh, A p> vanishes or omega does.  Convergence is tested on the
+// <rh, r> or <rh, A p> vanishes or omega does, and stops unconverged when the
+// breakdown recurs on the restart itself.  Convergence is tested on the
 // recursively updated residual at the half step (s) and the full step (r).
 template <typename T>
 typename Krylov<T>::Result Krylov<T>::bicgstab(const Op& A, T* x, const T* b, bool x0_zero, double tol_abs,
@@ -103,6 +104,7 @@ typename Krylov<T>::Result Krylov<T>::bicgstab(const Op& A, T* x, const T* b, bo
   bool fresh = true;
   cplx rho(1.0, 0.0), alpha(1.0, 0.0), omega(1.0, 0.0), rho_new;
   while (res.iterations < maxit) {
+    const bool restarted = fresh;
     if (fresh) {
       blas_convert<T, T>(rh, r, n, s);
       blas_convert<T, T>(p, r, n, s);
@@ -121,7 +123,10 @@ typename Krylov<T>::Result Krylov<T>::bicgstab(const Op& A, T* x, const T* b, bo
     c_->read_scalars(d, h, 2);
     const cplx rv(h[0], h[1]);
     if (!std::isfinite(h[0]) || !std::isfinite(h[1])) raise(MG_ERR_NAN, "non-finite scalar in BiCGStab");
-    if (std::abs(rv) <= 1e-30 * rn * rn) {  // breakdown: restart from the current residual
+    if (std::abs(rv) <= 1e-30 * rn * rn) {
+      // breakdown: restart from the current residual, unless this step already
+      // was the restart (<r, A r> = 0: no progress possible from here)
+      if (restarted) break;
       res.restarts++;
       fresh = true;
       continue;
