@@ -1,4 +1,5 @@
-"""Krylov solvers of the oracle: flexible GCR and minimal-residual relaxation.
+"""Krylov solvers of the oracle: flexible GCR, minimal-residual relaxation, and
+the comparison solvers BiCGStab and CGNR.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
@@ -99,3 +100,71 @@ def mr(A, r, nu: int):
         e = e + alpha * r
         r = r - alpha * w
     return e
+
+
+# ----------------------------------------------------------------------------- comparison solvers
+# The paper times multigrid against the Krylov solvers in use ("Results"):
+# BiCGStab, CG on the normal residual (CGNR) and a mixed-precision version by
+# iterative refinement.  The oracle restates the textbook methods; their
+# solutions are D^{-1} b like every other solve, so the GPU solvers are
+# checked by their true residuals with the oracle's D.
+
+def bicgstab(A, b, x0=None, tol_abs: float = 0.0, maxiter: int = 1000):
+    """BiCGStab (van der Vorst) for ``A x = b``: shadow residual ``r_hat = r_0``,
+    two applications of A per iteration, stop on ``||r|| <= tol_abs``."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A(x) if x0 is not None else b.copy()
+    info = SolveInfo(residual=math.sqrt(norm2(r)))
+    if info.residual <= tol_abs:
+        info.converged = True
+        return x, info
+    rh = r.copy()
+    rho = alpha = omega = 1.0 + 0j
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    for it in range(maxiter):
+        rho_new = inner(rh, r)
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = A(p)
+        alpha = rho_new / inner(rh, v)
+        s = r - alpha * v
+        t = A(s)
+        omega = inner(t, s) / inner(t, t)
+        x = x + alpha * p + omega * s
+        r = s - omega * t
+        rho = rho_new
+        info.iterations = it + 1
+        info.residual = math.sqrt(norm2(r))
+        info.history.append(info.residual)
+        if info.residual <= tol_abs:
+            info.converged = True
+            break
+    return x, info
+
+
+def cgnr(A, Adag, b, x0=None, tol_abs: float = 0.0, maxiter: int = 1000):
+    """CG on the normal equations ``A^dag A x = A^dag b`` (CGLS: the residual
+    ``r = b - A x`` is carried along and tested, ``||r|| <= tol_abs``)."""
+    x = np.zeros_like(b) if x0 is None else x0.copy()
+    r = b - A(x) if x0 is not None else b.copy()
+    z = Adag(r)
+    p = z.copy()
+    zz = norm2(z)
+    info = SolveInfo(residual=math.sqrt(norm2(r)))
+    for it in range(maxiter):
+        if info.residual <= tol_abs or zz == 0.0:
+            break
+        w = A(p)
+        a = zz / norm2(w)
+        x = x + a * p
+        r = r - a * w
+        z = Adag(r)
+        zz_new = norm2(z)
+        p = z + (zz_new / zz) * p
+        zz = zz_new
+        info.iterations = it + 1
+        info.residual = math.sqrt(norm2(r))
+        info.history.append(info.residual)
+    info.converged = info.residual <= tol_abs
+    return x, info

@@ -262,3 +262,42 @@ def test_free_field_mg_solve_matches_fft():
     assert info.converged
     ref = _free_solution(dims, m0, eta)
     assert np.abs(x.reshape(ref.shape) - ref).max() / np.abs(ref).max() < 1e-10
+
+
+def _random_system(n, seed):
+    rng = np.random.default_rng(seed)
+    M = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / np.sqrt(2 * n)
+    M += 2.0 * np.eye(n)                              # non-Hermitian, eigenvalues around 2
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    return M, b
+
+
+def test_bicgstab_and_cgnr_against_linalg_solve():
+    from oracle.krylov import bicgstab, cgnr
+    M, b = _random_system(60, 11)
+    ref = np.linalg.solve(M, b)
+    A = lambda v: M @ v
+    x, info = bicgstab(A, b, tol_abs=1e-12 * np.linalg.norm(b), maxiter=200)
+    assert info.converged and np.abs(x - ref).max() < 1e-10 * np.abs(ref).max()
+    x, info = cgnr(A, lambda v: M.conj().T @ v, b, tol_abs=1e-12 * np.linalg.norm(b), maxiter=400)
+    assert info.converged and np.abs(x - ref).max() < 1e-10 * np.abs(ref).max()
+    # a wrong adjoint (the transpose without conjugation) breaks CGNR on this complex system
+    _, bad = cgnr(A, lambda v: M.T @ v, b, tol_abs=1e-12 * np.linalg.norm(b), maxiter=400)
+    assert not bad.converged
+
+
+def test_comparison_solvers_on_the_reduced_dirac_system():
+    """BiCGStab and CGNR (with D_r^dag = gamma_5 A_e^{-1} D_r A_e gamma_5) solve
+    D_r y_e = b_r; the reconstructed solution satisfies D x = b."""
+    from oracle.krylov import bicgstab, cgnr
+    dims = (4, 4, 4, 4)
+    W = WilsonClover(I.make_gauge(dims, 0.5, 1, 0.5, 21), 1.0, 0.1)
+    b = I.gaussian_source(dims, 22).reshape(W.shape + (12,))
+    br = W.b_r(b)
+    A = lambda v: W.Dr(v * W.even) * W.even
+    Adag = lambda v: W.gamma5(W.Minv(W.Dr(W.M(W.gamma5(v * W.even)))) * W.even)
+    tol = 1e-11 * np.sqrt(norm2(br))
+    for y, info in (bicgstab(A, br, tol_abs=tol, maxiter=500), cgnr(A, Adag, br, tol_abs=tol, maxiter=2000)):
+        assert info.converged
+        x = W.reconstruct(y, b)
+        assert np.sqrt(norm2(b - W.D(x)) / norm2(b)) < 1e-10
