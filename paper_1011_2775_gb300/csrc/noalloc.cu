@@ -51,22 +51,26 @@ void run_op(mg::Ctx* c, int op, T* base) {
     case MG_OP_D:
       mg::dslash<T>(g, mg::EPI_CX_PAY, 0, oe, io, c->gauge<T>(), c->A<T>(0), ie, 1.0, 0xff, s);
       mg::dslash<T>(g, mg::EPI_CX_PAY, 1, oo, ie, c->gauge<T>(), c->A<T>(1), io, 1.0, 0xff, s);
+      c->dslash_launches += 2;
       break;
     case MG_OP_DP:
       mg::clover_apply<T>(g, t1, ie, c->Ainv<T>(0), s);
       mg::clover_apply<T>(g, t2, io, c->Ainv<T>(1), s);
       mg::dslash<T>(g, mg::EPI_XPAY, 0, oe, t2, c->gauge<T>(), nullptr, ie, 1.0, 0xff, s);
       mg::dslash<T>(g, mg::EPI_XPAY, 1, oo, t1, c->gauge<T>(), nullptr, io, 1.0, 0xff, s);
+      c->dslash_launches += 2;
       break;
     case MG_OP_DR:
       mg::clover_apply<T>(g, t1, ie, c->Ainv<T>(0), s);
       mg::dslash<T>(g, mg::EPI_CH, 1, t2, t1, c->gauge<T>(), c->Ainv<T>(1), nullptr, 0.0, 0xff, s);
       mg::dslash<T>(g, mg::EPI_XPAY, 0, oe, t2, c->gauge<T>(), nullptr, ie, -1.0, 0xff, s);
+      c->dslash_launches += 2;
       MG_CUDA(cudaMemsetAsync(oo, 0, sizeof(T) * h, s));  // the array keeps the last call's contents
       break;
     case MG_OP_BR:
       mg::clover_apply<T>(g, t1, io, c->Ainv<T>(1), s);
       mg::dslash<T>(g, mg::EPI_XPAY, 0, oe, t1, c->gauge<T>(), nullptr, ie, -1.0, 0xff, s);
+      c->dslash_launches += 1;
       MG_CUDA(cudaMemsetAsync(oo, 0, sizeof(T) * h, s));
       break;
     case MG_OP_M:
@@ -79,6 +83,7 @@ void run_op(mg::Ctx* c, int op, T* base) {
     case MG_OP_HOP:
       mg::dslash<T>(g, mg::EPI_H, 0, oe, io, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, s);
       mg::dslash<T>(g, mg::EPI_H, 1, oo, ie, c->gauge<T>(), nullptr, nullptr, 0.0, 0xff, s);
+      c->dslash_launches += 2;
       break;
     default:
       mg::raise(MG_ERR_ARG, "mg_apply_noalloc supports D, D_p, D_r, b_r, M, M^{-1} and H on the fine level");

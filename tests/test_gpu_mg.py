@@ -402,3 +402,40 @@ def test_four_level_solve():
     assert _true_residual(W, psi, eta) <= 1e-10
     assert si.coarse_iterations[1] > 0 and si.coarse_iterations[2] > 0 and si.coarse_iterations[3] > 0
     S.close()
+
+
+def test_setup_rayleigh_quotients_with_the_oracle_dp():
+    """Row a8 on the GPU, judged by the oracle ("Setup procedure": inverse
+    iteration watched through the Rayleigh quotient v^dag D_p^dag D_p v / v^dag v).
+    The GPU's null vectors, evaluated with the oracle's FP64 D_p: after one
+    relaxation pass (GCR(8) from the same Philox start vectors) their
+    quotients equal those of the oracle's own FP64 setup to FP32 accuracy;
+    they fall as the number of passes grows; after ten passes they stay
+    within a factor two of the oracle's ten-pass quotients (the FP32 and FP64
+    iterations drift apart) and far below a random vector's."""
+    from oracle.multigrid import setup_null_vectors
+    dims = (8, 8, 8, 8)
+    U = I.make_gauge(dims, 0.25, 5, 0.5, 4101)
+    m0 = -0.3
+    W = WilsonClover(U, 1.0, m0)
+    nv, seed = 8, 4103
+
+    def rq(v):
+        v = v.reshape(W.shape + (12,))
+        return norm2(W.Dp(v)) / norm2(v)
+
+    rq_random = np.mean([rq(gaussian_vector(seed, 0, k, W.shape, 12)) for k in range(nv)])
+    got = {}
+    for iters in (1, 3, 10):   # rq_tol 0: every vector takes exactly `iters` passes
+        S = _solver(dims, U, 1.0, m0)
+        S.set_params(levels=2, blocks=[(4, 4, 4, 4)], nv=[nv], seed=seed, setup_iters=iters, setup_rq_tol=0.0)
+        info = S.setup()
+        assert info.passes[0] == nv * iters
+        got[iters] = np.array([rq(v) for v in S.get_null_vectors(0)])
+        S.close()
+    ref1 = np.array([rq(v) for v in setup_null_vectors(W, nv, seed, 0, iters=1, inner_iters=8, rq_tol=0.0)])
+    assert np.abs(got[1] - ref1).max() <= 1e-4 * ref1.max()
+    assert got[10].mean() < got[3].mean() < got[1].mean() < rq_random
+    ref10 = np.array([rq(v) for v in setup_null_vectors(W, nv, seed, 0, iters=10, inner_iters=8, rq_tol=0.0)])
+    assert got[10].mean() < 2.0 * ref10.mean()
+    assert got[10].mean() < 0.05 * rq_random

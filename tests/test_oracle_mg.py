@@ -199,6 +199,36 @@ def test_complete_basis_two_grid_converges_in_one_iteration():
     assert info.converged and info.outer_iterations == 1
 
 
+@pytest.mark.parametrize("nu_post", [4, 1])
+def test_complete_basis_cycle_with_post_smoothing_is_exact(nu_post):
+    """P9 with post-smoothing: with a unitary P and an exact coarse solve the
+    coarse correction already is D_r^{-1} r_e, so the MR steps on the residual
+    r_e - D_r z_e must leave it unchanged (one cycle equals the dense inverse
+    of D_r) and MG-GCR still converges in one outer iteration.  A smoother run
+    on r_e instead of the updated residual, or before the prolongated
+    correction is added, fails both."""
+    dims = (4, 4, 4, 4)
+    W = WilsonClover(I.make_gauge(dims, 0.3, 0, 0.5, 71), 1.0, -0.1)
+    nv = 96
+    V = _random_vectors(W, nv, 72)
+    prm = MGParams(blocks=[(2, 2, 2, 2)], nv=[nv], tol_coarse=1e-14, maxit_coarse=400, restart_coarse=400,
+                   nu_post=nu_post)
+    mg = Multigrid(W, prm, null_vectors=[V])
+    r = _vec(dims, 74) * W.even
+    z = mg.cycle(0, r)
+    sel = np.flatnonzero((np.ones(W.shape + (12,)) * W.even).ravel())   # even-site components
+    cols = []
+    for j in sel:                                   # dense D_r on the even sites, column by column
+        e = np.zeros(r.size, dtype=np.complex128)
+        e[j] = 1.0
+        cols.append(W.Dr(e.reshape(r.shape)).ravel()[sel])
+    ze = np.linalg.solve(np.stack(cols, axis=1), r.ravel()[sel])
+    assert np.abs(z.ravel()[sel] - ze).max() < 1e-10 * np.abs(ze).max()
+    assert np.abs(z.ravel()[np.setdiff1d(np.arange(r.size), sel)]).max() == 0.0
+    x, info = mg.solve(_vec(dims, 73), tol=1e-10)
+    assert info.converged and info.outer_iterations == 1
+
+
 def test_mg_gcr_config1_matches_dense(two_grid_44):
     """P10: 2-level MG-GCR with setup on config 1 (4^4, 2^4 blocks, Nv = 8) reaches
     true residual <= 1e-10 and matches dense LU within cond * 1e-10."""
