@@ -144,6 +144,10 @@ typedef struct {
                                   /* lock-step, 1..16 (1: one after another)                      */
   int cuda_graphs;                /* 1: replay the 2-level cycle of a single-rhs solve as a        */
                                   /* captured CUDA graph (0: launch its kernels one by one)        */
+  int coarse_impl;                /* coarsest-level persistent GCR: 0 chosen by timing on the      */
+                                  /* first solve; 1 single-system kernel, 2 batched kernel,        */
+                                  /* 3 links streamed through shared memory (even-odd levels;     */
+                                  /* otherwise 1)                                                  */
 } mg_params;
 
 typedef struct {
@@ -182,7 +186,7 @@ MG_API const char* mg_last_error(void);
 /* Fill `p` with the defaults: 2 levels, 4^4 blocks, Nv = 24, 20 passes of 8
  * GCR iterations, RQ tolerance 0.05, nu_post = 4, coarse tolerance 0.1,
  * coarse restart 32 / cap 50, outer restart 16 / cap 500, FP32 storage,
- * Galerkin projection of D_p, seed 3, rhs_block 16, cuda_graphs 1. */
+ * Galerkin projection of D_p, seed 3, rhs_block 16, cuda_graphs 1, coarse_impl 0. */
 MG_API int mg_default_params(mg_params* p);
 
 /* Create a context for a lattice of `dims` on CUDA device `device`; kernels
@@ -407,6 +411,23 @@ MG_API int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int 
  * Errors as mg_benchmark_kernel; MG_KERNEL_COARSE_DR takes nrhs = 1 only. */
 MG_API int mg_benchmark_kernel_nrhs(void* ctx, int kernel, int prec, int nrhs, int warmup, int iters, double* avg_ms,
                                     double* bytes_per_launch);
+
+/* Times `iters` solves of the coarsest level's system (after `warmup`
+ * untimed ones) for a fixed Philox right-hand side: the persistent
+ * coarsest-level GCR with its even-odd reconstruction, as the multigrid cycle
+ * runs it (section "Implementation": unpreconditioned GCR on the coarsest
+ * lattice to the relative tolerance tol_coarse), with the implementation
+ * mg_params.coarse_impl selects or the autotuner picked.  CUDA events on the
+ * context's stream.  Outputs: *avg_ms per solve, *iterations_per_solve (GCR
+ * iterations), *bytes_per_solve = the coarse links one application of the
+ * reduced operator reads (half x 8 Nc^2 complex, folded links in FP32 and
+ * Y in the storage format) times the applications per solve (iterations +
+ * 1.5 for b_r and the closing true residual; odd-extent coarsest levels:
+ * the 9 Nc^2 complex FP32 links per site, iterations + 1).  Needs mg_setup.
+ * Errors: MG_ERR_ARG, MG_ERR_STATE, MG_ERR_CUDA (also when a bounded wait
+ * inside the persistent kernel ran out of time). */
+MG_API int mg_benchmark_coarse_solve(void* ctx, int warmup, int iters, double* avg_ms, double* bytes_per_solve,
+                                     double* iterations_per_solve);
 
 /* Lattice size of level `level` after setup (dims_out[4] = {Lx,Ly,Lz,Lt})
  * and its dof per site (12 on the fine level, 2*nv[level-1] on coarse ones). */

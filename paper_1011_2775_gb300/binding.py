@@ -40,6 +40,7 @@ EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "m
             "mg_set_clover", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
             "mg_get_coarse_links", "mg_save_setup", "mg_load_setup", "mg_update_mass", "mg_adapt_setup", "mg_solve", "mg_solve_batch",
             "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
+            "mg_benchmark_coarse_solve",
             "mg_level_info"]
 
 
@@ -61,7 +62,8 @@ class mg_params(ctypes.Structure):
                 ("coarse_op", ctypes.c_int),
                 ("seed", ctypes.c_uint64),
                 ("rhs_block", ctypes.c_int),
-                ("cuda_graphs", ctypes.c_int)]
+                ("cuda_graphs", ctypes.c_int),
+                ("coarse_impl", ctypes.c_int)]
 
 
 class mg_setup_info(ctypes.Structure):
@@ -129,6 +131,7 @@ def lib() -> ctypes.CDLL:
             "mg_benchmark_kernel": [vp, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_apply_noalloc": [vp, ip, vp, vp, ip],
             "mg_benchmark_kernel_nrhs": [vp, ip, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
+            "mg_benchmark_coarse_solve": [vp, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_level_info": [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)],
         }
         for name, args in sig.items():
@@ -337,6 +340,14 @@ def mg_benchmark_kernel_nrhs(ctx, kernel: int, prec: int = MG_FP32, nrhs: int = 
     _check(lib().mg_benchmark_kernel_nrhs(ctx, int(kernel), int(prec), int(nrhs), int(warmup), int(iters),
                                           ctypes.byref(ms), ctypes.byref(by)), "mg_benchmark_kernel_nrhs")
     return ms.value, by.value
+
+
+def mg_benchmark_coarse_solve(ctx, warmup: int = 3, iters: int = 20):
+    """Returns ``(avg_ms_per_solve, link_bytes_per_solve, gcr_iterations_per_solve)`` of the coarsest-level solve."""
+    ms, by, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib().mg_benchmark_coarse_solve(ctx, int(warmup), int(iters), ctypes.byref(ms), ctypes.byref(by),
+                                           ctypes.byref(it)), "mg_benchmark_coarse_solve")
+    return ms.value, by.value, it.value
 
 
 def mg_level_info(ctx, level: int):

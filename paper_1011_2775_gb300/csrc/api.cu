@@ -186,6 +186,7 @@ int mg_default_params(mg_params* p) {
   p->seed = 3;
   p->rhs_block = 16;
   p->cuda_graphs = 1;
+  p->coarse_impl = 0;
   return MG_OK;
 }
 
@@ -285,6 +286,7 @@ int mg_set_params(void* ctx, const mg_params* p) {
     if (p->coarse_op != MG_COARSE_DP && p->coarse_op != MG_COARSE_D) mg::raise(MG_ERR_ARG, "bad coarse_op");
     if (p->rhs_block < 1 || p->rhs_block > 16) mg::raise(MG_ERR_ARG, "rhs_block must be in [1, 16]");
     if (p->cuda_graphs != 0 && p->cuda_graphs != 1) mg::raise(MG_ERR_ARG, "cuda_graphs must be 0 or 1");
+    if (p->coarse_impl < 0 || p->coarse_impl > 3) mg::raise(MG_ERR_ARG, "coarse_impl must be in [0, 3]");
     int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
     int ndof = 12;
     for (int l = 0; l + 1 < p->levels; l++) {
@@ -389,7 +391,7 @@ int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where) {
 
 // ---- setup reuse (the paper saves null vectors and coarse operators for later use)
 namespace {
-constexpr char kSetupMagic[8] = {'M', 'G', 'C', 'L', 'S', 'E', 'T', '1'};
+constexpr char kSetupMagic[8] = {'M', 'G', 'C', 'L', 'S', 'E', 'T', '2'};
 
 struct SetupHeader {
   char magic[8];
@@ -723,6 +725,17 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
       c->sync();
     }
     stage_out_finish(c, so, out, sizeof(double) * 2 * nout * nrhs, where);
+    return MG_OK;
+  });
+}
+
+int mg_benchmark_coarse_solve(void* ctx, int warmup, int iters, double* avg_ms, double* bytes_per_solve,
+                              double* iterations_per_solve) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!avg_ms || !bytes_per_solve || !iterations_per_solve || iters < 1 || warmup < 0)
+      mg::raise(MG_ERR_ARG, "bad benchmark arguments");
+    mg::mg_benchmark_coarse_solve(c, warmup, iters, avg_ms, bytes_per_solve, iterations_per_solve);
     return MG_OK;
   });
 }

@@ -119,6 +119,9 @@ struct CoarseGCRBuffers {
   DBuf r, y, br, tA, tB, W, Z, partials, scal;
   // batched solves (coarse_batch.cu; grown on demand)
   DBuf bx_r, bx_y, bx_br, bx_tB, bx_W, bx_Z, bx_part, bx_scal;
+  // streamed solve (coarse_stream.cu; grown on demand): partial sums, the
+  // Gram-Schmidt coefficients, grid-barrier counter and abort flag
+  DBuf st_part, st_beta, st_sync;
   void init(const LevelGeom& G, int nc, int m);
 };
 // x = D_hat^{-1} b to ||b - D_hat x|| <= tol_rel ||b|| (or maxit iterations) by
@@ -128,6 +131,16 @@ struct CoarseGCRBuffers {
 void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuffers& B, int m, int maxit,
                       double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s,
                       int grid = 0);
+// The same solve with the links streamed through shared memory by bulk
+// asynchronous copies and three grid barriers per iteration
+// (coarse_stream.cu): even-odd levels only.  grid: blocks of the cooperative
+// launch, one of coarse_gcr_stream_grids().  Raises FLAG_TIMEOUT if a wait
+// runs out of time.
+bool coarse_gcr_stream_ok(const LevelGeom& G, const CoarseOp& C);
+std::vector<int> coarse_gcr_stream_grids(const LevelGeom& G, const CoarseOp& C);
+void coarse_gcr_stream_solve(const LevelGeom& G, const CoarseOp& C, CoarseGCRBuffers& B, int m, int maxit,
+                             double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s,
+                             int grid);
 // smaller grids worth timing against B.grid: the fewest blocks that keep the
 // largest number of stencil sites per block, and one more site per block
 // (fewer blocks at every grid barrier)

@@ -79,7 +79,7 @@ struct Workspace {
   ~Workspace();
 };
 
-enum Flag { FLAG_SINGULAR = 0, FLAG_GS_BREAKDOWN = 1, FLAG_NAN = 2, FLAG_COUNT = 16 };
+enum Flag { FLAG_SINGULAR = 0, FLAG_GS_BREAKDOWN = 1, FLAG_NAN = 2, FLAG_TIMEOUT = 3, FLAG_COUNT = 16 };
 
 // --------------------------------------------------------------------------- fine level
 // dslash epilogues: out = f(H in), H the hopping term including its -1/2
@@ -410,5 +410,7 @@ void mg_reset_counters(Ctx* c);
 // times `iters` applications of the level-1 coarse D_hat_r (see mg_benchmark_kernel)
 void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes);
 void mg_read_counters(Ctx* c, long long* coarse_iters);
+// times `iters` coarsest-level solves (see mg_benchmark_coarse_solve)
+void mg_benchmark_coarse_solve(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes, double* its);
 
 }  // namespace mg

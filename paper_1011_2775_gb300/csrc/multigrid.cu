@@ -257,11 +257,19 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
     // batched kernel with one system (row-blocked GEMV: fewer registers, more
     // co-resident CTAs).  The autotuner times them on the first solve of this
     // lattice (the tuning runs do not count towards the iteration statistics).
+    // The streamed kernel (links through shared memory by bulk copies, even-odd
+    // levels) is a third implementation, on the full grid or on the largest
+    // grid that splits its work evenly; candidates 100 + k.
     const int restart = p.restart_coarse > 0 ? p.restart_coarse : 32;
     long long* d_it = H.d_iters.as<long long>() + l;
     const std::vector<int> smaller = coarse_gcr_smaller_grids(G, W.cg);
+    const std::vector<int> streamed =
+        coarse_gcr_stream_ok(G, H.cop[l]) ? coarse_gcr_stream_grids(G, H.cop[l]) : std::vector<int>();
     auto run = [&](int which, long long* it) {
-      if (which == 1)
+      if (which >= 100)
+        coarse_gcr_stream_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, b, x, it,
+                                c->ws.flags.as<int>(), s, streamed[which - 100]);
+      else if (which == 1)
         coarse_gcr_solve_batch(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, 1, b, x, it,
                                c->ws.flags.as<int>(), s);
       else
@@ -270,11 +278,23 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
     };
     if (W.coarse_impl < 0) {
       if (!W.tune_iters.get()) W.tune_iters.alloc(sizeof(long long));
-      TuneKey key{"coarse_gcr", {G.L[0], G.L[1], G.L[2], G.L[3]}, H.cop[l].nc, H.cop[l].store};
+      TuneKey key{"coarse_gcr2", {G.L[0], G.L[1], G.L[2], G.L[3]}, H.cop[l].nc, H.cop[l].store};
       std::vector<int> cands = {0, 1};
       for (size_t k = 0; k < smaller.size(); k++) cands.push_back(2 + (int)k);
-      W.coarse_impl = tuned_block(key, cands, [&](int which) { run(which, W.tune_iters.as<long long>()); }, s);
-      if (W.coarse_impl >= 2 + (int)smaller.size()) W.coarse_impl = 0;  // a cached choice from other grids
+      for (size_t k = 0; k < streamed.size(); k++) cands.push_back(100 + (int)k);
+      if (c->params.coarse_impl > 0) {
+        // a forced implementation (mg_params.coarse_impl): 1 original, 2 batched, 3 streamed
+        cands = c->params.coarse_impl == 1 ? std::vector<int>{0}
+                : c->params.coarse_impl == 2 ? std::vector<int>{1}
+                : streamed.empty()           ? std::vector<int>{0}
+                                             : std::vector<int>{100};
+        W.coarse_impl = cands[0];
+      } else {
+        W.coarse_impl = tuned_block(key, cands, [&](int which) { run(which, W.tune_iters.as<long long>()); }, s);
+      }
+      const bool valid = (W.coarse_impl >= 0 && W.coarse_impl < 2 + (int)smaller.size()) ||
+                         (W.coarse_impl >= 100 && W.coarse_impl < 100 + (int)streamed.size());
+      if (!valid) W.coarse_impl = 0;  // a cached choice from other grids
     }
     run(W.coarse_impl, d_it);
     return;
@@ -752,7 +772,9 @@ bool mg_precondition_graph(Ctx* c, float* z_e, const double* r_e, float* r32) {
 }
 
 void mg_solve_params_changed(Ctx* c) {
-  if (!c->mg || !c->mg->graph.exec) return;
+  if (!c->mg) return;
+  for (LevelWork& W : c->mg->work) W.coarse_impl = -1;   // choose (or force) the coarsest solver again
+  if (!c->mg->graph.exec) return;
   MG_CUDA(cudaStreamSynchronize(c->stream));   // no replay in flight
   c->mg->graph.drop();
 }
@@ -787,6 +809,43 @@ void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* 
   *bytes = (double)G.half * (18.0 * nc * nc + 7.0 * nc) * sizeof(float2);
 }
 
+void mg_benchmark_coarse_solve(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes, double* its) {
+  if (!c->mg || c->mg->L < 2) raise(MG_ERR_STATE, "multigrid not set up");
+  Hierarchy& H = *c->mg;
+  const int l = H.L - 1;
+  const LevelGeom& G = H.geo[l];
+  const CoarseOp& C = H.cop[l];
+  const size_t n = full_n(H, l);
+  DBuf bb(sizeof(float) * 2 * n), xb(sizeof(float) * 2 * n);
+  philox_coarse_vector(G, 777, l, 0, bb.as<float>(), c->stream);
+  long long* d_it = H.d_iters.as<long long>() + l;
+  long long before = 0, after = 0;
+  for (int w = 0; w < warmup; w++) coarse_solve(c, H, l, xb.as<float>(), bb.as<float>());
+  MG_CUDA(cudaMemcpyAsync(&before, d_it, sizeof(before), cudaMemcpyDeviceToHost, c->stream));
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  MG_CUDA(cudaEventRecord(e0, c->stream));
+  for (int it = 0; it < iters; it++) coarse_solve(c, H, l, xb.as<float>(), bb.as<float>());
+  MG_CUDA(cudaEventRecord(e1, c->stream));
+  MG_CUDA(cudaEventSynchronize(e1));
+  MG_CUDA(cudaMemcpyAsync(&after, d_it, sizeof(after), cudaMemcpyDeviceToHost, c->stream));
+  c->sync();
+  float t = 0;
+  MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (c->read_flag(FLAG_TIMEOUT, true)) raise(MG_ERR_CUDA, "a wait in the persistent coarse solve ran out of time");
+  *avg_ms = t / iters;
+  *its = (double)(after - before) / iters;
+  // links of one application of the reduced operator: the folded odd-site links
+  // (FP32) and the even-site Y in the storage format, each half x 8 Nc^2 complex
+  const double esz = C.store == STORE_F32 ? 8.0 : 4.0;
+  const double nc = C.nc;
+  const double per_app = G.eo ? (double)G.half * 8.0 * nc * nc * (8.0 + esz) : (double)G.nsites * 9.0 * nc * nc * 8.0;
+  *bytes = per_app * (*its + (G.eo ? 1.5 : 1.0));
+}
+
 void mg_reset_counters(Ctx* c) {
   if (!c->mg) return;
   c->mg->iters.assign(c->mg->L, 0);
@@ -801,6 +860,7 @@ void mg_read_counters(Ctx* c, long long* coarse_iters) {
   c->sync();
   for (int l = 0; l < c->mg->L && l < MG_MAX_LEVELS; l++) coarse_iters[l] = c->mg->iters[l] + dev[l];
   if (c->read_flag(FLAG_NAN, true)) raise(MG_ERR_NAN, "non-finite residual in the coarse solve");
+  if (c->read_flag(FLAG_TIMEOUT, true)) raise(MG_ERR_CUDA, "a wait in the persistent coarse solve ran out of time");
 }
 
 void mg_level_dims(Ctx* c, int level, int dims[4], int* ndof) {

@@ -284,3 +284,64 @@ def test_bench_lattice_galerkin_operator(bench_lattice):
     w = S.apply(B.MG_OP_HOP, t, level=1) * ev                    # Y_eo X_o^{-1} (...)
     got_r = S.apply(B.MG_OP_DR, np.ascontiguousarray(ye), level=1)
     assert rel(got_r * ev, ye - w) <= TOL32
+
+
+@pytest.mark.parametrize("impl", [1, 2, 3], ids=["single", "batched", "streamed"])
+def test_nv24_cycle_with_each_coarsest_solver(nv24, impl):
+    """The three persistent coarsest-level solvers (mg_params.coarse_impl: the
+    single-system kernel, the batched kernel with one system, the kernel that
+    streams the links through shared memory) each reproduce the oracle's
+    cycle at Nc = 48."""
+    from paper_1011_2775_gb300 import binding as B
+    S, W, mg = nv24["S"], nv24["W"], nv24["ref"]
+    S.set_params(coarse_impl=impl)
+    try:
+        r = I.gaussian_source(nv24["dims"], 8104)
+        got = S.apply(B.MG_OP_CYCLE, r, level=0)
+        ref = mg.cycle(0, r.reshape(W.shape + (12,)) * W.even).reshape(r.shape)
+        assert rel(got, ref) <= 1e-4
+    finally:
+        S.set_params(coarse_impl=0)
+
+
+@pytest.mark.parametrize("impl", [1, 3], ids=["single", "streamed"])
+def test_nv24_32_cycle_with_each_coarsest_solver(nv24_32, impl):
+    """Level-1 cycle of the 3-level hierarchy (coarsest Nc = 64) with each
+    persistent solver."""
+    from paper_1011_2775_gb300 import binding as B
+    S, mg = nv24_32["S"], nv24_32["ref"]
+    S.set_params(coarse_impl=impl)
+    try:
+        lev = mg.levels[1]
+        r = _rand(lev.shape + (lev.ndof,), 45)
+        got = S.apply(B.MG_OP_CYCLE, np.ascontiguousarray(r), level=1)
+        ref = mg.cycle(1, r * lev.even)
+        assert rel(got.reshape(ref.shape), ref) <= 1e-4
+    finally:
+        S.set_params(coarse_impl=0)
+
+
+@pytest.mark.parametrize("store", [0, 1, 2], ids=["fp32", "fp16", "bf16"])
+def test_streamed_coarsest_solver_solves_and_is_deterministic(store):
+    """MG-GCR with the streamed coarsest solver reaches 1e-10 with the oracle's
+    D, iterates as often as with the single-system kernel (the same GCR,
+    up to rounding in the Gram-Schmidt norms), and two identical solves agree
+    bit for bit (deterministic reductions)."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (8, 8, 8, 16)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 8301)
+    W = WilsonClover(U, 1.0, -0.6)
+    eta = I.gaussian_source(dims, 8302)
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(levels=2, blocks=[(4, 4, 4, 4)], nv=[16], seed=8303, maxit_fine=3000, storage=store, coarse_impl=3)
+    S.setup()
+    psi, info = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    psi2, info2 = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    r = eta.reshape(W.shape + (12,)) - W.D(psi.reshape(W.shape + (12,)))
+    assert np.sqrt(norm2(r) / norm2(eta)) <= 1e-10
+    assert info2.outer_iterations == info.outer_iterations
+    assert np.array_equal(psi, psi2)
+    S.set_params(coarse_impl=1)
+    _, ref = S.solve(eta, 1e-10, B.MG_MODE_MG)
+    assert abs(info.outer_iterations - ref.outer_iterations) <= 2
+    S.close()
