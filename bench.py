@@ -33,28 +33,45 @@ DIMS = (16, 16, 16, 32)
 EPS, APE, ALPHA, CSW = 0.25, 5, 0.5, 1.0
 MASSES = (-0.2, -0.3, -0.35)
 GAUGE_SEED, SOURCE_SEED, NULLVEC_SEED = 2001, 2002, 2003
-# coarse GCR tolerance and restart swept on GB300 at the three masses (0.25-0.3
-# beat the paper's 0.1 there: each coarsest iteration is a few barrier-bound
-# microseconds, so fewer of them per outer iteration pay); the paper's setting
-# is timed beside it as extra.paper_coarse_params
-MG = dict(levels=2, blocks=[(4, 4, 4, 4)], nv=[24], tol_coarse=0.3, restart_coarse=64)
-PAPER_COARSE = dict(tol_coarse=0.1, restart_coarse=32)
+# the paper's coarse tolerance 0.1 (a sweep of 0.05 ... 0.3 on GB300 with the
+# streamed coarsest solver is flat within 2% between 0.1 and 0.3); 0.3 is timed
+# beside it as extra.coarse_tolerance
+MG = dict(levels=2, blocks=[(4, 4, 4, 4)], nv=[24], tol_coarse=0.1, restart_coarse=64)
+ALT_COARSE_TOL = 0.3
 TOL = 1e-10
 HBM_DIMS = (32, 32, 32, 64)          # 1.1 GB per FP32 fused-dslash launch: far beyond the 129 MB L2
 L2_FLUSH_BYTES = 512 << 20
-CPU_SAMPLE_DR = 5                    # oracle D_r applications in one CPU sample
+# The CPU oracle sample: the oracle's complete MG-GCR on an 8^4 lattice of the
+# same construction and parameters (4^4 blocks, Nv = 24), its setup cut to 4
+# inverse-iteration passes per vector to bound the sample; one process per host
+# core (independent sources), so that all cores work.  The per-outer-iteration
+# cost (fine and coarse work) is projected to the 16^3x32 workload by volume.
+CPU_DIMS = (8, 8, 8, 8)
+CPU_SETUP_ITERS = 4
+CPU_STEP_ITERS = 2                   # outer iterations per step of the reference arm
+CPU_MAX_PROCS = 16
 BATCH_RHS = 12                       # right-hand sides of the batched solve
 MRHS = (4, 12)                       # right-hand sides of the multi-RHS D_r measurements
 PROFILE_MRHS = 4                     # --profile dslash_mrhs: right-hand sides per launch
 PROFILE_MRHS_DIMS = (32, 32, 32, 32) # ... on a lattice that keeps an ncu capture to a few GB
-# fine D_r applications of one MG-GCR solve of the 16^3x32 workload at m0=-0.35
-# (the GPU arm's solve.fine_dr_applications on GB300: 50 outer iterations);
-# projects the reference arm's sample to one solve
-REFERENCE_DR_PER_SOLVE = 306
+# outer iterations of the GPU arm's MG-GCR solve of the 16^3x32 workload at
+# m0 = -0.35 on GB300 (coarse tolerance 0.1): projects the reference arm's
+# per-iteration sample to one solve
+REFERENCE_OUTER_PER_SOLVE = 42
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the FP32 fused
 # dslash on 32^3x64, from the ncu capture in profiles/dslash_fp32_32x32x32x64.md
 # (set to None whenever that kernel changes)
 DSLASH_TRAFFIC_BYTES = 1.125e9
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the streamed
+# coarsest-level solve on this workload (None whenever that kernel changes)
+COARSE_TRAFFIC_BYTES = 79.52e6        # profiles/coarse_gcr_stream_4x4x4x8.md: 76.88 MB read + 2.64 MB written
+                                      # per launch of COARSE_PROFILE_ITERS iterations (the links' first touch
+                                      # after the fine-level work; L2 hits afterwards)
+DSLASH_FLOPS_PER_SITE = 1824        # fused hop + clover inverse, per output site
+COARSE_PROFILE_ITERS = 34            # --profile coarse: GCR iterations per launch (the step's average)
+
+
+SECTIONS = {}                        # wall seconds of the bench's sections (reported in the JSON line)
 
 
 def workload_name(m0):
@@ -146,31 +163,73 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------- CPU oracle sample
-def cpu_sample(m0: float, n_dr: int) -> dict:
-    """Times n_dr applications of the oracle's FP64 D_r on this workload, in a
-    single-threaded subprocess (run as ``python bench.py --cpu-sample``)."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(m0), str(n_dr)],
-                         capture_output=True, text=True, env=env, timeout=900)
-    for line in out.stdout.splitlines()[::-1]:
-        if line.startswith("{"):
-            return json.loads(line)
-    raise RuntimeError("cpu sample failed: " + out.stderr[-2000:])
-
-
-def cpu_sample_main(m0: float, n_dr: int):
+def oracle_worker(job):
+    """One host process: the oracle's multigrid on CPU_DIMS (setup with
+    CPU_SETUP_ITERS passes), then either one complete solve ("solve") or
+    `steps` samples of CPU_STEP_ITERS outer iterations ("steps").  Runs in a
+    spawned process with one thread."""
+    mode, seed, steps, dims = job
     from oracle.dirac import WilsonClover
+    from oracle.multigrid import MGParams, Multigrid
     from paper_1011_2775_gb300 import inputs as I
-    U = I.make_gauge(DIMS, EPS, APE, ALPHA, GAUGE_SEED)
-    W = WilsonClover(U, CSW, m0)
-    y = I.gaussian_source(DIMS, SOURCE_SEED).reshape(W.shape + (12,)) * W.even
-    W.Dr(y)  # warm
+    U = I.make_gauge(dims, EPS, APE, ALPHA, GAUGE_SEED)
+    W = WilsonClover(U, CSW, MASSES[-1])
+    prm = MGParams(blocks=[(4, 4, 4, 4)], nv=[24], tol_coarse=MG["tol_coarse"], restart_coarse=MG["restart_coarse"],
+                   setup_iters=CPU_SETUP_ITERS, seed=NULLVEC_SEED)
     t0 = time.perf_counter()
-    for _ in range(n_dr):
-        y = W.Dr(y)
-        y = y / max(1.0, float(abs(y).max()))
-    dt = time.perf_counter() - t0
-    print(json.dumps({"seconds": dt, "n_dr": n_dr, "ms_per_dr": 1e3 * dt / n_dr}))
+    mg = Multigrid(W, prm)
+    setup_s = time.perf_counter() - t0
+    eta = I.gaussian_source(dims, SOURCE_SEED + seed).reshape(W.shape + (12,))
+    if mode == "solve":
+        t0 = time.perf_counter()
+        _, info = mg.solve(eta, TOL)
+        dt = time.perf_counter() - t0
+        return {"setup_s": setup_s, "solve_s": dt, "outer_iterations": info.outer_iterations,
+                "true_residual": info.true_residual}
+    mg.params.maxit_fine = CPU_STEP_ITERS
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        mg.solve(eta, TOL, max_attempts=1)
+        times.append(time.perf_counter() - t0)
+    return {"setup_s": setup_s, "step_s": times}
+
+
+def oracle_pool(jobs):
+    """Runs the jobs in spawned single-thread processes, one per host core (at most CPU_MAX_PROCS)."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        return pool.map(oracle_worker, jobs)
+
+
+def host_cores(limit: int = 0) -> int:
+    n = max(1, min(CPU_MAX_PROCS, os.cpu_count() or 1))
+    return min(n, limit) if limit > 0 else n
+
+
+def cpu_baseline(gpu_outer: int, gpu_small_ms: float) -> dict:
+    """The oracle's complete MG-GCR solve of CPU_DIMS in every host process at
+    once; the per-outer-iteration wall time (fine and coarse work), divided by
+    the processes working concurrently, projected to one solve of the
+    16^3x32 workload by volume and the GPU's outer-iteration count."""
+    n = host_cores()
+    res = oracle_pool([("solve", q, 0, CPU_DIMS) for q in range(n)])
+    per_it = statistics.median(r["solve_s"] / r["outer_iterations"] for r in res)
+    vol = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) / (CPU_DIMS[0] * CPU_DIMS[1] * CPU_DIMS[2] * CPU_DIMS[3])
+    value = 1e3 * per_it * vol * gpu_outer / n
+    return {"value": value, "unit": "ms", "cores": n, "kind": "oracle",
+            "sample": (f"{n} concurrent single-thread processes, each the oracle's complete MG-GCR solve (setup "
+                       f"{CPU_SETUP_ITERS} passes per vector, then to 1e-10) of an 8^4 lattice of the same "
+                       f"construction and parameters (4^4 blocks, Nv=24); projection: median wall time per outer "
+                       f"iteration x {vol:.0f} (volume) x {gpu_outer} (outer iterations of the GPU solve) / {n} "
+                       f"(processes)"),
+            "measured_8x8x8x8": {"solve_ms_median": 1e3 * statistics.median(r["solve_s"] for r in res),
+                                 "setup_ms_median": 1e3 * statistics.median(r["setup_s"] for r in res),
+                                 "outer_iterations": [r["outer_iterations"] for r in res],
+                                 "true_residual_max": max(r["true_residual"] for r in res),
+                                 "gpu_solve_ms_same_config": gpu_small_ms}}
 
 
 def profile_main(args):
@@ -201,6 +260,24 @@ def profile_main(args):
         torch.cuda.profiler.stop()
         print(json.dumps({"profile": "solve", "steps": args.steps, "kernel_launches": info.kernel_launches,
                           "outer_iterations": info.outer_iterations, "true_residual": info.true_residual}))
+        S.close()
+    elif args.profile == "coarse":
+        # the persistent coarsest-level solve of the workload, `steps` launches of
+        # COARSE_PROFILE_ITERS GCR iterations each
+        S = Solver(DIMS)
+        S.load_gauge(U)
+        S.set_clover(CSW, args.mass)
+        S.set_params(seed=NULLVEC_SEED, maxit_fine=2000, **MG)
+        S.setup()
+        S.set_params(tol_coarse=1e-12, maxit_coarse=COARSE_PROFILE_ITERS)
+        B.mg_benchmark_coarse_solve(S.ctx, max(1, args.warmup), 1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        ms, by, its = B.mg_benchmark_coarse_solve(S.ctx, 0, args.steps)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile": "coarse", "launches": args.steps, "gcr_iterations": its, "ms_per_solve": ms,
+                          "link_bytes_per_solve": by}))
         S.close()
     elif args.profile == "block":
         etas = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED + 10, nrhs=BATCH_RHS)).cuda()
@@ -309,9 +386,22 @@ def run_gpu(args, dist: Dist) -> dict:
     e2e_ms = dist.max(statistics.median(e2e_times))
     nbytes = eta.nbytes
 
+    # the step's dominant kernel, the persistent coarsest-level solve, timed alone
+    # with CUDA events on the solve's stream at the step's average number of GCR
+    # iterations per coarse solve (one coarse solve per outer iteration)
+    per_solve = last.coarse_iterations[1] / max(1, last.outer_iterations)
+    keep = (S.params.tol_coarse, S.params.maxit_coarse)
+    S.set_params(tol_coarse=1e-12, maxit_coarse=max(1, round(per_solve)))
+    c_ms, c_bytes, c_its = B.mg_benchmark_coarse_solve(S.ctx, 3, 20)
+    S.set_params(tol_coarse=keep[0], maxit_coarse=keep[1])
+    coarse = {"ms": c_ms, "bytes": c_bytes, "gcr_iterations": c_its, "avg_iterations_in_step": per_solve,
+              "share_of_step": c_ms * last.outer_iterations / ms}
+
     extra = {}
     if not args.no_extra:
+        t_x = time.perf_counter()
         extra = run_extras(args, S, U, eta, flush, stream, dev)
+        SECTIONS["extras"] = time.perf_counter() - t_x
 
     # plain FP64 even-odd GCR on the same system (bounded)
     eo = None
@@ -349,8 +439,36 @@ def run_gpu(args, dist: Dist) -> dict:
             ms_k, by = B.mg_benchmark_kernel_nrhs(H.ctx, B.MG_KERNEL_DR, B.MG_FP32, nrhs, warmup=3, iters=10)
             kern[f"dr_fp32_nrhs{nrhs}"] = {"ms": ms_k, "bytes": by, "gbs": by / ms_k / 1e6, "ms_per_rhs": ms_k / nrhs}
     H.close()
+    # CUDA-core FMA peaks of this GPU (denominators of the ALU-bound kernels)
+    peaks = {"fp64_fma_tflops": B.mg_benchmark_fma(dev, B.MG_FP64), "fp32_fma_tflops": B.mg_benchmark_fma(dev, B.MG_FP32)}
+    kern["dslash_clover_fp64"]["tflops"] = kern["dslash_clover_fp64"]["bytes"] / 2112.0 * DSLASH_FLOPS_PER_SITE / \
+        kern["dslash_clover_fp64"]["ms"] / 1e9
+    kern["dslash_clover_fp64"]["frac_of_fp64_fma_peak"] = kern["dslash_clover_fp64"]["tflops"] / peaks["fp64_fma_tflops"]
+
+    # the GPU's solve of the CPU sample's configuration (8^4, setup with the same passes)
+    small = None
+    if not args.no_cpu:
+        Us = I.make_gauge(CPU_DIMS, EPS, APE, ALPHA, GAUGE_SEED)
+        T = Solver(CPU_DIMS, device=dev, stream=stream.cuda_stream)
+        T.load_gauge(Us)
+        T.set_clover(CSW, m0)
+        T.set_params(seed=NULLVEC_SEED, maxit_fine=2000, setup_iters=CPU_SETUP_ITERS, **MG)
+        T.setup()
+        es = torch.from_numpy(I.gaussian_source(CPU_DIMS, SOURCE_SEED)).to(f"cuda:{dev}")
+        ps = torch.zeros_like(es)
+        T.solve(es, TOL, B.MG_MODE_MG, out=ps)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        T.solve(es, TOL, B.MG_MODE_MG, out=ps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        small = e0.elapsed_time(e1)
+        T.close()
     return dict(ms=ms, times=times, info=last, setup_ms=setup_ms, sinfo=sinfo, e2e_ms=e2e_ms, nbytes=nbytes,
-                eo=eo, kern=kern, clocks=clk, launches=launches // max(1, args.steps), extra=extra)
+                eo=eo, kern=kern, clocks=clk, launches=launches // max(1, args.steps), extra=extra, coarse=coarse,
+                peaks=peaks, small_ms=small)
 
 
 def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
@@ -377,19 +495,19 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), res
 
-    # ---- the same solve with the paper's coarse tolerance 0.1 and restart 32
-    Q = Solver(DIMS, device=dev, stream=stream.cuda_stream)
-    Q.load_gauge(U)
-    Q.set_clover(CSW, args.mass)
-    Q.set_params(seed=NULLVEC_SEED, maxit_fine=2000, **dict(MG, **PAPER_COARSE))
-    Q.setup()
+    # ---- the same solve with coarse tolerance 0.3 (setup kept) and with the
+    #      original single-system coarsest kernel
     e_d = torch.from_numpy(eta).to(f"cuda:{dev}")
     p_d = torch.zeros_like(e_d)
-    Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
-    t_p, (_, qi) = timed(lambda: Q.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
-    out["paper_coarse_params"] = dict(PAPER_COARSE, ms=t_p, outer_iterations=qi.outer_iterations,
-                                      coarse_iterations=qi.coarse_iterations[1], true_residual=qi.true_residual)
-    Q.close()
+    alt = {}
+    for name, kw in (("tol_0.3", dict(tol_coarse=ALT_COARSE_TOL)), ("single_system_kernel", dict(coarse_impl=1))):
+        S.set_params(**kw)
+        S.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
+        t_p, (_, qi) = timed(lambda: S.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
+        alt[name] = {"ms": t_p, "outer_iterations": qi.outer_iterations, "coarse_iterations": qi.coarse_iterations[1],
+                     "true_residual": qi.true_residual}
+        S.set_params(tol_coarse=MG["tol_coarse"], coarse_impl=0)
+    out["coarse_tolerance"] = alt
     del e_d, p_d
 
     # ---- batched right-hand sides (12 Gaussian sources, the point-source count of one propagator)
@@ -532,7 +650,9 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     out["fp16_storage"] = {"ms": statistics.median(ts), "outer_iterations": qi.outer_iterations,
                            "coarse_iterations": qi.coarse_iterations[1], "true_residual": qi.true_residual}
     Q.close()
+    t_k = time.perf_counter()
     out["krylov"] = run_krylov(dev, flush, stream)
+    SECTIONS["krylov"] = time.perf_counter() - t_k
     return out
 
 
@@ -640,8 +760,9 @@ CONFIG3_MG = dict(levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 32])
 
 
 def run_config3(dev: int) -> dict:
-    """The 3-level solve on 24^3x64 with BF16 and with FP32 storage, and the FP32
-    dslash on this lattice (467 MB per launch, beyond L2)."""
+    """The 24^3x64 configuration: the 3-level solve with BF16 storage of P and
+    the coarse links, the 2-level solve with BF16 and with FP32 storage, and
+    the FP32 dslash on this lattice (467 MB per launch, beyond L2)."""
     import torch
     from paper_1011_2775_gb300 import binding as B
     from paper_1011_2775_gb300 import inputs as I
@@ -652,20 +773,18 @@ def run_config3(dev: int) -> dict:
     eta = torch.from_numpy(I.gaussian_source(CONFIG3_DIMS, 3002)).to(f"cuda:{dev}")
     psi = torch.zeros_like(eta)
     out = {"lattice": "24^3x64", "m0": -0.35, "mg": "3-level: 4^4 (Nv=24) then 2^4 (Nv=32), coarsest 3^3x8"}
-    for name, store, mg in (("bf16", B.MG_STORE_BF16, CONFIG3_MG), ("fp32", B.MG_STORE_FP32, CONFIG3_MG),
-                            ("fp32_adaptive", B.MG_STORE_FP32, CONFIG3_MG), ("two_level_fp32", B.MG_STORE_FP32, MG)):
+    for name, store, mg in (("three_level_bf16", B.MG_STORE_BF16, CONFIG3_MG),
+                            ("two_level_bf16", B.MG_STORE_BF16, MG), ("two_level_fp32", B.MG_STORE_FP32, MG)):
         S = Solver(CONFIG3_DIMS, device=dev, stream=stream.cuda_stream)
         S.load_gauge(U)
         S.set_clover(CSW, -0.35)
         S.set_params(seed=3003, maxit_fine=2000, storage=store, **mg)
         t0 = time.perf_counter()
         S.setup()
-        if name.endswith("adaptive"):
-            S.adapt_setup(passes=1, relax=2, transfers=1)
         setup_ms = 1e3 * (time.perf_counter() - t0)
         S.solve(eta, TOL, B.MG_MODE_MG, out=psi, allow_not_converged=True)
         ts = []
-        for _ in range(2):
+        for _ in range(1):
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -677,14 +796,14 @@ def run_config3(dev: int) -> dict:
         out[name] = {"solve_ms": min(ts), "setup_ms": setup_ms, "outer_iterations": info.outer_iterations,
                      "level1_iterations": info.coarse_iterations[1], "level2_iterations": info.coarse_iterations[2],
                      "true_residual": info.true_residual, "levels": mg["levels"]}
-        if name == "fp32":
+        if name == "two_level_fp32":
             ms_k, by = B.mg_benchmark_kernel(S.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, warmup=10, iters=50)
             out["dslash_clover_fp32"] = {"ms": ms_k, "bytes": by, "gbs": by / ms_k / 1e6}
         S.close()
     return out
 
 
-def run_multi(dev: int) -> dict:
+def run_multi(dev: int, sequential: bool = False) -> dict:
     """All 28 right-hand sides through mg_solve_batch (lock-step, shared coarsest
     launches) against each lattice's own block solve and against 28 solves one
     after another; every time is CUDA events on the one stream all contexts use."""
@@ -731,14 +850,16 @@ def run_multi(dev: int) -> dict:
         t, _ = timed(lambda: S.solve(e, TOL, B.MG_MODE_MG, out=o))
         t_lat.append(t)
     t_seq = []
-    for S, e, o in zip(solvers, etas, outs):
-        S.set_params(rhs_block=1)
-        t, (_, si) = timed(lambda: S.solve(e, TOL, B.MG_MODE_MG, out=o))
-        t_seq.append(t)
-        S.set_params(rhs_block=16)
+    if sequential:
+        for S, e, o in zip(solvers, etas, outs):
+            S.set_params(rhs_block=1)
+            t, (_, si) = timed(lambda: S.solve(e, TOL, B.MG_MODE_MG, out=o))
+            t_seq.append(t)
+            S.set_params(rhs_block=16)
     out = {"lattices": [f"{d[0]}^3x{d[3]} x{n} {kind}" for d, kind, n in MULTI], "m0": MULTI_M0,
-           "all_in_one_ms": t_all, "per_lattice_block_ms": t_lat, "one_at_a_time_ms": t_seq,
-           "speedup_vs_one_at_a_time": sum(t_seq) / t_all, "speedup_vs_per_lattice_blocks": sum(t_lat) / t_all,
+           "all_in_one_ms": t_all, "per_lattice_block_ms": t_lat, "one_at_a_time_ms": t_seq or None,
+           "speedup_vs_one_at_a_time": sum(t_seq) / t_all if t_seq else None,
+           "speedup_vs_per_lattice_blocks": sum(t_lat) / t_all,
            "outer_iterations": [i.outer_iterations for i in infos],
            "true_residual_max": max(i.true_residual for i in infos), "setup_ms": setup_ms}
     for S in solvers:
@@ -754,24 +875,25 @@ def main():
     ap.add_argument("--impl", choices=["mg", "reference"], default="mg")
     ap.add_argument("--mass", type=float, default=MASSES[-1])
     ap.add_argument("--no-eo", action="store_true", help="skip the plain EO-GCR comparison")
-    ap.add_argument("--eo-maxit", type=int, default=20000)
+    ap.add_argument("--eo-maxit", type=int, default=5000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
-    ap.add_argument("--config3", action="store_true",
-                    help="also run the 3-level 24^3x64 solve with BF16 and FP32 storage (about a minute)")
-    ap.add_argument("--multi", action="store_true",
-                    help="also solve the batched sources on three lattices of uneven size (about a minute)")
+    ap.add_argument("--no-config3", action="store_true",
+                    help="skip the 24^3x64 solves (2 and 3 levels, BF16 and FP32 storage)")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="skip the batched sources on three lattices of uneven size")
+    ap.add_argument("--ref-procs", type=int, default=0,
+                    help="reference arm: host processes (default: one per core, at most 16)")
+    ap.add_argument("--ref-dims", help=argparse.SUPPRESS)   # reference arm on another lattice (CPU tests)
+    ap.add_argument("--multi-sequential", action="store_true",
+                    help="also solve the 28 batched sources one at a time (about 30 s)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FP16-storage, gradient and multi-RHS D_r measurements")
-    ap.add_argument("--profile", choices=["solve", "block", "dslash", "dslash_mrhs"],
+    ap.add_argument("--profile", choices=["solve", "block", "dslash", "dslash_mrhs", "coarse"],
                     help="for ncu --profile-from-start off: bracket `steps` solves (after setup and warm-up), "
                          "`steps` block solves of the batched right-hand sides, or `steps` launches of the FP32 fused "
                          "dslash (HBM-size lattice; dslash_mrhs: its multi-RHS form), with cudaProfilerStart/Stop; "
                          "nothing else is run")
-    ap.add_argument("--cpu-sample", nargs=2, help=argparse.SUPPRESS)
     args = ap.parse_args()
-    if args.cpu_sample:
-        cpu_sample_main(float(args.cpu_sample[0]), int(args.cpu_sample[1]))
-        return
     if args.profile:
         profile_main(args)
         return
@@ -783,59 +905,80 @@ def main():
         if dist.rank != 0:
             dist.close()
             return
-        samples = []
-        for i in range(args.warmup + args.steps):
-            s = cpu_sample(args.mass, CPU_SAMPLE_DR)
-            if i >= args.warmup:
-                samples.append(s)
-        ms_dr = statistics.median(s["ms_per_dr"] for s in samples)
-        value = ms_dr * REFERENCE_DR_PER_SOLVE
+        # every host process: the oracle's setup on CPU_DIMS, then warmup + steps
+        # samples of CPU_STEP_ITERS outer iterations; a step's value is the
+        # median over the processes, projected to one 16^3x32 solve
+        n = host_cores(args.ref_procs)
+        rdims = tuple(int(x) for x in args.ref_dims.split(",")) if args.ref_dims else CPU_DIMS
+        res = oracle_pool([("steps", q, args.warmup + args.steps, rdims) for q in range(n)])
+        vol = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) / (rdims[0] * rdims[1] * rdims[2] * rdims[3])
+        steps = [1e3 * statistics.median(r["step_s"][i] for r in res) / CPU_STEP_ITERS * vol * REFERENCE_OUTER_PER_SOLVE / n
+                 for i in range(args.warmup, args.warmup + args.steps)]
+        value = statistics.mean(steps)
+        sample = (f"{n} concurrent single-thread processes, each the oracle's MG-GCR on a "
+                  f"{'x'.join(str(d) for d in rdims)} lattice of the same "
+                  f"construction and parameters (4^4 blocks, Nv=24, setup {CPU_SETUP_ITERS} passes per vector, not "
+                  f"timed); a step = {CPU_STEP_ITERS} outer iterations (fine and coarse work) in every process; "
+                  f"projection: median seconds per outer iteration x {vol:.0f} (volume) x "
+                  f"{REFERENCE_OUTER_PER_SOLVE} (outer iterations of the GPU solve) / {n} (processes)")
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "ms", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": workload_name(args.mass)},
-                "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
-                                 "sample": f"{CPU_SAMPLE_DR} oracle D_r applications per step, projected to a solve "
-                                           f"by {REFERENCE_DR_PER_SOLVE} fine D_r applications (coarse work excluded)"},
+                "cpu_baseline": {"value": value, "unit": "ms", "cores": n, "kind": "oracle", "sample": sample},
                 "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         dist.close()
         return
 
     r = run_gpu(args, dist)
-    if args.multi:
-        r["extra"]["multi_lattice"] = run_multi(dist.local)
-    if args.config3:
-        r["extra"]["three_level_24x64"] = run_config3(dist.local)
+    if not args.no_multi:
+        t_m = time.perf_counter()
+        r["extra"]["multi_lattice"] = run_multi(dist.local, args.multi_sequential)
+        SECTIONS["multi_lattice"] = time.perf_counter() - t_m
+    if not args.no_config3:
+        t_c = time.perf_counter()
+        r["extra"]["config3_24x64"] = run_config3(dist.local)
+        SECTIONS["config3"] = time.perf_counter() - t_c
     info = r["info"]
     dr_per_solve = info.dslash_launches / 2.0
+    c = r["coarse"]
+    roof = {"kernel": "persistent coarsest-level GCR with links streamed through shared memory (k_coarse_gcr_stream, "
+                      "with its site-local pre/post launches), 4^3x8 x Nc=48 coarse lattice of the step",
+            "bound": "hbm", "achieved": c["bytes"] / c["ms"] / 1e6, "peak": hbm_peak, "unit": "GB/s",
+            "frac": c["bytes"] / c["ms"] / 1e6 / hbm_peak,
+            "traffic": (COARSE_TRAFFIC_BYTES if COARSE_TRAFFIC_BYTES and round(c["gcr_iterations"]) == COARSE_PROFILE_ITERS
+                        else None),
+            "peak_kind": peak_kind, "bytes_per_launch": c["bytes"], "ms_per_launch": c["ms"],
+            "gcr_iterations_per_launch": c["gcr_iterations"], "share_of_step": c["share_of_step"],
+            "note": "the 75.5 MB of links per iteration stay in the 129 MB L2; bytes are the links each GCR iteration "
+                    "streams (folded odd-site links FP32 + even-site Y), per launch"}
     k = r["kern"]["dslash_clover_fp32"]
-    roof = {"kernel": "fused hop + clover-inverse dslash, FP32, 32^3x64 (HBM-resident)", "bound": "hbm",
-            "achieved": k["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": k["gbs"] / hbm_peak,
-            "traffic": DSLASH_TRAFFIC_BYTES, "peak_kind": peak_kind, "bytes_per_launch": k["bytes"],
-            "ms_per_launch": k["ms"]}
+    roof_dslash = {"kernel": "fused hop + clover-inverse dslash, FP32, 32^3x64 (HBM-resident)", "bound": "hbm",
+                   "achieved": k["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": k["gbs"] / hbm_peak,
+                   "traffic": DSLASH_TRAFFIC_BYTES, "peak_kind": peak_kind, "bytes_per_launch": k["bytes"],
+                   "ms_per_launch": k["ms"]}
     line = {"metric": METRIC, "value": r["ms"], "unit": "ms", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms"], "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": workload_name(args.mass), "lattice": "16x16x16x32", "m0": args.mass,
-                       "mg": "2-level, 4^4 blocks, Nv=24, coarse GCR(64) tol 0.3, nu_post=4 MR",
+                       "mg": "2-level, 4^4 blocks, Nv=24, coarse GCR(64) tol 0.1, nu_post=4 MR",
                        "precision": "FP64 outer GCR(16), FP32 preconditioner", "l2": "flushed before every solve",
                        "parallelism": f"replicas x{dist.world}"},
-            "roofline": roof,
+            "roofline": roof, "roofline_dslash": roof_dslash,
             "e2e": {"value": r["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": r["nbytes"],
                     "d2h_bytes_per_step": r["nbytes"]},
             "gpu_launches": r["launches"], "clocks": r["clocks"],
             "solve": {"outer_iterations": info.outer_iterations, "coarse_iterations": info.coarse_iterations[1],
                       "true_residual": info.true_residual, "fine_dr_applications": dr_per_solve,
                       "step_ms": r["times"]},
-            "setup_ms": r["setup_ms"], "setup_passes": r["sinfo"].passes[0],
+            "setup_ms": r["setup_ms"], "setup_passes": r["sinfo"].passes[0], "peaks": dict(r["peaks"], hbm_gbs=hbm_peak),
             "eo_gcr": r["eo"], "kernels": r["kern"], **r["extra"]}
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
-        s = cpu_sample(args.mass, CPU_SAMPLE_DR)
-        line["cpu_baseline"] = {"value": s["ms_per_dr"] * dr_per_solve, "unit": "ms", "cores": 1, "kind": "oracle",
-                                "sample": f"{CPU_SAMPLE_DR} applications of the oracle's FP64 D_r on this workload "
-                                          f"({s['ms_per_dr']:.0f} ms each), projected by the {dr_per_solve:.0f} fine "
-                                          f"D_r applications of one MG solve; coarse work excluded"}
+        t_b = time.perf_counter()
+        line["cpu_baseline"] = cpu_baseline(info.outer_iterations, r["small_ms"])
+        SECTIONS["cpu_baseline"] = time.perf_counter() - t_b
+    line["bench_sections_s"] = SECTIONS
     if dist.rank == 0:
         print(json.dumps(line))
     dist.close()

@@ -412,6 +412,14 @@ MG_API int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int 
 MG_API int mg_benchmark_kernel_nrhs(void* ctx, int kernel, int prec, int nrhs, int warmup, int iters, double* avg_ms,
                                     double* bytes_per_launch);
 
+/* Measures the CUDA-core FMA throughput of `device` in precision `prec`
+ * (MG_FP64 or MG_FP32) with CUDA events: 8 independent FMA chains per thread,
+ * 8 blocks of 256 threads per SM, 2 flops per FMA.  The roofline
+ * denominator of the kernels bound by FP64 (or FP32) arithmetic rather than
+ * by memory; not part of the paper's method.  *tflops receives TFLOP/s.
+ * Errors: MG_ERR_ARG, MG_ERR_CUDA. */
+MG_API int mg_benchmark_fma(int device, int prec, double* tflops);
+
 /* Times `iters` solves of the coarsest level's system (after `warmup`
  * untimed ones) for a fixed Philox right-hand side: the persistent
  * coarsest-level GCR with its even-odd reconstruction, as the multigrid cycle

@@ -40,7 +40,7 @@ EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "m
             "mg_set_clover", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
             "mg_get_coarse_links", "mg_save_setup", "mg_load_setup", "mg_update_mass", "mg_adapt_setup", "mg_solve", "mg_solve_batch",
             "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
-            "mg_benchmark_coarse_solve",
+            "mg_benchmark_coarse_solve", "mg_benchmark_fma",
             "mg_level_info"]
 
 
@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
             "mg_apply_noalloc": [vp, ip, vp, vp, ip],
             "mg_benchmark_kernel_nrhs": [vp, ip, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_benchmark_coarse_solve": [vp, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp)],
+            "mg_benchmark_fma": [ip, ip, ctypes.POINTER(dp)],
             "mg_level_info": [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)],
         }
         for name, args in sig.items():
@@ -348,6 +349,13 @@ def mg_benchmark_coarse_solve(ctx, warmup: int = 3, iters: int = 20):
     _check(lib().mg_benchmark_coarse_solve(ctx, int(warmup), int(iters), ctypes.byref(ms), ctypes.byref(by),
                                            ctypes.byref(it)), "mg_benchmark_coarse_solve")
     return ms.value, by.value, it.value
+
+
+def mg_benchmark_fma(device: int = 0, prec: int = MG_FP32) -> float:
+    """Measured CUDA-core FMA throughput of `device` in TFLOP/s."""
+    t = ctypes.c_double()
+    _check(lib().mg_benchmark_fma(int(device), int(prec), ctypes.byref(t)), "mg_benchmark_fma")
+    return t.value
 
 
 def mg_level_info(ctx, level: int):

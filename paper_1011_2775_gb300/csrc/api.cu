@@ -729,6 +729,15 @@ int mg_apply(void* ctx, int op, int level, void* out, const void* in, int nrhs, 
   });
 }
 
+int mg_benchmark_fma(int device, int prec, double* tflops) {
+  return guarded([&]() {
+    if (!tflops || (prec != MG_FP64 && prec != MG_FP32)) mg::raise(MG_ERR_ARG, "bad FMA benchmark arguments");
+    MG_CUDA(cudaSetDevice(device));
+    *tflops = mg::fma_peak_tflops(prec);
+    return MG_OK;
+  });
+}
+
 int mg_benchmark_coarse_solve(void* ctx, int warmup, int iters, double* avg_ms, double* bytes_per_solve,
                               double* iterations_per_solve) {
   return guarded([&]() {

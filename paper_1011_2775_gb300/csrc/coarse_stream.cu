@@ -29,7 +29,7 @@
 //    w comes from Pythagoras (the w_j are orthonormal), with an exact second
 //    reduction when that subtraction loses more than three digits; <w', r>
 //    = <w, r> / gamma because r is orthogonal to the w_j.  The block's slice
-//    of the Krylov vectors w_j stays in shared memory when it fits.
+//    of the Krylov vectors w_j stays in shared memory when it is small.
 //  * Every inner product is reduced deterministically (per-block FP64
 //    partials summed in the same order by every block), so all blocks take
 //    identical decisions and the result is reproducible bit for bit.
@@ -170,14 +170,16 @@ __device__ void gather(const SArgs& a, int i0, int i1, int ips, int site_base, c
   __syncthreads();
 }
 
-// Sum over the warp of 16 per-lane values; afterwards lane l holds the total
-// of value (l >> 1) & 15 (each level keeps half of the values and passes the
-// other half to its partner).
-__device__ __forceinline__ float reduce16(float v[16]) {
+// Sum over the warp of V per-lane values (V = 2, 4, 8, 16): each of the first
+// log2 V levels keeps half of the values and passes the other half to its
+// partner, the remaining levels add whole values.  Afterwards lane l holds the
+// total of value (l >> log2(32 / V)) & (V - 1).
+template <int V>
+__device__ __forceinline__ float reduce_values(float v[V]) {
   const int lane = threadIdx.x & 31;
+  int off = 16;
 #pragma unroll
-  for (int lvl = 0; lvl < 4; lvl++) {
-    const int off = 16 >> lvl, half = 8 >> lvl;
+  for (int half = V / 2; half >= 1; half /= 2, off /= 2) {
     const bool up = (lane & off) != 0;
 #pragma unroll
     for (int i = 0; i < half; i++) {
@@ -186,44 +188,71 @@ __device__ __forceinline__ float reduce16(float v[16]) {
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
     }
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  float t = v[0];
+#pragma unroll
+  for (int o = 16 / V; o >= 1; o /= 2) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
 }
 
-// out[row] = sum_k L[row][k] v[k] for the nr rows of a staged item; lane 4 row
-// returns {re, im} of its row in `res` (true when it holds one)
-template <int ST>
-__device__ __forceinline__ bool item_rows(const unsigned char* stage, int nr, int K, const float2* v, float2& res) {
+// out[row] = sum_k L[row][k] v[k] for the NR rows of a staged item (row-major,
+// K complex per row, storage format ST).  Every lane strides along the rows
+// two float4 steps at a time, loading the vector element once for all rows.
+// Returns true on the lane that holds row `row`'s {re, im} in `res`.
+template <int ST, int NR>
+__device__ __forceinline__ bool item_rows(const unsigned char* stage, int K, const float2* v, float2& res, int& row) {
+  constexpr int V = NR <= 1 ? 2 : NR <= 2 ? 4 : NR <= 4 ? 8 : 16;
+  constexpr int SH = V == 2 ? 4 : V == 4 ? 3 : V == 8 ? 2 : 1;   // log2(32 / V)
   const float4* v4 = reinterpret_cast<const float4*>(v);
   const int lane = threadIdx.x & 31;
   const int K2 = K >> 1;
-  float acc[16];
+  float acc[V];
 #pragma unroll
-  for (int i = 0; i < 16; i++) acc[i] = 0.f;
-  for (int q = lane; q < K2; q += 32) {
+  for (int i = 0; i < V; i++) acc[i] = 0.f;
+  auto step = [&](int q) {
     const float4 x = v4[q];
 #pragma unroll
-    for (int r = 0; r < kMaxRows; r++) {
-      if (r < nr) {
-        float4 m;
-        if constexpr (ST == kStF32)
-          m = reinterpret_cast<const float4*>(stage)[(size_t)r * K2 + q];
-        else
-          m = LinkPair<ST>::decode(reinterpret_cast<const uint2*>(stage)[(size_t)r * K2 + q]);
-        acc[2 * r] = fmaf(m.x, x.x, acc[2 * r]);
-        acc[2 * r] = fmaf(-m.y, x.y, acc[2 * r]);
-        acc[2 * r] = fmaf(m.z, x.z, acc[2 * r]);
-        acc[2 * r] = fmaf(-m.w, x.w, acc[2 * r]);
-        acc[2 * r + 1] = fmaf(m.x, x.y, acc[2 * r + 1]);
-        acc[2 * r + 1] = fmaf(m.y, x.x, acc[2 * r + 1]);
-        acc[2 * r + 1] = fmaf(m.z, x.w, acc[2 * r + 1]);
-        acc[2 * r + 1] = fmaf(m.w, x.z, acc[2 * r + 1]);
-      }
+    for (int r = 0; r < NR; r++) {
+      float4 m;
+      if constexpr (ST == kStF32)
+        m = reinterpret_cast<const float4*>(stage)[(size_t)r * K2 + q];
+      else
+        m = LinkPair<ST>::decode(reinterpret_cast<const uint2*>(stage)[(size_t)r * K2 + q]);
+      acc[2 * r] = fmaf(m.x, x.x, acc[2 * r]);
+      acc[2 * r] = fmaf(-m.y, x.y, acc[2 * r]);
+      acc[2 * r] = fmaf(m.z, x.z, acc[2 * r]);
+      acc[2 * r] = fmaf(-m.w, x.w, acc[2 * r]);
+      acc[2 * r + 1] = fmaf(m.x, x.y, acc[2 * r + 1]);
+      acc[2 * r + 1] = fmaf(m.y, x.x, acc[2 * r + 1]);
+      acc[2 * r + 1] = fmaf(m.z, x.w, acc[2 * r + 1]);
+      acc[2 * r + 1] = fmaf(m.w, x.z, acc[2 * r + 1]);
     }
+  };
+  int q = lane;
+  for (; q + 32 < K2; q += 64) {
+    step(q);
+    step(q + 32);
   }
-  const float t = reduce16(acc);                       // lane l: value (l >> 1) & 15
-  const float im = __shfl_down_sync(0xffffffffu, t, 2);  // lane 4r + 2 holds Im of row r
+  if (q < K2) step(q);
+  const float t = reduce_values<V>(acc);                       // lane l: value (l >> SH) & (V - 1)
+  const float im = __shfl_down_sync(0xffffffffu, t, 1 << SH);  // value 2 row + 1
   res = make_float2(t, im);
-  return (lane & 3) == 0 && (lane >> 2) < nr;
+  row = lane >> (SH + 1);
+  return (lane & ((2 << SH) - 1)) == 0 && row < NR;
+}
+
+template <int ST>
+__device__ __forceinline__ bool item_rows_n(int nr, const unsigned char* stage, int K, const float2* v, float2& res,
+                                            int& row) {
+  switch (nr) {
+    case 1: return item_rows<ST, 1>(stage, K, v, res, row);
+    case 2: return item_rows<ST, 2>(stage, K, v, res, row);
+    case 3: return item_rows<ST, 3>(stage, K, v, res, row);
+    case 4: return item_rows<ST, 4>(stage, K, v, res, row);
+    case 5: return item_rows<ST, 5>(stage, K, v, res, row);
+    case 6: return item_rows<ST, 6>(stage, K, v, res, row);
+    case 7: return item_rows<ST, 7>(stage, K, v, res, row);
+    default: return item_rows<ST, 8>(stage, K, v, res, row);
+  }
 }
 
 // One phase of this warp's items: waits for each staged item, computes its
@@ -248,11 +277,11 @@ __device__ bool run_items(const SArgs& a, Stream& st, int kind, const float2* gv
     const int s = it / ips, r0 = (it % ips) * rows;
     const int nr = min(rows, nc - r0);
     float2 res;
-    const bool mine = kind == 0 ? item_rows<kStF32>(st.ring + (size_t)stage * a.stage_bytes, nr, K,
-                                                    gv + (size_t)(s - sbase) * K, res)
-                                : item_rows<ST>(st.ring + (size_t)stage * a.stage_bytes, nr, K,
-                                                gv + (size_t)(s - sbase) * K, res);
-    if (mine) epi((size_t)s * nc + r0 + (lane >> 2), res);
+    int row;
+    const unsigned char* sp = st.ring + (size_t)stage * a.stage_bytes;
+    const float2* vp = gv + (size_t)(s - sbase) * K;
+    const bool mine = kind == 0 ? item_rows_n<kStF32>(nr, sp, K, vp, res, row) : item_rows_n<ST>(nr, sp, K, vp, res, row);
+    if (mine) epi((size_t)s * nc + r0 + row, res);
     __syncwarp();
     if (lane == 0) issue(a, st, st.t + kStagesPerWarp);
     st.t++;
@@ -704,13 +733,15 @@ Plan make_plan(const LevelGeom& G, const CoarseOp& C, int grid, int m) {
   const size_t budget = (size_t)optin - 4096;   // static shared memory and slack
   const size_t fixed = sizeof(float2) * (kNR * kWarps + kNR) + sizeof(float2) * 2 * kThreads;
   p.grid = grid;
-  // the w_j slice in shared memory when it takes at most a quarter of the
-  // budget; a block's slice has at most ceil(n / grid) elements plus the
-  // rows of the partial items at both ends of its range
+  // the w_j slice in shared memory only when it is small (a sixteenth of the
+  // budget): measured on GB300 at Nc = 48, m = 64, a deeper link ring gains
+  // more than shared-memory Gram-Schmidt vectors save.  A block's slice has
+  // at most ceil(n / grid) elements plus the rows of the partial items at
+  // both ends of its range.
   const size_t n = (size_t)G.half * nc;
   const int gb = std::max(1, grid);
   const int ebound = (int)((n + gb - 1) / gb) + (int)((7LL * G.half + gb - 1) / gb) + 2 * kMaxRows;
-  const bool wsmem = (size_t)m * ebound * sizeof(float2) <= budget / 4;
+  const bool wsmem = (size_t)m * ebound * sizeof(float2) <= budget / 16;
   const size_t wbytes = wsmem ? (size_t)m * ebound * sizeof(float2) : 0;
   int gsites = 4;
   for (int pass = 0; pass < 3; pass++) {

@@ -410,6 +410,8 @@ void mg_reset_counters(Ctx* c);
 // times `iters` applications of the level-1 coarse D_hat_r (see mg_benchmark_kernel)
 void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes);
 void mg_read_counters(Ctx* c, long long* coarse_iters);
+// measured CUDA-core FMA throughput of the current GPU (peaks.cu), TFLOP/s
+double fma_peak_tflops(int prec);
 // times `iters` coarsest-level solves (see mg_benchmark_coarse_solve)
 void mg_benchmark_coarse_solve(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes, double* its);
 
