@@ -279,6 +279,29 @@ def profile_main(args):
         print(json.dumps({"profile": "coarse", "launches": args.steps, "gcr_iterations": its, "ms_per_solve": ms,
                           "link_bytes_per_solve": by}))
         S.close()
+    elif args.profile == "block_tc":
+        # the block solve of BATCH_RHS sources with FP16 links: its coarsest-level
+        # solves run on tensor cores (k_coarse_gcr_tc)
+        etas = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED + 10, nrhs=BATCH_RHS)).cuda()
+        psis = torch.zeros_like(etas)
+        S = Solver(DIMS)
+        S.load_gauge(U)
+        S.set_clover(CSW, args.mass)
+        S.set_params(seed=NULLVEC_SEED, maxit_fine=2000, rhs_block=BATCH_RHS, storage=B.MG_STORE_FP16, coarse_impl=4,
+                     **MG)
+        S.setup()
+        for _ in range(args.warmup):
+            S.solve(etas, TOL, B.MG_MODE_MG, out=psis)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.steps):
+            _, info = S.solve(etas, TOL, B.MG_MODE_MG, out=psis)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile": "block_tc", "nrhs": BATCH_RHS, "steps": args.steps,
+                          "kernel_launches": info.kernel_launches, "outer_iterations": info.outer_iterations,
+                          "true_residual": info.true_residual}))
+        S.close()
     elif args.profile == "block":
         etas = torch.from_numpy(I.gaussian_source(DIMS, SOURCE_SEED + 10, nrhs=BATCH_RHS)).cuda()
         psis = torch.zeros_like(etas)
@@ -888,7 +911,7 @@ def main():
                     help="also solve the 28 batched sources one at a time (about 30 s)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FP16-storage, gradient and multi-RHS D_r measurements")
-    ap.add_argument("--profile", choices=["solve", "block", "dslash", "dslash_mrhs", "coarse"],
+    ap.add_argument("--profile", choices=["solve", "block", "block_tc", "dslash", "dslash_mrhs", "coarse"],
                     help="for ncu --profile-from-start off: bracket `steps` solves (after setup and warm-up), "
                          "`steps` block solves of the batched right-hand sides, or `steps` launches of the FP32 fused "
                          "dslash (HBM-size lattice; dslash_mrhs: its multi-RHS form), with cudaProfilerStart/Stop; "

@@ -146,8 +146,10 @@ typedef struct {
                                   /* captured CUDA graph (0: launch its kernels one by one)        */
   int coarse_impl;                /* coarsest-level persistent GCR: 0 chosen by timing on the      */
                                   /* first solve; 1 single-system kernel, 2 batched kernel,        */
-                                  /* 3 links streamed through shared memory (even-odd levels;     */
-                                  /* otherwise 1)                                                  */
+                                  /* 3 links streamed through shared memory (even-odd levels),     */
+                                  /* 4 tensor cores (even-odd levels, FP16 storage, Nc a multiple  */
+                                  /* of 8 up to 64; also the batched cycle's solves); an           */
+                                  /* implementation that does not apply falls back to 1            */
 } mg_params;
 
 typedef struct {

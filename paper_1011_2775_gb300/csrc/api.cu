@@ -286,7 +286,7 @@ int mg_set_params(void* ctx, const mg_params* p) {
     if (p->coarse_op != MG_COARSE_DP && p->coarse_op != MG_COARSE_D) mg::raise(MG_ERR_ARG, "bad coarse_op");
     if (p->rhs_block < 1 || p->rhs_block > 16) mg::raise(MG_ERR_ARG, "rhs_block must be in [1, 16]");
     if (p->cuda_graphs != 0 && p->cuda_graphs != 1) mg::raise(MG_ERR_ARG, "cuda_graphs must be 0 or 1");
-    if (p->coarse_impl < 0 || p->coarse_impl > 3) mg::raise(MG_ERR_ARG, "coarse_impl must be in [0, 3]");
+    if (p->coarse_impl < 0 || p->coarse_impl > 4) mg::raise(MG_ERR_ARG, "coarse_impl must be in [0, 4]");
     int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
     int ndof = 12;
     for (int l = 0; l + 1 < p->levels; l++) {

@@ -178,8 +178,13 @@ void precondition_all(std::vector<Run*>& runs, int k) {
       }
     const mg_params& p0 = c0->params;
     const int restart = p0.restart_coarse > 0 ? p0.restart_coarse : 32;
-    for (const auto& L : launches)
+    for (const auto& L : launches) {
+      // the systems of one FP16 lattice on tensor cores (mg_params.coarse_impl 0 or 4)
+      if ((p0.coarse_impl == 0 || p0.coarse_impl == 4) &&
+          coarse_gcr_tc_try(L, mg_batch_buffers(c0), restart, p0.maxit_coarse, c0->ws.flags.as<int>(), c0->stream))
+        continue;
       coarse_gcr_solve_multi(L, mg_batch_buffers(c0), restart, p0.maxit_coarse, c0->ws.flags.as<int>(), c0->stream);
+    }
     cudaEvent_t done;
     MG_CUDA(cudaEventCreateWithFlags(&done, cudaEventDisableTiming));
     MG_CUDA(cudaEventRecord(done, c0->stream));

@@ -21,6 +21,8 @@
 
 namespace mg {
 
+struct CoarseSystem;   // one coarse system of a batched solve (below)
+
 // Storage format of prolongators / coarse links
 enum Store { STORE_F32 = 0, STORE_F16 = 1, STORE_BF16 = 2 };
 
@@ -122,6 +124,8 @@ struct CoarseGCRBuffers {
   // streamed solve (coarse_stream.cu; grown on demand): partial sums, the
   // Gram-Schmidt coefficients, grid-barrier counter and abort flag
   DBuf st_part, st_beta, st_sync;
+  // tensor-core solve (coarse_tc.cu; grown on demand)
+  DBuf tc_y, tc_r, tc_br, tc_s, tc_sy, tc_t, tc_tb, tc_W, tc_Z, tc_part, tc_sync;
   void init(const LevelGeom& G, int nc, int m);
 };
 // x = D_hat^{-1} b to ||b - D_hat x|| <= tol_rel ||b|| (or maxit iterations) by
@@ -141,6 +145,21 @@ std::vector<int> coarse_gcr_stream_grids(const LevelGeom& G, const CoarseOp& C);
 void coarse_gcr_stream_solve(const LevelGeom& G, const CoarseOp& C, CoarseGCRBuffers& B, int m, int maxit,
                              double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s,
                              int grid);
+// The same GCR for nb (1 .. 16) systems of one even-odd lattice whose links
+// are stored in FP16, with the hop terms on tensor cores (coarse_tc.cu):
+// system p's right-hand side at b + 2 p bstride floats, its solution at
+// x + 2 p xstride floats (full coarse vectors), tolerance tol_rel[p]; grid:
+// one of coarse_gcr_tc_grids().  Raises FLAG_TIMEOUT if a wait runs out of time.
+bool coarse_gcr_tc_ok(const LevelGeom& G, const CoarseOp& C, int nb);
+std::vector<int> coarse_gcr_tc_grids(const LevelGeom& G, const CoarseOp& C, int nb);
+void coarse_gcr_tc_solve(const LevelGeom& G, const CoarseOp& C, CoarseGCRBuffers& B, int m, int maxit,
+                         const double* tol_rel, int nb, const float* b, size_t bstride, float* x, size_t xstride,
+                         long long* d_iters, int* flags, cudaStream_t s, int grid);
+// the systems on tensor cores when they are consecutive vectors of one FP16
+// lattice that coarse_gcr_tc_ok accepts (returns false, launching nothing,
+// otherwise)
+bool coarse_gcr_tc_try(const std::vector<CoarseSystem>& sys, CoarseGCRBuffers& B, int m, int maxit, int* flags,
+                       cudaStream_t s);
 // smaller grids worth timing against B.grid: the fewest blocks that keep the
 // largest number of stencil sites per block, and one more site per block
 // (fewer blocks at every grid barrier)

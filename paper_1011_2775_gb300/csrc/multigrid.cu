@@ -265,8 +265,15 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
     const std::vector<int> smaller = coarse_gcr_smaller_grids(G, W.cg);
     const std::vector<int> streamed =
         coarse_gcr_stream_ok(G, H.cop[l]) ? coarse_gcr_stream_grids(G, H.cop[l]) : std::vector<int>();
+    const std::vector<int> tensor =
+        coarse_gcr_tc_ok(G, H.cop[l], 1) ? coarse_gcr_tc_grids(G, H.cop[l], 1) : std::vector<int>();
     auto run = [&](int which, long long* it) {
-      if (which >= 100)
+      if (which >= 200) {
+        const double tol = p.tol_coarse;
+        const size_t nf = G.vec_complex();
+        coarse_gcr_tc_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, &tol, 1, b, nf, x, nf, it,
+                            c->ws.flags.as<int>(), s, tensor[which - 200]);
+      } else if (which >= 100)
         coarse_gcr_stream_solve(G, H.cop[l], W.cg, restart, p.maxit_coarse, p.tol_coarse, b, x, it,
                                 c->ws.flags.as<int>(), s, streamed[which - 100]);
       else if (which == 1)
@@ -278,22 +285,36 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
     };
     if (W.coarse_impl < 0) {
       if (!W.tune_iters.get()) W.tune_iters.alloc(sizeof(long long));
-      TuneKey key{"coarse_gcr2", {G.L[0], G.L[1], G.L[2], G.L[3]}, H.cop[l].nc, H.cop[l].store};
+      TuneKey key{"coarse_gcr3", {G.L[0], G.L[1], G.L[2], G.L[3]}, H.cop[l].nc, H.cop[l].store};
       std::vector<int> cands = {0, 1};
       for (size_t k = 0; k < smaller.size(); k++) cands.push_back(2 + (int)k);
       for (size_t k = 0; k < streamed.size(); k++) cands.push_back(100 + (int)k);
-      if (c->params.coarse_impl > 0) {
-        // a forced implementation (mg_params.coarse_impl): 1 original, 2 batched, 3 streamed
-        cands = c->params.coarse_impl == 1 ? std::vector<int>{0}
-                : c->params.coarse_impl == 2 ? std::vector<int>{1}
-                : streamed.empty()           ? std::vector<int>{0}
-                                             : std::vector<int>{100};
-        W.coarse_impl = cands[0];
+      const int forced = c->params.coarse_impl;
+      // one system on tensor cores uses one column of eight of every MMA and
+      // pays two site-inverse passes per iteration: measured slower than the
+      // streamed kernel on GB300, so it runs only when forced
+      if (forced == 4)
+        for (size_t k = 0; k < tensor.size(); k++) cands.push_back(200 + (int)k);
+      if (forced > 0) {
+        // a forced implementation (mg_params.coarse_impl): 1 original, 2 batched,
+        // 3 streamed, 4 tensor cores; the grid is still chosen by timing
+        std::vector<int> f;
+        for (int cnd : cands)
+          if ((forced == 1 && (cnd == 0 || (cnd >= 2 && cnd < 100))) || (forced == 2 && cnd == 1) ||
+              (forced == 3 && cnd >= 100 && cnd < 200) || (forced == 4 && cnd >= 200))
+            f.push_back(cnd);
+        if (f.empty()) f.push_back(0);
+        W.coarse_impl = f.size() == 1 ? f[0]
+                                      : tuned_block(TuneKey{forced == 3 ? "coarse_gcr_stream" : forced == 4 ? "coarse_gcr_tc"
+                                                                                                            : "coarse_gcr_single",
+                                                            {G.L[0], G.L[1], G.L[2], G.L[3]}, H.cop[l].nc, H.cop[l].store},
+                                                    f, [&](int which) { run(which, W.tune_iters.as<long long>()); }, s);
       } else {
         W.coarse_impl = tuned_block(key, cands, [&](int which) { run(which, W.tune_iters.as<long long>()); }, s);
       }
       const bool valid = (W.coarse_impl >= 0 && W.coarse_impl < 2 + (int)smaller.size()) ||
-                         (W.coarse_impl >= 100 && W.coarse_impl < 100 + (int)streamed.size());
+                         (W.coarse_impl >= 100 && W.coarse_impl < 100 + (int)streamed.size()) ||
+                         (W.coarse_impl >= 200 && W.coarse_impl < 200 + (int)tensor.size());
       if (!valid) W.coarse_impl = 0;  // a cached choice from other grids
     }
     run(W.coarse_impl, d_it);
@@ -653,8 +674,14 @@ void mg_batch_coarse(Ctx* c, int nb) {
     const int gmax = coarse_gcr_batch_max();
     std::vector<CoarseSystem> sys;
     mg_batch_systems(c, nb, sys);
+    const LevelGeom& G1 = b.H.geo[1];
+    const CoarseOp& C1 = b.H.cop[1];
+    const bool tc = b.p.coarse_impl == 0 || b.p.coarse_impl == 4;
     for (int q0 = 0; q0 < nb; q0 += gmax) {
       std::vector<CoarseSystem> part(sys.begin() + q0, sys.begin() + std::min(nb, q0 + gmax));
+      // tensor cores for FP16 links (the group's systems are consecutive vectors of this context)
+      if (tc && coarse_gcr_tc_try(part, b.H.work[1].cg, restart, b.p.maxit_coarse, c->ws.flags.as<int>(), b.s))
+        continue;
       coarse_gcr_solve_multi(part, b.H.work[1].cg, restart, b.p.maxit_coarse, c->ws.flags.as<int>(), b.s);
     }
   } else {
