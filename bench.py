@@ -279,6 +279,29 @@ def profile_main(args):
         print(json.dumps({"profile": "coarse", "launches": args.steps, "gcr_iterations": its, "ms_per_solve": ms,
                           "link_bytes_per_solve": by}))
         S.close()
+    elif args.profile == "transfer":
+        # the level-0 restriction and prolongation on the even sites of the
+        # workload, one launch each for 1 and BATCH_RHS right-hand sides
+        S = Solver(DIMS)
+        S.load_gauge(U)
+        S.set_clover(CSW, args.mass)
+        S.set_params(seed=NULLVEC_SEED, maxit_fine=2000, **MG)
+        S.setup()
+        codes = [(B.MG_KERNEL_RESTRICT, 1), (B.MG_KERNEL_PROLONG, 1), (B.MG_KERNEL_RESTRICT, BATCH_RHS),
+                 (B.MG_KERNEL_PROLONG, BATCH_RHS)]
+        for code, nrhs in codes:
+            B.mg_benchmark_kernel_nrhs(S.ctx, code, B.MG_FP32, nrhs, warmup=max(1, args.warmup), iters=1)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        res = []
+        for code, nrhs in codes:
+            ms, by = B.mg_benchmark_kernel_nrhs(S.ctx, code, B.MG_FP32, nrhs, warmup=0, iters=args.steps)
+            res.append({"kernel": "restrict" if code == B.MG_KERNEL_RESTRICT else "prolong", "nrhs": nrhs,
+                        "ms_per_launch": ms, "bytes_per_launch": by})
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile": "transfer", "launches": args.steps, "results": res}))
+        S.close()
     elif args.profile == "block_tc":
         # the block solve of BATCH_RHS sources with FP16 links: its coarsest-level
         # solves run on tensor cores (k_coarse_gcr_tc)
@@ -419,6 +442,13 @@ def run_gpu(args, dist: Dist) -> dict:
     S.set_params(tol_coarse=keep[0], maxit_coarse=keep[1])
     coarse = {"ms": c_ms, "bytes": c_bytes, "gcr_iterations": c_its, "avg_iterations_in_step": per_solve,
               "share_of_step": c_ms * last.outer_iterations / ms}
+    # the level-0 restriction and prolongation on the even sites (back-to-back
+    # launches; P of the even sites, 151 MB in FP32, exceeds the L2)
+    transfer = {}
+    for name, code in [("restrict", B.MG_KERNEL_RESTRICT), ("prolong", B.MG_KERNEL_PROLONG)]:
+        for nrhs in (1, BATCH_RHS):
+            ms_t, by = B.mg_benchmark_kernel_nrhs(S.ctx, code, B.MG_FP32, nrhs, warmup=3, iters=20)
+            transfer[f"{name}_nrhs{nrhs}"] = {"ms": ms_t, "bytes": by, "gbs": by / ms_t / 1e6}
 
     extra = {}
     if not args.no_extra:
@@ -449,7 +479,7 @@ def run_gpu(args, dist: Dist) -> dict:
     H.load_gauge(U_big)
     H.set_clover(CSW, m0)
     del U_big
-    kern = {}
+    kern = dict(transfer)
     for name, code, prec in [("dslash_clover_fp32", B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32),
                              ("dslash_xpay_fp32", B.MG_KERNEL_DSLASH_XPAY, B.MG_FP32),
                              ("dr_fp32", B.MG_KERNEL_DR, B.MG_FP32),
@@ -911,7 +941,7 @@ def main():
                     help="also solve the 28 batched sources one at a time (about 30 s)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FP16-storage, gradient and multi-RHS D_r measurements")
-    ap.add_argument("--profile", choices=["solve", "block", "block_tc", "dslash", "dslash_mrhs", "coarse"],
+    ap.add_argument("--profile", choices=["solve", "block", "block_tc", "dslash", "dslash_mrhs", "coarse", "transfer"],
                     help="for ncu --profile-from-start off: bracket `steps` solves (after setup and warm-up), "
                          "`steps` block solves of the batched right-hand sides, or `steps` launches of the FP32 fused "
                          "dslash (HBM-size lattice; dslash_mrhs: its multi-RHS form), with cudaProfilerStart/Stop; "

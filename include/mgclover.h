@@ -175,7 +175,9 @@ enum mg_kernel {
   MG_KERNEL_DSLASH_CLOVER = 0,  /* fused hop + clover-inverse epilogue (t_o = A_o^{-1} H_oe s_e) */
   MG_KERNEL_DSLASH_XPAY = 1,    /* fused hop + axpy epilogue (y_e - H_eo t_o)                    */
   MG_KERNEL_DR = 2,             /* a whole D_r application (clover apply + the two kernels above) */
-  MG_KERNEL_COARSE_DR = 3       /* a whole coarse D_hat_r application on level 1 (needs setup)   */
+  MG_KERNEL_COARSE_DR = 3,      /* a whole coarse D_hat_r application on level 1 (needs setup)   */
+  MG_KERNEL_RESTRICT = 4,       /* R = P^dag from the fine even sites to level 1 (needs setup)   */
+  MG_KERNEL_PROLONG = 5         /* P from level 1 onto the fine even sites (needs setup)         */
 };
 
 /* Name of a status code (static string). */
@@ -397,7 +399,12 @@ MG_API int mg_apply_noalloc(void* ctx, int op, void* out, const void* in, int pr
  *   DSLASH_CLOVER: Vh * (8 links * 18 + 24 spinor + 72 clover + 24 out) reals,
  *   DSLASH_XPAY:   Vh * (8 * 18 + 24 + 24 x + 24 out) reals,
  *   DR:            the sum of its three kernels,
- *   COARSE_DR:     Vc/2 * (18 Nc^2 link/inverse entries + 7 Nc vector entries) complex.
+ *   COARSE_DR:     Vc/2 * (18 Nc^2 link/inverse entries + 7 Nc vector entries) complex,
+ *   RESTRICT, PROLONG: the P rows of the even fine sites (Vh * 12 * Nv entries
+ *                  of the storage format: 8 bytes FP32, 4 bytes FP16/BF16) + the
+ *                  even half of the fine vector (24 Vh floats) + the coarse
+ *                  vector (Vc * 2 Nv complex FP32).
+ * The transfers always run in FP32 (`prec` is ignored for them); the other
  * `prec` selects FP64 or FP32 for the fine kernels.  Errors: MG_ERR_ARG,
  * MG_ERR_STATE, MG_ERR_CUDA. */
 MG_API int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int iters, double* avg_ms,
@@ -409,7 +416,8 @@ MG_API int mg_benchmark_kernel(void* ctx, int kernel, int prec, int warmup, int 
  * site and spinors once per (site, rhs):
  *   DSLASH_CLOVER: Vh * (144 + 72 + 48 nrhs) reals,
  *   DSLASH_XPAY:   Vh * (144 + 72 nrhs) reals,
- *   DR:            Vh * (432 + 168 nrhs) reals.
+ *   DR:            Vh * (432 + 168 nrhs) reals,
+ *   RESTRICT, PROLONG: the P rows once + nrhs times both vectors.
  * Errors as mg_benchmark_kernel; MG_KERNEL_COARSE_DR takes nrhs = 1 only. */
 MG_API int mg_benchmark_kernel_nrhs(void* ctx, int kernel, int prec, int nrhs, int warmup, int iters, double* avg_ms,
                                     double* bytes_per_launch);

@@ -34,7 +34,7 @@ MG_MODE_MG, MG_MODE_EO_GCR, MG_MODE_BICGSTAB, MG_MODE_CGNR, MG_MODE_BICGSTAB_MP 
 MG_COARSE_DP, MG_COARSE_D = 0, 1
 MG_FORCE_SU3, MG_FORCE_WIRTINGER = 0, 1
 
-MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_DR = range(4)
+MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_DR, MG_KERNEL_RESTRICT, MG_KERNEL_PROLONG = range(6)
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
             "mg_set_clover", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",

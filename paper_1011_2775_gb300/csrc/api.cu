@@ -766,6 +766,10 @@ int mg_benchmark_kernel_nrhs(void* ctx, int kernel, int prec, int nrhs, int warm
       mg::mg_benchmark_coarse(c, warmup, iters, avg_ms, bytes_per_launch);
       return MG_OK;
     }
+    if (kernel == MG_KERNEL_RESTRICT || kernel == MG_KERNEL_PROLONG) {
+      mg::mg_benchmark_transfer(c, kernel == MG_KERNEL_RESTRICT, nrhs, warmup, iters, avg_ms, bytes_per_launch);
+      return MG_OK;
+    }
     if (kernel < MG_KERNEL_DSLASH_CLOVER || kernel > MG_KERNEL_DR) mg::raise(MG_ERR_ARG, "bad kernel");
     const bool f32 = prec == MG_FP32;
     const size_t half_reals = 24 * c->Vh;

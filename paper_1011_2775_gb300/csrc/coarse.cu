@@ -22,6 +22,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "async_copy.cuh"
 #include "coarse.h"
 #include "coarse_dev.cuh"
 #include "philox.cuh"
@@ -78,12 +79,14 @@ __device__ __forceinline__ void sput(void* p, size_t e, cx<float> z) {
 }
 
 struct TArgs {
-  int nv, ndof, nb, fine_half;
+  int nv, ndof, nb, fine_half, nbe;
   int b[4], cd[4];
   FineAccess fa;
   const int* blockmap;
+  const int* evenlist;
   const void* P;
   const float* Ps;
+  int* flags;
 };
 
 TArgs targs(const TransferOp& T) {
@@ -97,9 +100,12 @@ TArgs targs(const TransferOp& T) {
     a.cd[m] = T.cdims[m];
   }
   a.fa = T.fa;
+  a.nbe = T.nbe;
   a.blockmap = T.blockmap.as<int>();
+  a.evenlist = T.evenlist.as<int>();
   a.P = T.P.get();
   a.Ps = T.Pscale.as<float>();
+  a.flags = T.flags;
   return a;
 }
 
@@ -170,9 +176,212 @@ __global__ void __launch_bounds__(256) k_restrict(TArgs a, float* __restrict__ o
   }
 }
 
+// Fine-level (Wilson) transfers.  One CTA per (coarse site, chirality, group
+// of NR right-hand sides) walks the block's selected fine sites (all, or the
+// even ones from the block's list) in tiles of kFTile sites through a
+// kFStages-deep shared-memory pipeline.  A producer warp fills a stage --
+// per site its P rows of the chirality, 6 Nv contiguous elements, with one
+// bulk asynchronous copy each, and for the restriction the chirality's three
+// float4 chunks of each right-hand side with 16-byte cp.async copies spread
+// over its lanes (many tiny bulk copies would queue on the copy engine) --
+// completed on the stage's "full" mbarrier; the consumer warps compute from
+// the stage and release it on its "empty" mbarrier.  The bytes in flight per SM are set by the shared-memory budget
+// (2-3 stages of each resident CTA), not by registers.  Every wait is bounded;
+// a wait that runs out raises FLAG_TIMEOUT and the kernel carries on without
+// it (every address stays in bounds), so the launch always ends.
+constexpr int kFTile = 8;
+constexpr int kFStages = 3;
+constexpr int kFineMaxSites = 512;   // selected fine sites per block (indices kept in shared memory)
+
+template <int ST>
+__host__ __device__ constexpr int fine_esz() {
+  return ST == STORE_F32 ? 8 : 4;
+}
+
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+bool fine_transfer_ok(const TransferOp& T, bool even_only, const void* fine, size_t fstride, const void* coarse,
+                      size_t cstride) {
+  return T.fa.wilson && T.nv <= 32 && T.nv % 2 == 0 && T.nb <= kFineMaxSites && (!even_only || T.nbe > 0) &&
+         reinterpret_cast<uintptr_t>(fine) % 16 == 0 && reinterpret_cast<uintptr_t>(coarse) % 16 == 0 &&
+         fstride % 4 == 0 && cstride % 4 == 0;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// an arrival on bar once all of the calling thread's earlier cp.async copies
+// have landed (the barrier's expected count includes this arrival)
+__device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Restriction.  Consumer warp w takes the tile's sites w, w + 4; lane k < Nv
+// accumulates conj(P[site][d][k]) x[site][d] (P from consecutive addresses, x
+// as a broadcast).  The four warp sums are added in a fixed order.
+constexpr int kRCons = 4;
+
+template <int ST, int NR>
+struct RestrictSmem {
+  static constexpr int esz = fine_esz<ST>();
+  int rowb, xoff, stb;
+  size_t sacc, stage0, idx, total;
+  __host__ __device__ RestrictSmem(int nv, int nsel) {
+    rowb = 6 * nv * esz;
+    xoff = kFTile * rowb;
+    stb = xoff + kFTile * NR * 48;
+    sacc = align16(sizeof(uint64_t) * 2 * kFStages);
+    stage0 = align16(sacc + sizeof(float2) * kRCons * NR * 32);
+    idx = stage0 + (size_t)kFStages * stb;
+    total = idx + sizeof(int) * 2 * nsel;
+  }
+};
+
+template <int ST, int NR>
+__global__ void __launch_bounds__((kRCons + 1) * 32) k_restrict_fine(TArgs a, float* __restrict__ out,
+                                                                     const float* __restrict__ v, int even_only,
+                                                                     int nrhs, size_t vstride, size_t cstride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int esz = fine_esz<ST>();
+  const int nv = a.nv, Vh = a.fa.Vh;
+  const int nsel = even_only ? a.nbe : a.nb;
+  const RestrictSmem<ST, NR> L(nv, nsel);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + kFStages;
+  float2* sacc = reinterpret_cast<float2*>(smem_raw + L.sacc);   // [kRCons][NR][32]
+  unsigned char* stage0 = smem_raw + L.stage0;
+  int* si = reinterpret_cast<int*>(smem_raw + L.idx);            // [nsel] block-local index
+  int* sx = si + nsel;                                           // [nsel] storage index
+  const int nrg = (nrhs + NR - 1) / NR;
+  const int cc = blockIdx.x / (2 * nrg), rem = blockIdx.x % (2 * nrg);
+  const int ch = rem / nrg, r0 = (rem % nrg) * NR;
+  const int nr = min(NR, nrhs - r0);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    for (int st = 0; st < kFStages; st++) {
+      mbar_init(&full[st], 1 + 32);   // lane 0's arrival + every producer lane's cp.async arrival
+      mbar_init(&empty[st], kRCons);
+    }
+    mbar_fence_init();
+  }
+  for (int t = tid; t < nsel; t += blockDim.x) {
+    const int i = even_only ? a.evenlist[cc * a.nbe + t] : t;
+    si[t] = i;
+    sx[t] = a.blockmap[cc * a.nb + i];
+  }
+  __syncthreads();
+  const int ntile = (nsel + kFTile - 1) / kFTile;
+  bool ok = true;
+  if (w == kRCons) {   // producer
+    const unsigned char* Pb = static_cast<const unsigned char*>(a.P);
+    for (int T = 0; T < ntile; T++) {
+      const int st = T % kFStages, use = T / kFStages;
+      if (use > 0) ok &= mbar_wait(&empty[st], (unsigned)((use - 1) & 1));
+      const int s0 = T * kFTile, ns = min(kFTile, nsel - s0);
+      unsigned char* sp = stage0 + (size_t)st * L.stb;
+      if (lane == 0) mbar_expect_tx(&full[st], (unsigned)(ns * L.rowb));
+      __syncwarp();
+      if (lane < ns)
+        bulk_copy_g2s(sp + lane * L.rowb, Pb + (((size_t)(cc * a.nb + si[s0 + lane]) * 12 + 6 * ch) * nv) * esz,
+                      (unsigned)L.rowb, &full[st]);
+      for (int u = lane; u < ns * nr * 3; u += 32) {
+        const int s = u / (nr * 3), rq = u - s * nr * 3, r = rq / 3, q = rq - r * 3;
+        const int idx = sx[s0 + s], par = idx >= Vh, cb = idx - par * Vh;
+        cp_async16(sp + L.xoff + ((s * NR + r) * 3 + q) * 16,
+                   reinterpret_cast<const float4*>(v + (size_t)(r0 + r) * vstride + (size_t)par * 24 * Vh) +
+                       (size_t)(3 * ch + q) * Vh + cb);
+      }
+      cp_async_arrive(&full[st]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[st]);
+    }
+  } else {   // consumers
+    float acc[NR][2];
+#pragma unroll
+    for (int r = 0; r < NR; r++) acc[r][0] = acc[r][1] = 0.f;
+    for (int T = 0; T < ntile; T++) {
+      const int st = T % kFStages, use = T / kFStages;
+      ok &= mbar_wait(&full[st], (unsigned)(use & 1));
+      const unsigned char* sp = stage0 + (size_t)st * L.stb;
+      const float4* xs = reinterpret_cast<const float4*>(sp + L.xoff);
+      const int ns = min(kFTile, nsel - T * kFTile);
+      if (lane < nv) {
+        for (int s = w; s < ns; s += kRCons) {
+          const void* prow = sp + s * L.rowb;
+#pragma unroll
+          for (int d = 0; d < 6; d++) {
+            const cx<float> p = sget<ST>(prow, (size_t)d * nv + lane);
+#pragma unroll
+            for (int r = 0; r < NR; r++) {
+              if (r < nr) {
+                const float4 c4 = xs[(s * NR + r) * 3 + (d >> 1)];
+                const float xr = (d & 1) ? c4.z : c4.x, xi = (d & 1) ? c4.w : c4.y;
+                acc[r][0] = fmaf(p.re, xr, fmaf(p.im, xi, acc[r][0]));
+                acc[r][1] = fmaf(p.re, xi, fmaf(-p.im, xr, acc[r][1]));
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);
+    }
+#pragma unroll
+    for (int r = 0; r < NR; r++) sacc[(w * NR + r) * 32 + lane] = make_float2(acc[r][0], acc[r][1]);
+    consumer_sync(kRCons * 32);
+    const float sc = a.Ps[cc * 2 + ch];
+    for (int t = tid; t < nr * nv; t += kRCons * 32) {
+      const int r = t / nv, k = t - r * nv;
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int q = 0; q < kRCons; q++) {
+        re += sacc[(q * NR + r) * 32 + k].x;
+        im += sacc[(q * NR + r) * 32 + k].y;
+      }
+      reinterpret_cast<float2*>(out + (size_t)(r0 + r) * cstride)[(size_t)cc * 2 * nv + ch * nv + k] =
+          make_float2(sc * re, sc * im);
+    }
+  }
+  if (!ok && a.flags) atomicExch(&a.flags[FLAG_TIMEOUT], 1);
+}
+
+template <int ST, int NR>
+void launch_restrict_fine(const TArgs& a, int ncoarse, int nrhs, float* out, const float* v, bool even_only,
+                          size_t vstride, size_t cstride, cudaStream_t s) {
+  const unsigned grid = (unsigned)((size_t)ncoarse * 2 * ((nrhs + NR - 1) / NR));
+  const RestrictSmem<ST, NR> L(a.nv, even_only ? a.nbe : a.nb);
+  MG_CUDA(cudaFuncSetAttribute(k_restrict_fine<ST, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  k_restrict_fine<ST, NR><<<grid, (kRCons + 1) * 32, L.total, s>>>(a, out, v, even_only, nrhs, vstride, cstride);
+  MG_LAUNCH();
+}
+
+template <int ST>
+void restrict_fine(const TArgs& a, int ncoarse, int nrhs, float* out, const float* v, bool even_only,
+                   size_t vstride, size_t cstride, cudaStream_t s) {
+  if (nrhs >= 4)
+    launch_restrict_fine<ST, 4>(a, ncoarse, nrhs, out, v, even_only, vstride, cstride, s);
+  else if (nrhs >= 2)
+    launch_restrict_fine<ST, 2>(a, ncoarse, nrhs, out, v, even_only, vstride, cstride, s);
+  else
+    launch_restrict_fine<ST, 1>(a, ncoarse, nrhs, out, v, even_only, vstride, cstride, s);
+}
+
 void restrict_vec_multi(const TransferOp& T, int nrhs, float* out_c, size_t cstride, const float* v, size_t vstride,
                         bool even_only, cudaStream_t s) {
   TArgs a = targs(T);
+  if (fine_transfer_ok(T, even_only, v, vstride, out_c, cstride)) {
+    switch (T.store) {
+      case STORE_F32: restrict_fine<STORE_F32>(a, T.ncoarse, nrhs, out_c, v, even_only, vstride, cstride, s); break;
+      case STORE_F16: restrict_fine<STORE_F16>(a, T.ncoarse, nrhs, out_c, v, even_only, vstride, cstride, s); break;
+      default: restrict_fine<STORE_BF16>(a, T.ncoarse, nrhs, out_c, v, even_only, vstride, cstride, s); break;
+    }
+    return;
+  }
   const size_t sm = sizeof(float2) * (kBS / 32) * 2 * (size_t)T.nv;
   const unsigned grid = (unsigned)((size_t)T.ncoarse * nrhs);
   switch (T.store) {
@@ -218,9 +427,194 @@ __global__ void k_prolong(TArgs a, float* __restrict__ v, const float* __restric
   }
 }
 
+// Prolongation onto the fine (Wilson) level, with the pipeline of the
+// restriction (one CTA per (coarse site, chirality, group of NR right-hand
+// sides)); the producer also copies the coarse vectors of the chirality once.
+// Consumer warp w forms the float4 chunk 3 ch + w (spin-colour components
+// 6 ch + 2w, +1) of the tile's sites: lane = site (lane & 7) + 8 g, the four
+// g lanes of a site taking its NR right-hand sides, each split over 4 / NR
+// lanes that share the Nv/2 pairs of null vectors and add their sums with
+// shuffles; one lane per (site, right-hand side) stores the chunk with one
+// 16-byte store.  A staged site occupies an odd
+// number of 16-byte units, so the eight sites of a quarter-warp read
+// different banks; the coarse vector is read as a broadcast.
+constexpr int kPCons = 3;
+
+template <int ST, int NR>
+struct ProlongSmem {
+  static constexpr int esz = fine_esz<ST>();
+  int rowb, pitch, stb;
+  size_t svc, stage0, idx, total;
+  __host__ __device__ ProlongSmem(int nv, int nsel) {
+    rowb = 6 * nv * esz;
+    pitch = 16 * ((rowb / 16) | 1);
+    stb = kFTile * pitch;
+    svc = align16(sizeof(uint64_t) * (2 * kFStages + 1));
+    stage0 = align16(svc + sizeof(float2) * NR * nv);
+    idx = stage0 + (size_t)kFStages * stb;
+    total = idx + sizeof(int) * 2 * nsel;
+  }
+};
+
+template <int ST, int NR>
+__global__ void __launch_bounds__((kPCons + 1) * 32) k_prolong_fine(TArgs a, float* __restrict__ v,
+                                                                    const float* __restrict__ in_c, int even_only,
+                                                                    int nrhs, size_t vstride, size_t cstride) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int esz = fine_esz<ST>();
+  const int nv = a.nv, Vh = a.fa.Vh;
+  const int nsel = even_only ? a.nbe : a.nb;
+  const ProlongSmem<ST, NR> L(nv, nsel);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+  uint64_t* empty = full + kFStages;
+  uint64_t* cbar = empty + kFStages;
+  const float2* svc = reinterpret_cast<const float2*>(smem_raw + L.svc);   // [NR][nv]
+  unsigned char* stage0 = smem_raw + L.stage0;
+  int* si = reinterpret_cast<int*>(smem_raw + L.idx);
+  int* sx = si + nsel;
+  const int nrg = (nrhs + NR - 1) / NR;
+  const int cc = blockIdx.x / (2 * nrg), rem = blockIdx.x % (2 * nrg);
+  const int ch = rem / nrg, r0 = (rem % nrg) * NR;
+  const int nr = min(NR, nrhs - r0);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  if (tid == 0) {
+    for (int st = 0; st < kFStages; st++) {
+      mbar_init(&full[st], 1);
+      mbar_init(&empty[st], kPCons);
+    }
+    mbar_init(cbar, 1);
+    mbar_fence_init();
+  }
+  for (int t = tid; t < nsel; t += blockDim.x) {
+    const int i = even_only ? a.evenlist[cc * a.nbe + t] : t;
+    si[t] = i;
+    sx[t] = a.blockmap[cc * a.nb + i];
+  }
+  __syncthreads();
+  const int ntile = (nsel + kFTile - 1) / kFTile;
+  bool ok = true;
+  if (w == kPCons) {   // producer
+    if (lane == 0) mbar_expect_tx(cbar, (unsigned)(nr * nv * 8));
+    __syncwarp();
+    if (lane < nr)
+      bulk_copy_g2s(smem_raw + L.svc + (size_t)lane * nv * 8,
+                    in_c + (size_t)(r0 + lane) * cstride + ((size_t)cc * 2 * nv + ch * nv) * 2, (unsigned)(nv * 8),
+                    cbar);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(cbar);
+    const unsigned char* Pb = static_cast<const unsigned char*>(a.P);
+    for (int T = 0; T < ntile; T++) {
+      const int st = T % kFStages, use = T / kFStages;
+      if (use > 0) ok &= mbar_wait(&empty[st], (unsigned)((use - 1) & 1));
+      const int s0 = T * kFTile, ns = min(kFTile, nsel - s0);
+      if (lane == 0) mbar_expect_tx(&full[st], (unsigned)(ns * L.rowb));
+      __syncwarp();
+      if (lane < ns)
+        bulk_copy_g2s(stage0 + (size_t)st * L.stb + lane * L.pitch,
+                      Pb + (((size_t)(cc * a.nb + si[s0 + lane]) * 12 + 6 * ch) * nv) * esz, (unsigned)L.rowb,
+                      &full[st]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[st]);
+    }
+  } else {   // consumers
+    ok &= mbar_wait(cbar, 0u);
+    constexpr int KQ = 4 / NR;   // lanes sharing the pairs of one (site, right-hand side)
+    const int s = lane & 7, g = lane >> 3, rq = g / KQ, kq = g % KQ;
+    const int npair = nv / 2;
+    const float4* c2p = reinterpret_cast<const float4*>(svc + rq * nv);
+    for (int T = 0; T < ntile; T++) {
+      const int st = T % kFStages, use = T / kFStages;
+      ok &= mbar_wait(&full[st], (unsigned)(use & 1));
+      const int s0 = T * kFTile, ns = min(kFTile, nsel - s0);
+      const unsigned char* row0 = stage0 + (size_t)st * L.stb + s * L.pitch + 2 * w * nv * esz;
+      const unsigned char* row1 = row0 + nv * esz;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      if (s < ns && rq < nr) {
+        for (int kp = kq; kp < npair; kp += KQ) {
+          float2 p0[2], p1[2];
+          if (ST == STORE_F32) {
+            const float4 u0 = reinterpret_cast<const float4*>(row0)[kp];
+            const float4 u1 = reinterpret_cast<const float4*>(row1)[kp];
+            p0[0] = make_float2(u0.x, u0.y);
+            p0[1] = make_float2(u0.z, u0.w);
+            p1[0] = make_float2(u1.x, u1.y);
+            p1[1] = make_float2(u1.z, u1.w);
+          } else {
+            const uint2 u0 = reinterpret_cast<const uint2*>(row0)[kp];
+            const uint2 u1 = reinterpret_cast<const uint2*>(row1)[kp];
+            if (ST == STORE_F16) {
+              p0[0] = __half22float2(*reinterpret_cast<const __half2*>(&u0.x));
+              p0[1] = __half22float2(*reinterpret_cast<const __half2*>(&u0.y));
+              p1[0] = __half22float2(*reinterpret_cast<const __half2*>(&u1.x));
+              p1[1] = __half22float2(*reinterpret_cast<const __half2*>(&u1.y));
+            } else {
+              p0[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u0.x));
+              p0[1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u0.y));
+              p1[0] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u1.x));
+              p1[1] = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u1.y));
+            }
+          }
+          const float4 c2 = c2p[kp];
+#pragma unroll
+          for (int h = 0; h < 2; h++) {
+            const float cr = h ? c2.z : c2.x, ci = h ? c2.w : c2.y;
+            acc[0] = fmaf(p0[h].x, cr, fmaf(-p0[h].y, ci, acc[0]));
+            acc[1] = fmaf(p0[h].x, ci, fmaf(p0[h].y, cr, acc[1]));
+            acc[2] = fmaf(p1[h].x, cr, fmaf(-p1[h].y, ci, acc[2]));
+            acc[3] = fmaf(p1[h].x, ci, fmaf(p1[h].y, cr, acc[3]));
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[st]);   // the stage is read; what follows uses registers
+#pragma unroll
+      for (int o = 8; o < 8 * KQ; o <<= 1)
+#pragma unroll
+        for (int e = 0; e < 4; e++) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+      if (s < ns && rq < nr && kq == 0) {
+        const float sc = a.Ps[cc * 2 + ch];
+        const int idx = sx[s0 + s], par = idx >= Vh, cb = idx - par * Vh;
+        reinterpret_cast<float4*>(v + (size_t)(r0 + rq) * vstride + (size_t)par * 24 * Vh)[(size_t)(3 * ch + w) * Vh +
+                                                                                           cb] =
+            make_float4(sc * acc[0], sc * acc[1], sc * acc[2], sc * acc[3]);
+      }
+    }
+  }
+  if (!ok && a.flags) atomicExch(&a.flags[FLAG_TIMEOUT], 1);
+}
+
+template <int ST, int NR>
+void launch_prolong_fine(const TArgs& a, const TransferOp& T, int nrhs, float* v, const float* in_c, bool even_only,
+                         size_t vstride, size_t cstride, cudaStream_t s) {
+  const unsigned grid = (unsigned)((size_t)T.ncoarse * 2 * ((nrhs + NR - 1) / NR));
+  const ProlongSmem<ST, NR> L(T.nv, even_only ? T.nbe : T.nb);
+  MG_CUDA(cudaFuncSetAttribute(k_prolong_fine<ST, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total));
+  k_prolong_fine<ST, NR><<<grid, (kPCons + 1) * 32, L.total, s>>>(a, v, in_c, even_only, nrhs, vstride, cstride);
+  MG_LAUNCH();
+}
+
+template <int ST>
+void prolong_fine(const TArgs& a, const TransferOp& T, int nrhs, float* v, const float* in_c, bool even_only,
+                  size_t vstride, size_t cstride, cudaStream_t s) {
+  if (nrhs >= 4)
+    launch_prolong_fine<ST, 4>(a, T, nrhs, v, in_c, even_only, vstride, cstride, s);
+  else if (nrhs >= 2)
+    launch_prolong_fine<ST, 2>(a, T, nrhs, v, in_c, even_only, vstride, cstride, s);
+  else
+    launch_prolong_fine<ST, 1>(a, T, nrhs, v, in_c, even_only, vstride, cstride, s);
+}
+
 void prolong_vec_multi(const TransferOp& T, int nrhs, float* v, size_t vstride, const float* in_c, size_t cstride,
                        bool even_only, cudaStream_t s) {
   TArgs a = targs(T);
+  if (fine_transfer_ok(T, even_only, v, vstride, in_c, cstride)) {
+    switch (T.store) {
+      case STORE_F32: prolong_fine<STORE_F32>(a, T, nrhs, v, in_c, even_only, vstride, cstride, s); break;
+      case STORE_F16: prolong_fine<STORE_F16>(a, T, nrhs, v, in_c, even_only, vstride, cstride, s); break;
+      default: prolong_fine<STORE_BF16>(a, T, nrhs, v, in_c, even_only, vstride, cstride, s); break;
+    }
+    return;
+  }
   const size_t sm = sizeof(float2) * 2 * T.nv;
   const unsigned grid = (unsigned)((size_t)T.ncoarse * nrhs);
   switch (T.store) {

@@ -57,6 +57,12 @@ struct TransferOp {
   int store = STORE_F32;
   FineAccess fa{};
   DBuf blockmap;           // int[ncoarse][nb] fine storage index
+  // The block-local indices of each block's even fine sites, in order
+  // (int[ncoarse][nbe]); nbe = -1 when blocks differ in their number of even
+  // sites, and the transfers restricted to even sites then scan the whole block.
+  DBuf evenlist;
+  int nbe = -1;
+  int* flags = nullptr;    // the context's error flags (FLAG_TIMEOUT from the pipelined transfers)
   DBuf P;                  // [ncoarse][nb][fine_ndof][nv] in `store` format
   DBuf Pscale;             // float[ncoarse][2]: per (block, chirality) scale (1 for FP32)
 };

@@ -412,6 +412,9 @@ void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* 
 void mg_read_counters(Ctx* c, long long* coarse_iters);
 // measured CUDA-core FMA throughput of the current GPU (peaks.cu), TFLOP/s
 double fma_peak_tflops(int prec);
+// times the level-0 restriction (restrict = true) or prolongation on the even
+// sites for nrhs right-hand sides (see mg_benchmark_kernel_nrhs)
+void mg_benchmark_transfer(Ctx* c, bool restrict, int nrhs, int warmup, int iters, double* avg_ms, double* bytes);
 // times `iters` coarsest-level solves (see mg_benchmark_coarse_solve)
 void mg_benchmark_coarse_solve(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes, double* its);
 

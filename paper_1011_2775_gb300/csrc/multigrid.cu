@@ -551,6 +551,7 @@ void mg_build(Ctx* c, mg_setup_info* info) {
     T.fine_half = l == 0 ? G.Vh : (G.eo ? G.half : G.nsites);
     T.store = (p.storage == MG_STORE_FP16) ? STORE_F16 : (p.storage == MG_STORE_BF16 ? STORE_BF16 : STORE_F32);
     T.fa.wilson = l == 0;
+    T.flags = c->ws.flags.as<int>();
     T.fa.Vh = G.Vh;
     T.fa.ndof = G.ndof;
     // block map: coarse storage index -> fine storage indices of its block (bx fastest)
@@ -574,6 +575,25 @@ void mg_build(Ctx* c, mg_setup_info* info) {
     }
     T.blockmap.alloc(sizeof(int) * bm.size());
     MG_CUDA(cudaMemcpy(T.blockmap.get(), bm.data(), sizeof(int) * bm.size(), cudaMemcpyHostToDevice));
+    std::vector<int> el;
+    T.nbe = -1;
+    for (int cs = 0; cs < Gc.nsites; cs++) {
+      int n = 0;
+      for (int i = 0; i < T.nb; i++)
+        if (bm[(size_t)cs * T.nb + i] < T.fine_half) {
+          el.push_back(i);
+          n++;
+        }
+      if (cs == 0) T.nbe = n;
+      if (n != T.nbe || n == 0) {
+        T.nbe = -1;
+        break;
+      }
+    }
+    if (T.nbe > 0) {
+      T.evenlist.alloc(sizeof(int) * el.size());
+      MG_CUDA(cudaMemcpy(T.evenlist.get(), el.data(), sizeof(int) * el.size(), cudaMemcpyHostToDevice));
+    }
     const size_t esz = T.store == STORE_F32 ? sizeof(float2) : 4;
     T.P.alloc(esz * (size_t)T.ncoarse * T.nb * T.fine_ndof * T.nv);
     T.Pscale.alloc(sizeof(float) * 2 * (size_t)T.ncoarse);
@@ -834,6 +854,43 @@ void mg_benchmark_coarse(Ctx* c, int warmup, int iters, double* avg_ms, double* 
   *avg_ms = t / iters;
   const double nc = H.cop[1].nc;
   *bytes = (double)G.half * (18.0 * nc * nc + 7.0 * nc) * sizeof(float2);
+}
+
+void mg_benchmark_transfer(Ctx* c, bool restrict, int nrhs, int warmup, int iters, double* avg_ms, double* bytes) {
+  if (!c->mg || c->mg->L < 2) raise(MG_ERR_STATE, "multigrid not set up");
+  Hierarchy& H = *c->mg;
+  const TransferOp& T = H.tr[0];
+  const size_t fn = (size_t)48 * c->Vh, cn = (size_t)2 * 2 * T.nv * T.ncoarse;
+  DBuf fb(sizeof(float) * fn * nrhs), cb(sizeof(float) * cn * nrhs);
+  for (int q = 0; q < nrhs; q++) {
+    float* f = fb.as<float>() + q * fn;
+    philox_fine_vector(c->g, 4242, 0, q, f, f + fn / 2, c->stream);
+    philox_coarse_vector(H.geo[1], 4243, 1, q, cb.as<float>() + q * cn, c->stream);
+  }
+  auto once = [&]() {
+    if (restrict)
+      restrict_vec_multi(T, nrhs, cb.as<float>(), cn, fb.as<float>(), fn, true, c->stream);
+    else
+      prolong_vec_multi(T, nrhs, fb.as<float>(), fn, cb.as<float>(), cn, true, c->stream);
+  };
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  for (int w = 0; w < warmup; w++) once();
+  MG_CUDA(cudaEventRecord(e0, c->stream));
+  for (int it = 0; it < iters; it++) once();
+  MG_CUDA(cudaEventRecord(e1, c->stream));
+  MG_CUDA(cudaEventSynchronize(e1));
+  float t = 0;
+  MG_CUDA(cudaEventElapsedTime(&t, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *avg_ms = t / iters;
+  // P rows of the even sites once, the even half of each fine vector and each
+  // coarse vector once
+  const double esz = T.store == STORE_F32 ? 8.0 : 4.0;
+  const double neven = T.nbe > 0 ? (double)T.nbe * T.ncoarse : (double)c->Vh;
+  *bytes = neven * 12.0 * T.nv * esz + nrhs * ((double)c->Vh * 24 * sizeof(float) + (double)cn * sizeof(float));
 }
 
 void mg_benchmark_coarse_solve(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes, double* its) {
