@@ -442,6 +442,13 @@ def run_gpu(args, dist: Dist) -> dict:
     S.set_params(tol_coarse=keep[0], maxit_coarse=keep[1])
     coarse = {"ms": c_ms, "bytes": c_bytes, "gcr_iterations": c_its, "avg_iterations_in_step": per_solve,
               "share_of_step": c_ms * last.outer_iterations / ms}
+    # its floors on the same grid: one grid barrier, and one iteration's link
+    # stream L2 -> shared memory without arithmetic (three barriers + one stream
+    # per GCR iteration)
+    f_bar, f_stream, f_bytes, f_grid = B.mg_benchmark_coarse_floor(S.ctx)
+    coarse["floor"] = {"grid": f_grid, "barrier_us": f_bar, "link_stream_us": f_stream, "link_bytes": f_bytes,
+                       "link_stream_gbs": f_bytes / f_stream / 1e3, "iteration_floor_us": 3 * f_bar + f_stream,
+                       "iteration_us": 1e3 * c_ms / max(1.0, c_its)}
     # the level-0 restriction and prolongation on the even sites (back-to-back
     # launches; P of the even sites, 151 MB in FP32, exceeds the L2)
     transfer = {}
@@ -553,13 +560,14 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     e_d = torch.from_numpy(eta).to(f"cuda:{dev}")
     p_d = torch.zeros_like(e_d)
     alt = {}
-    for name, kw in (("tol_0.3", dict(tol_coarse=ALT_COARSE_TOL)), ("single_system_kernel", dict(coarse_impl=1))):
+    for name, kw in (("tol_0.3", dict(tol_coarse=ALT_COARSE_TOL)), ("single_system_kernel", dict(coarse_impl=1)),
+                     ("outer_fp64_products", dict(outer_prec=B.MG_FP64))):
         S.set_params(**kw)
         S.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
         t_p, (_, qi) = timed(lambda: S.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
         alt[name] = {"ms": t_p, "outer_iterations": qi.outer_iterations, "coarse_iterations": qi.coarse_iterations[1],
                      "true_residual": qi.true_residual}
-        S.set_params(tol_coarse=MG["tol_coarse"], coarse_impl=0)
+        S.set_params(tol_coarse=MG["tol_coarse"], coarse_impl=0, outer_prec=B.MG_FP32)
     out["coarse_tolerance"] = alt
     del e_d, p_d
 
@@ -590,11 +598,13 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     loss = torch.sum(torch.conj(chi_d) * psi).real
     t_bwd, _ = timed(lambda: loss.backward())
     lam = eta_d.grad.detach()
-    t_force, _ = timed(lambda: S.force(lam, psi.detach(), kind=B.MG_FORCE_SU3))
+    t_force, f64 = timed(lambda: S.force(lam, psi.detach(), kind=B.MG_FORCE_SU3))
+    t_force32, f32 = timed(lambda: S.force(lam, psi.detach(), kind=B.MG_FORCE_SU3 | B.MG_FORCE_FP32))
     out["gradient"] = {"forward_ms": t_fwd, "backward_ms": t_bwd, "backward_over_forward": t_bwd / t_fwd,
-                       "force_ms": t_force, "what": "backward = adjoint MG solve through gamma_5 D gamma_5 + "
+                       "force_ms": t_force, "force_fp32_ms": t_force32,
+                       "force_fp32_rel_err": float((f32 - f64).abs().max() / f64.abs().max()), "what": "backward = adjoint MG solve through gamma_5 D gamma_5 + "
                                                    "FP64 hop and clover link derivative"}
-    del eta_d, U_d, chi_d, psi, lam, loss
+    del eta_d, U_d, chi_d, psi, lam, loss, f64, f32
 
     # ---- the 2-level cycle replayed as a CUDA graph (default) against direct launches
     e_g = torch.from_numpy(eta).to(f"cuda:{dev}")
@@ -1004,6 +1014,7 @@ def main():
                         else None),
             "peak_kind": peak_kind, "bytes_per_launch": c["bytes"], "ms_per_launch": c["ms"],
             "gcr_iterations_per_launch": c["gcr_iterations"], "share_of_step": c["share_of_step"],
+            "floor": c["floor"],
             "note": "the 75.5 MB of links per iteration stay in the 129 MB L2; bytes are the links each GCR iteration "
                     "streams (folded odd-site links FP32 + even-site Y), per launch"}
     k = r["kern"]["dslash_clover_fp32"]
@@ -1016,7 +1027,9 @@ def main():
             "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": workload_name(args.mass), "lattice": "16x16x16x32", "m0": args.mass,
                        "mg": "2-level, 4^4 blocks, Nv=24, coarse GCR(64) tol 0.1, nu_post=4 MR",
-                       "precision": "FP64 outer GCR(16), FP32 preconditioner", "l2": "flushed before every solve",
+                       "precision": "FP64 outer GCR(16) (FP64 vectors, orthogonalisation, updates and true residuals; "
+                                    "FP32 D_r products of its directions), FP32 preconditioner",
+                       "l2": "flushed before every solve",
                        "parallelism": f"replicas x{dist.world}"},
             "roofline": roof, "roofline_dslash": roof_dslash,
             "e2e": {"value": r["e2e_ms"], "unit": "ms", "h2d_bytes_per_step": r["nbytes"],

@@ -118,7 +118,9 @@ enum mg_coarse_op { MG_COARSE_DP = 0, MG_COARSE_D = 1 };
 /* Output of mg_force. */
 enum mg_force_kind {
   MG_FORCE_SU3 = 0,        /* su(3) force sum_a F^a T_a (traceless Hermitian), T_a = lambda_a / 2     */
-  MG_FORCE_WIRTINGER = 1   /* unconstrained gradient dL/dRe U + i dL/dIm U of every complex link entry */
+  MG_FORCE_WIRTINGER = 1,  /* unconstrained gradient dL/dRe U + i dL/dIm U of every complex link entry */
+  MG_FORCE_FP32 = 16       /* flag, or-ed with a kind: compute in FP32 (FP32 gauge copy, vectors and  */
+                           /* arithmetic; the result is still written as complex128)                  */
 };
 
 /* Multigrid parameters (section "Implementation"; section "Setup procedure").
@@ -150,6 +152,11 @@ typedef struct {
                                   /* 4 tensor cores (even-odd levels, FP16 storage, Nc a multiple  */
                                   /* of 8 up to 64; also the batched cycle's solves); an           */
                                   /* implementation that does not apply falls back to 1            */
+  int outer_prec;                 /* MG mode: precision of the outer FGCR's product D_r z inside a */
+                                  /* restart cycle -- MG_FP32 (the FP32 D_r of the FP32 cycle      */
+                                  /* output, widened to FP64 for the FP64 orthogonalisation and    */
+                                  /* update) or MG_FP64; the true residual at every restart and    */
+                                  /* the final check are FP64 either way                           */
 } mg_params;
 
 typedef struct {
@@ -190,7 +197,8 @@ MG_API const char* mg_last_error(void);
 /* Fill `p` with the defaults: 2 levels, 4^4 blocks, Nv = 24, 20 passes of 8
  * GCR iterations, RQ tolerance 0.05, nu_post = 4, coarse tolerance 0.1,
  * coarse restart 32 / cap 50, outer restart 16 / cap 500, FP32 storage,
- * Galerkin projection of D_p, seed 3, rhs_block 16, cuda_graphs 1, coarse_impl 0. */
+ * Galerkin projection of D_p, seed 3, rhs_block 16, cuda_graphs 1, coarse_impl 0,
+ * outer_prec MG_FP32. */
 MG_API int mg_default_params(mg_params* p);
 
 /* Create a context for a lattice of `dims` on CUDA device `device`; kernels
@@ -345,7 +353,8 @@ MG_API int mg_solve_dagger(void* ctx, void* psi, const void* eta, int nrhs, doub
  * derivative of L = Re <chi, D^{-1} eta> with respect to the gauge field --
  * an extension: the paper does not differentiate the solve.  Both the hopping
  * term and the clover term (through its plaquette leaves, with the csw of the
- * last mg_set_clover) are differentiated, in FP64.
+ * last mg_set_clover) are differentiated, in FP64 -- or in FP32 when `kind`
+ * carries the MG_FORCE_FP32 flag (FP32 gauge copy, vectors and arithmetic).
  *   MG_FORCE_SU3:       F_mu(x) = sum_a F^a T_a with F^a = df/d omega^a for
  *                       U_mu(x) -> exp(i omega^a T_a) U_mu(x), T_a = lambda_a/2;
  *   MG_FORCE_WIRTINGER: g_mu(x) with df = Re sum tr(g^dag dU) for any complex
@@ -446,6 +455,20 @@ MG_API int mg_benchmark_fma(int device, int prec, double* tflops);
  * inside the persistent kernel ran out of time). */
 MG_API int mg_benchmark_coarse_solve(void* ctx, int warmup, int iters, double* avg_ms, double* bytes_per_solve,
                                      double* iterations_per_solve);
+
+/* Floors of one coarsest-level GCR iteration (section "Implementation":
+ * unpreconditioned GCR on the coarsest lattice; needs setup and an even-odd
+ * coarsest level), on the grid of the streamed solver (coarse_impl 3), timed
+ * with CUDA events on the context stream: *barrier_us = one time-bounded grid
+ * barrier of a cooperative kernel that does nothing else (3000 in a row; a
+ * GCR iteration passes three), *stream_us = moving the links one iteration
+ * reads -- the folded odd-site links A (FP32) and the even-site Y (storage
+ * format), *stream_bytes in total -- from L2 to shared memory by per-warp
+ * double-buffered bulk copies without arithmetic (20 repetitions), *grid =
+ * the CTAs used.  Errors: MG_ERR_ARG, MG_ERR_STATE (no setup, or no even-odd
+ * coarsest level), MG_ERR_CUDA (also when a bounded wait ran out of time). */
+MG_API int mg_benchmark_coarse_floor(void* ctx, double* barrier_us, double* stream_us, double* stream_bytes,
+                                     int* grid);
 
 /* Lattice size of level `level` after setup (dims_out[4] = {Lx,Ly,Lz,Lt})
  * and its dof per site (12 on the fine level, 2*nv[level-1] on coarse ones). */

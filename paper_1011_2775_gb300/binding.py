@@ -32,7 +32,7 @@ MG_FP64, MG_FP32 = 0, 1
 MG_STORE_FP32, MG_STORE_FP16, MG_STORE_BF16 = 0, 1, 2
 MG_MODE_MG, MG_MODE_EO_GCR, MG_MODE_BICGSTAB, MG_MODE_CGNR, MG_MODE_BICGSTAB_MP = range(5)
 MG_COARSE_DP, MG_COARSE_D = 0, 1
-MG_FORCE_SU3, MG_FORCE_WIRTINGER = 0, 1
+MG_FORCE_SU3, MG_FORCE_WIRTINGER, MG_FORCE_FP32 = 0, 1, 16
 
 MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_DR, MG_KERNEL_RESTRICT, MG_KERNEL_PROLONG = range(6)
 
@@ -40,7 +40,7 @@ EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "m
             "mg_set_clover", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
             "mg_get_coarse_links", "mg_save_setup", "mg_load_setup", "mg_update_mass", "mg_adapt_setup", "mg_solve", "mg_solve_batch",
             "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
-            "mg_benchmark_coarse_solve", "mg_benchmark_fma",
+            "mg_benchmark_coarse_solve", "mg_benchmark_coarse_floor", "mg_benchmark_fma",
             "mg_level_info"]
 
 
@@ -63,7 +63,8 @@ class mg_params(ctypes.Structure):
                 ("seed", ctypes.c_uint64),
                 ("rhs_block", ctypes.c_int),
                 ("cuda_graphs", ctypes.c_int),
-                ("coarse_impl", ctypes.c_int)]
+                ("coarse_impl", ctypes.c_int),
+                ("outer_prec", ctypes.c_int)]
 
 
 class mg_setup_info(ctypes.Structure):
@@ -132,6 +133,8 @@ def lib() -> ctypes.CDLL:
             "mg_apply_noalloc": [vp, ip, vp, vp, ip],
             "mg_benchmark_kernel_nrhs": [vp, ip, ip, ip, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp)],
             "mg_benchmark_coarse_solve": [vp, ip, ip, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp)],
+            "mg_benchmark_coarse_floor": [vp, ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(dp),
+                                          ctypes.POINTER(ip)],
             "mg_benchmark_fma": [ip, ip, ctypes.POINTER(dp)],
             "mg_level_info": [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip)],
         }
@@ -341,6 +344,15 @@ def mg_benchmark_kernel_nrhs(ctx, kernel: int, prec: int = MG_FP32, nrhs: int = 
     _check(lib().mg_benchmark_kernel_nrhs(ctx, int(kernel), int(prec), int(nrhs), int(warmup), int(iters),
                                           ctypes.byref(ms), ctypes.byref(by)), "mg_benchmark_kernel_nrhs")
     return ms.value, by.value
+
+
+def mg_benchmark_coarse_floor(ctx):
+    """Returns ``(barrier_us, stream_us, stream_bytes, grid)``: one grid barrier and one iteration's link
+    stream of the coarsest-level GCR, each timed alone on the streamed solver's grid."""
+    b, st, by, g = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib().mg_benchmark_coarse_floor(ctx, ctypes.byref(b), ctypes.byref(st), ctypes.byref(by), ctypes.byref(g)),
+           "mg_benchmark_coarse_floor")
+    return b.value, st.value, by.value, g.value
 
 
 def mg_benchmark_coarse_solve(ctx, warmup: int = 3, iters: int = 20):

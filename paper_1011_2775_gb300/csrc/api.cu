@@ -187,6 +187,7 @@ int mg_default_params(mg_params* p) {
   p->rhs_block = 16;
   p->cuda_graphs = 1;
   p->coarse_impl = 0;
+  p->outer_prec = MG_FP32;
   return MG_OK;
 }
 
@@ -287,6 +288,7 @@ int mg_set_params(void* ctx, const mg_params* p) {
     if (p->rhs_block < 1 || p->rhs_block > 16) mg::raise(MG_ERR_ARG, "rhs_block must be in [1, 16]");
     if (p->cuda_graphs != 0 && p->cuda_graphs != 1) mg::raise(MG_ERR_ARG, "cuda_graphs must be 0 or 1");
     if (p->coarse_impl < 0 || p->coarse_impl > 4) mg::raise(MG_ERR_ARG, "coarse_impl must be in [0, 4]");
+    if (p->outer_prec != MG_FP32 && p->outer_prec != MG_FP64) mg::raise(MG_ERR_ARG, "outer_prec must be MG_FP32 or MG_FP64");
     int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
     int ndof = 12;
     for (int l = 0; l + 1 < p->levels; l++) {
@@ -344,6 +346,7 @@ int mg_get_params(void* ctx, mg_params* p) {
 }
 
 int mg_setup(void* ctx, mg_setup_info* info) {
+  mg::Range range("mg_setup");
   return guarded([&]() {
     mg::Ctx* c = as_ctx(ctx);
     if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
@@ -489,6 +492,7 @@ int mg_load_setup(void* ctx, const char* path, mg_setup_info* info) {
 }
 
 int mg_adapt_setup(void* ctx, int passes, int relax, int transfers, mg_setup_info* info) {
+  mg::Range range("mg_adapt_setup");
   return guarded([&]() {
     const auto t0 = std::chrono::steady_clock::now();
     mg::Ctx* c = as_ctx(ctx);
@@ -549,6 +553,7 @@ int mg_get_coarse_links(void* ctx, int level, void* Y, void* X, int where) {
 }
 
 int mg_solve(void* ctx, void* psi, const void* eta, int nrhs, double tol, int mode, int where, mg_solve_info* info) {
+  mg::Range range("mg_solve");
   return guarded([&]() { return solve_impl(ctx, psi, eta, nrhs, tol, mode, where, info, false); });
 }
 
@@ -559,6 +564,7 @@ int mg_solve_dagger(void* ctx, void* psi, const void* eta, int nrhs, double tol,
 
 int mg_solve_batch(void* const* ctxs, int nctx, void* const* psi, const void* const* eta, const int* nrhs, double tol,
                    int where, mg_solve_info* infos) {
+  mg::Range range("mg_solve_batch");
   return guarded([&]() {
     const auto t0 = std::chrono::steady_clock::now();
     check_where(where);
@@ -631,7 +637,8 @@ int mg_force(void* ctx, void* F, const void* lambda, const void* psi, int kind, 
     mg::Ctx* c = as_ctx(ctx);
     check_where(where);
     if (!F || !lambda || !psi) mg::raise(MG_ERR_ARG, "null buffer");
-    if (kind != MG_FORCE_SU3 && kind != MG_FORCE_WIRTINGER) mg::raise(MG_ERR_ARG, "bad force kind");
+    const int base = kind & ~MG_FORCE_FP32;
+    if (base != MG_FORCE_SU3 && base != MG_FORCE_WIRTINGER) mg::raise(MG_ERR_ARG, "bad force kind");
     if (!c->have_clover) mg::raise(MG_ERR_STATE, "set the gauge field and clover first");
     const size_t vbytes = sizeof(double) * 24 * c->V, fbytes = sizeof(double) * 72 * c->V;
     Staged sl, sp, so;
@@ -745,6 +752,15 @@ int mg_benchmark_coarse_solve(void* ctx, int warmup, int iters, double* avg_ms, 
     if (!avg_ms || !bytes_per_solve || !iterations_per_solve || iters < 1 || warmup < 0)
       mg::raise(MG_ERR_ARG, "bad benchmark arguments");
     mg::mg_benchmark_coarse_solve(c, warmup, iters, avg_ms, bytes_per_solve, iterations_per_solve);
+    return MG_OK;
+  });
+}
+
+int mg_benchmark_coarse_floor(void* ctx, double* barrier_us, double* stream_us, double* stream_bytes, int* grid) {
+  return guarded([&]() {
+    mg::Ctx* c = as_ctx(ctx);
+    if (!barrier_us || !stream_us || !stream_bytes || !grid) mg::raise(MG_ERR_ARG, "bad benchmark arguments");
+    mg::mg_benchmark_coarse_floor(c, barrier_us, stream_us, stream_bytes, grid);
     return MG_OK;
   });
 }

@@ -27,11 +27,12 @@ namespace {
 struct BlockBuffers {
   int nb = 0, m = 0;
   DBuf be, bo, y, br, r, tmp, xe, xo, te, to;   // FP64, nb half vectors each
-  DBuf r32;                                     // FP32, nb half vectors
+  DBuf r32, w32;                                // FP32, nb half vectors
   std::vector<DBuf> W, Z;                       // W[k] FP64, Z[k] FP32: nb half vectors each
   DBuf scal;                                    // per rhs: beta[2 m m], alpha[2 m], gam[m], c[2 m], orth[4]
   DBuf rn2;                                     // per rhs: two norms
   std::unique_ptr<FineOps<double>> F64;
+  std::unique_ptr<FineOps<float>> F32;
   size_t per_rhs() const { return 2 * (size_t)m * m + 5 * (size_t)m + 8; }
 };
 
@@ -79,6 +80,7 @@ void prepare(Run& R, double tol) {
     for (DBuf* d : {&Bp->be, &Bp->bo, &Bp->y, &Bp->br, &Bp->r, &Bp->tmp, &Bp->xe, &Bp->xo, &Bp->te, &Bp->to})
       d->alloc(sizeof(double) * R.hs * R.nb);
     Bp->r32.alloc(sizeof(float) * R.hs * R.nb);
+    Bp->w32.alloc(sizeof(float) * R.hs * R.nb);
     Bp->W.resize(R.m);
     Bp->Z.resize(R.m);
     for (int k = 0; k < R.m; k++) {
@@ -88,6 +90,7 @@ void prepare(Run& R, double tol) {
     Bp->scal.alloc(sizeof(double) * Bp->per_rhs() * R.nb);
     Bp->rn2.alloc(sizeof(double) * 2 * R.nb);
     Bp->F64.reset(new FineOps<double>(c));
+    Bp->F32.reset(new FineOps<float>(c));
   }
   R.B = Bp;
   const int nb = R.nb;
@@ -259,8 +262,13 @@ int solve_runs(std::vector<Run>& runs, double tol) {
           double* wk = B.W[k].as<double>();
           double* tmp = B.tmp.as<double>();
           double* r = B.r.as<double>();
-          blas_convert<float, double>(tmp, B.Z[k].as<float>(), R.n * R.nb, c->stream);
-          B.F64->Dr_multi(wk, tmp, R.nb, R.hs);
+          if (c->params.outer_prec == MG_FP32) {   // the directions' product in FP32, true residuals FP64
+            B.F32->Dr_multi(B.w32.as<float>(), B.Z[k].as<float>(), R.nb, R.hs);
+            blas_convert<float, double>(wk, B.w32.as<float>(), R.n * R.nb, c->stream);
+          } else {
+            blas_convert<float, double>(tmp, B.Z[k].as<float>(), R.n * R.nb, c->stream);
+            B.F64->Dr_multi(wk, tmp, R.nb, R.hs);
+          }
           for (int q = 0; q < R.nb; q++) {
             if (!R.run[q]) continue;
             for (int j = 0; j < k; j++) Wp[j] = B.W[j].as<double>() + q * R.hs;

@@ -147,6 +147,11 @@ void coarse_gcr_solve(const LevelGeom& G, const CoarseOp& C, const CoarseGCRBuff
 // launch, one of coarse_gcr_stream_grids().  Raises FLAG_TIMEOUT if a wait
 // runs out of time.
 bool coarse_gcr_stream_ok(const LevelGeom& G, const CoarseOp& C);
+// floors of one coarsest-level GCR iteration on `grid` CTAs: the time of one
+// grid barrier and of streaming the iteration's links (A and the even-site Y)
+// L2 -> shared memory without arithmetic (floor.cu)
+void coarse_floor(const LevelGeom& G, const CoarseOp& C, int grid, int* flags, cudaStream_t s, double* barrier_us,
+                  double* stream_us, double* stream_bytes);
 std::vector<int> coarse_gcr_stream_grids(const LevelGeom& G, const CoarseOp& C);
 void coarse_gcr_stream_solve(const LevelGeom& G, const CoarseOp& C, CoarseGCRBuffers& B, int m, int maxit,
                              double tol_rel, const float* b, float* x, long long* d_iters, int* flags, cudaStream_t s,

@@ -20,8 +20,10 @@
 // every corner inserted where that corner's leaf begins.
 //
 // Two kernels: k_force_insertion writes W_{mu nu}(x) for the six planes of
-// every site (FP64, [parity][plane][9][Vh]); k_force_links computes K (or the
-// force) of every link and writes it in the ABI gauge layout.
+// every site ([parity][plane][9][Vh]); k_force_links computes K (or the
+// force) of every link and writes it in the ABI gauge layout (complex128).
+// Both run in FP64 or, on request, in FP32 (FP32 gauge copy, vectors and W,
+// FP32 arithmetic; the result is widened to complex128 on output).
 #include <cstring>
 
 #include "internal.h"
@@ -31,9 +33,31 @@ namespace mg {
 void set_last_error(const std::string& what);
 
 namespace {
-typedef cx<double> cd;
+template <typename T>
+struct V2of;
+template <>
+struct V2of<double> {
+  typedef double2 type;
+};
+template <>
+struct V2of<float> {
+  typedef float2 type;
+};
 
-__device__ __forceinline__ void m_mul(const cd a[9], const cd b[9], cd c[9]) {
+template <typename T>
+__device__ __forceinline__ typename V2of<T>::type mk2(T x, T y);
+template <>
+__device__ __forceinline__ double2 mk2<double>(double x, double y) {
+  return make_double2(x, y);
+}
+template <>
+__device__ __forceinline__ float2 mk2<float>(float x, float y) {
+  return make_float2(x, y);
+}
+
+template <typename T>
+__device__ __forceinline__ void m_mul(const cx<T> a[9], const cx<T> b[9], cx<T> c[9]) {
+  typedef cx<T> cd;
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -44,7 +68,9 @@ __device__ __forceinline__ void m_mul(const cd a[9], const cd b[9], cd c[9]) {
       c[i * 3 + j] = s;
     }
 }
-__device__ __forceinline__ void m_mul_acc(const cd a[9], const cd b[9], cd c[9]) {
+template <typename T>
+__device__ __forceinline__ void m_mul_acc(const cx<T> a[9], const cx<T> b[9], cx<T> c[9]) {
+  typedef cx<T> cd;
 #pragma unroll
   for (int i = 0; i < 3; i++)
 #pragma unroll
@@ -56,7 +82,9 @@ __device__ __forceinline__ void m_mul_acc(const cd a[9], const cd b[9], cd c[9])
       c[i * 3 + j] = s;
     }
 }
-__device__ __forceinline__ void m_dag_inplace(cd a[9]) {
+template <typename T>
+__device__ __forceinline__ void m_dag_inplace(cx<T> a[9]) {
+  typedef cx<T> cd;
 #pragma unroll
   for (int i = 0; i < 3; i++) {
     a[i * 3 + i] = conj(a[i * 3 + i]);
@@ -70,20 +98,21 @@ __device__ __forceinline__ void m_dag_inplace(cd a[9]) {
 }
 
 // gamma_mu psi in the block form [[0, a_mu], [b_mu, 0]] (see wilson_dev.cuh)
-template <int MU>
-__device__ __forceinline__ void gamma_mul(const cd in[12], cd out[12]) {
+template <int MU, typename T>
+__device__ __forceinline__ void gamma_mul(const cx<T> in[12], cx<T> out[12]) {
 #pragma unroll
   for (int col = 0; col < 3; col++) {
-    mul_a<MU, double>(in[6 + col], in[9 + col], out[col], out[3 + col]);
-    mul_b<MU, double>(in[col], in[3 + col], out[6 + col], out[9 + col]);
+    mul_a<MU, T>(in[6 + col], in[9 + col], out[col], out[3 + col]);
+    mul_b<MU, T>(in[col], in[3 + col], out[6 + col], out[9 + col]);
   }
 }
-__device__ __forceinline__ void gamma_dyn(int mu, const cd in[12], cd out[12]) {
+template <typename T>
+__device__ __forceinline__ void gamma_dyn(int mu, const cx<T> in[12], cx<T> out[12]) {
   switch (mu) {
-    case 0: gamma_mul<0>(in, out); break;
-    case 1: gamma_mul<1>(in, out); break;
-    case 2: gamma_mul<2>(in, out); break;
-    default: gamma_mul<3>(in, out); break;
+    case 0: gamma_mul<0, T>(in, out); break;
+    case 1: gamma_mul<1, T>(in, out); break;
+    case 2: gamma_mul<2, T>(in, out); break;
+    default: gamma_mul<3, T>(in, out); break;
   }
 }
 
@@ -95,32 +124,36 @@ __device__ __forceinline__ void step(const Geom& g, int c[4], int mu, int d) {
   if (c[mu] >= g.L[mu]) c[mu] -= g.L[mu];
 }
 
-__device__ __forceinline__ void link_at(const Geom& g, const double* gauge, const int c[4], int mu, cd u[9]) {
-  load_link<double>(gauge, g.Vh, (c[0] + c[1] + c[2] + c[3]) & 1, mu, cb_index(g, c), u);
+template <typename T>
+__device__ __forceinline__ void link_at(const Geom& g, const T* gauge, const int c[4], int mu, cx<T> u[9]) {
+  load_link<T>(gauge, g.Vh, (c[0] + c[1] + c[2] + c[3]) & 1, mu, cb_index(g, c), u);
 }
 
-__device__ __forceinline__ void w_at(const Geom& g, const double2* W, const int c[4], int p, cd w[9]) {
+template <typename T>
+__device__ __forceinline__ void w_at(const Geom& g, const typename V2of<T>::type* W, const int c[4], int p,
+                                     cx<T> w[9]) {
   const int par = (c[0] + c[1] + c[2] + c[3]) & 1;
-  const double2* q = W + (size_t)(par * 6 + p) * 9 * g.Vh + cb_index(g, c);
+  const typename V2of<T>::type* q = W + (size_t)(par * 6 + p) * 9 * g.Vh + cb_index(g, c);
 #pragma unroll
   for (int e = 0; e < 9; e++) {
-    const double2 v = q[(size_t)e * g.Vh];
+    const typename V2of<T>::type v = q[(size_t)e * g.Vh];
     w[e] = mkc(v.x, v.y);
   }
 }
 
 // W_{mu nu}(x) for the six planes mu < nu of every site.
-__global__ void __launch_bounds__(128) k_force_insertion(Geom g, const double* lam_e, const double* lam_o,
-                                                         const double* psi_e, const double* psi_o, double csw,
-                                                         double2* W) {
+template <typename T>
+__global__ void __launch_bounds__(128) k_force_insertion(Geom g, const T* lam_e, const T* lam_o, const T* psi_e,
+                                                         const T* psi_o, T csw, typename V2of<T>::type* W) {
+  typedef cx<T> cd;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * g.Vh) return;
   const int par = t >= g.Vh;
   const int i = t - par * g.Vh;
   cd lam[12], psi[12];
-  SpinorIO<double>::load(par ? lam_o : lam_e, g.Vh, i, lam);
-  SpinorIO<double>::load(par ? psi_o : psi_e, g.Vh, i, psi);
-  const double q = -0.25 * csw;   // C = -(i csw/4) S = q * (i S)
+  SpinorIO<T>::load(par ? lam_o : lam_e, g.Vh, i, lam);
+  SpinorIO<T>::load(par ? psi_o : psi_e, g.Vh, i, psi);
+  const T q = (T)-0.25 * csw;   // C = -(i csw/4) S = q * (i S)
   for (int mu = 0; mu < 4; mu++)
     for (int nu = mu + 1; nu < 4; nu++) {
       cd gn[12], gmn[12];
@@ -131,32 +164,34 @@ __global__ void __launch_bounds__(128) k_force_insertion(Geom g, const double* l
       for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int b = 0; b < 3; b++) {
-          cd s = mkc(0.0, 0.0);
+          cd s = mkc((T)0, (T)0);
 #pragma unroll
           for (int sp = 0; sp < 4; sp++) s = cfma_conj(lam[3 * sp + b], gmn[3 * sp + a], s);
           // S_ab = sum_s (sigma psi)_{s a} conj(lam_{s b}) = i * s;  C = q * i * S = -q * s
           C[a * 3 + b] = mkc(-q * s.re, -q * s.im);
         }
-      const cd tr3 = mkc((C[0].re + C[4].re + C[8].re) / 3.0, (C[0].im + C[4].im + C[8].im) / 3.0);
+      const cd tr3 = mkc((C[0].re + C[4].re + C[8].re) / (T)3, (C[0].im + C[4].im + C[8].im) / (T)3);
       C[0] = C[0] - tr3;
       C[4] = C[4] - tr3;
       C[8] = C[8] - tr3;
       const int p = plane_of(mu, nu);
-      double2* out = W + (size_t)(par * 6 + p) * 9 * g.Vh + i;
+      typename V2of<T>::type* out = W + (size_t)(par * 6 + p) * 9 * g.Vh + i;
 #pragma unroll
       for (int a = 0; a < 3; a++)
 #pragma unroll
         for (int b = 0; b < 3; b++) {
           const cd w = C[a * 3 + b] - conj(C[b * 3 + a]);
-          out[(size_t)(a * 3 + b) * g.Vh] = make_double2(0.25 * w.re, 0.25 * w.im);
+          out[(size_t)(a * 3 + b) * g.Vh] = mk2<T>((T)0.25 * w.re, (T)0.25 * w.im);
         }
     }
 }
 
 // K_mu(x) (or the force) of every link; thread = (site, mu = blockIdx.y).
-__global__ void __launch_bounds__(128) k_force_links(Geom g, const double* lam_e, const double* lam_o,
-                                                     const double* psi_e, const double* psi_o, const double* gauge,
-                                                     const double2* W, int kind, double2* out) {
+template <typename T>
+__global__ void __launch_bounds__(128) k_force_links(Geom g, const T* lam_e, const T* lam_o, const T* psi_e,
+                                                     const T* psi_o, const T* gauge,
+                                                     const typename V2of<T>::type* W, int kind, double2* out) {
+  typedef cx<T> cd;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * g.Vh) return;
   const int mu = blockIdx.y;
@@ -171,29 +206,29 @@ __global__ void __launch_bounds__(128) k_force_links(Geom g, const double* lam_e
     int y[4] = {x[0], x[1], x[2], x[3]};
     step(g, y, mu, +1);
     const int j = cb_index(g, y);
-    const double sgn = (mu == 3 && g.apbc && x[3] == g.L[3] - 1) ? -1.0 : 1.0;
+    const T sgn = (mu == 3 && g.apbc && x[3] == g.L[3] - 1) ? (T)-1 : (T)1;
     cd a[12], b[12], ga[12];
     // first outer product: psi(x+mu) against (1 - gamma) lam(x)
-    SpinorIO<double>::load(par ? lam_o : lam_e, g.Vh, i, a);
-    gamma_dyn(mu, a, ga);
+    SpinorIO<T>::load(par ? lam_o : lam_e, g.Vh, i, a);
+    gamma_dyn<T>(mu, a, ga);
 #pragma unroll
     for (int k = 0; k < 12; k++) a[k] = a[k] - ga[k];
-    SpinorIO<double>::load(par ? psi_e : psi_o, g.Vh, j, b);
+    SpinorIO<T>::load(par ? psi_e : psi_o, g.Vh, j, b);
 #pragma unroll
     for (int r = 0; r < 3; r++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
-        cd s = mkc(0.0, 0.0);
+        cd s = mkc((T)0, (T)0);
 #pragma unroll
         for (int sp = 0; sp < 4; sp++) s = cfma_conj(a[3 * sp + c], b[3 * sp + r], s);
         K[r * 3 + c] = s;
       }
     // second: lam(x+mu) against (1 + gamma) psi(x)
-    SpinorIO<double>::load(par ? psi_o : psi_e, g.Vh, i, a);
-    gamma_dyn(mu, a, ga);
+    SpinorIO<T>::load(par ? psi_o : psi_e, g.Vh, i, a);
+    gamma_dyn<T>(mu, a, ga);
 #pragma unroll
     for (int k = 0; k < 12; k++) a[k] = a[k] + ga[k];
-    SpinorIO<double>::load(par ? lam_e : lam_o, g.Vh, j, b);
+    SpinorIO<T>::load(par ? lam_e : lam_o, g.Vh, j, b);
 #pragma unroll
     for (int r = 0; r < 3; r++)
 #pragma unroll
@@ -201,7 +236,7 @@ __global__ void __launch_bounds__(128) k_force_links(Geom g, const double* lam_e
         cd s = K[r * 3 + c];
 #pragma unroll
         for (int sp = 0; sp < 4; sp++) s = cfma_conj(a[3 * sp + c], b[3 * sp + r], s);
-        K[r * 3 + c] = mkc(0.5 * sgn * s.re, 0.5 * sgn * s.im);
+        K[r * 3 + c] = mkc((T)0.5 * sgn * s.re, (T)0.5 * sgn * s.im);
       }
   }
 
@@ -232,32 +267,32 @@ __global__ void __launch_bounds__(128) k_force_links(Geom g, const double* lam_e
       // factor k of the plaquette
       auto factor = [&](int k, cd u[9]) {
         switch (k & 3) {
-          case 0: link_at(g, gauge, cr[0], al, u); break;
-          case 1: link_at(g, gauge, cr[1], be, u); break;
-          case 2: link_at(g, gauge, cr[3], al, u); m_dag_inplace(u); break;
-          default: link_at(g, gauge, cr[0], be, u); m_dag_inplace(u); break;
+          case 0: link_at<T>(g, gauge, cr[0], al, u); break;
+          case 1: link_at<T>(g, gauge, cr[1], be, u); break;
+          case 2: link_at<T>(g, gauge, cr[3], al, u); m_dag_inplace<T>(u); break;
+          default: link_at<T>(g, gauge, cr[0], be, u); m_dag_inplace<T>(u); break;
         }
       };
       // R = ((W1 A1 + A1 W2) A2 + A1 A2 W3) A3 + A1 A2 A3 W0, A_n = L_{j+n}, W_n = W(corner j+n)
-      cd A[9], M[9], T[9], P[9], R[9];
+      cd A[9], M[9], Q[9], P[9], R[9];
       factor(jpos + 1, A);
-      w_at(g, W, cr[(jpos + 1) & 3], p, M);
-      m_mul(M, A, T);
-      w_at(g, W, cr[(jpos + 2) & 3], p, M);
-      m_mul_acc(A, M, T);
+      w_at<T>(g, W, cr[(jpos + 1) & 3], p, M);
+      m_mul<T>(M, A, Q);
+      w_at<T>(g, W, cr[(jpos + 2) & 3], p, M);
+      m_mul_acc<T>(A, M, Q);
 #pragma unroll
       for (int e = 0; e < 9; e++) P[e] = A[e];
       factor(jpos + 2, A);
-      m_mul(T, A, R);
-      m_mul(P, A, T);                        // T = A1 A2
-      w_at(g, W, cr[(jpos + 3) & 3], p, M);
-      m_mul_acc(T, M, R);                    // R = (W1 A1 + A1 W2) A2 + A1 A2 W3
+      m_mul<T>(Q, A, R);
+      m_mul<T>(P, A, Q);                     // Q = A1 A2
+      w_at<T>(g, W, cr[(jpos + 3) & 3], p, M);
+      m_mul_acc<T>(Q, M, R);                 // R = (W1 A1 + A1 W2) A2 + A1 A2 W3
       factor(jpos + 3, A);
-      m_mul(R, A, P);                        // P = R A3
-      m_mul(T, A, R);                        // R = A1 A2 A3
-      w_at(g, W, cr[jpos], p, M);
-      m_mul_acc(R, M, P);                    // P = full R
-      if (jpos >= 2) m_dag_inplace(P);
+      m_mul<T>(R, A, P);                     // P = R A3
+      m_mul<T>(Q, A, R);                     // R = A1 A2 A3
+      w_at<T>(g, W, cr[jpos], p, M);
+      m_mul_acc<T>(R, M, P);                 // P = full R
+      if (jpos >= 2) m_dag_inplace<T>(P);
 #pragma unroll
       for (int e = 0; e < 9; e++) K[e] = K[e] + P[e];
     }
@@ -268,29 +303,29 @@ __global__ void __launch_bounds__(128) k_force_links(Geom g, const double* lam_e
   if (kind == MG_FORCE_WIRTINGER) {
 #pragma unroll
     for (int e = 0; e < 9; e++) o[e] = K[e];
-    m_dag_inplace(o);
+    m_dag_inplace<T>(o);
   } else {
     cd u[9], G[9];
-    load_link<double>(gauge, g.Vh, par, mu, i, u);
-    m_mul(u, K, G);                          // G = i U K (the i is applied below)
+    load_link<T>(gauge, g.Vh, par, mu, i, u);
+    m_mul<T>(u, K, G);                       // G = i U K (the i is applied below)
 #pragma unroll
     for (int e = 0; e < 9; e++) G[e] = times_i(G[e]);
     // H = (G + G^dag)/2, F = (H - tr(H)/3)/2
-    const double trh = (G[0].re + G[4].re + G[8].re) / 3.0;
+    const T trh = (G[0].re + G[4].re + G[8].re) / (T)3;
 #pragma unroll
     for (int a = 0; a < 3; a++)
 #pragma unroll
       for (int c = 0; c < 3; c++) {
         cd hh = G[a * 3 + c] + conj(G[c * 3 + a]);
-        hh = mkc(0.5 * hh.re, 0.5 * hh.im);
+        hh = mkc((T)0.5 * hh.re, (T)0.5 * hh.im);
         if (a == c) hh.re -= trh;
-        o[a * 3 + c] = mkc(0.5 * hh.re, 0.5 * hh.im);
+        o[a * 3 + c] = mkc((T)0.5 * hh.re, (T)0.5 * hh.im);
       }
   }
   const size_t lex = ((((size_t)x[3] * g.L[2] + x[2]) * g.L[1] + x[1]) * g.L[0] + x[0]);
   double2* dst = out + (lex * 4 + mu) * 9;
 #pragma unroll
-  for (int e = 0; e < 9; e++) dst[e] = make_double2(o[e].re, o[e].im);
+  for (int e = 0; e < 9; e++) dst[e] = make_double2((double)o[e].re, (double)o[e].im);
 }
 
 // psi <- gamma_5 psi on an ABI fine vector (complex128 [site][spin][colour])
@@ -310,24 +345,34 @@ void gamma5_abi(double* v, size_t sites, cudaStream_t s) {
   MG_LAUNCH();
 }
 
-void gauge_force(Ctx* c, double* out_abi, const double* lam_abi, const double* psi_abi, int kind) {
+template <typename T>
+void gauge_force_t(Ctx* c, double* out_abi, const double* lam_abi, const double* psi_abi, int kind) {
   const Geom& g = c->g;
-  const size_t half = 24 * c->Vh;   // doubles per half vector
-  DBuf vec(sizeof(double) * 4 * half);
-  DBuf W(sizeof(double) * 2 * 6 * 9 * c->V);
-  double* lam_e = vec.as<double>();
-  double* lam_o = lam_e + half;
-  double* psi_e = lam_o + half;
-  double* psi_o = psi_e + half;
-  pack_spinor(g, lam_abi, lam_e, lam_o, false, c->stream);
-  pack_spinor(g, psi_abi, psi_e, psi_o, false, c->stream);
+  const size_t half = 24 * c->Vh;   // reals per half vector
+  DBuf vec(sizeof(T) * 4 * half);
+  DBuf W(sizeof(T) * 2 * 6 * 9 * c->V);
+  T* lam_e = vec.as<T>();
+  T* lam_o = lam_e + half;
+  T* psi_e = lam_o + half;
+  T* psi_o = psi_e + half;
+  constexpr bool f32 = std::is_same<T, float>::value;
+  pack_spinor(g, lam_abi, lam_e, lam_o, f32, c->stream);
+  pack_spinor(g, psi_abi, psi_e, psi_o, f32, c->stream);
   const int bs = 128;
   const int nb = (int)((2 * c->Vh + bs - 1) / bs);
-  k_force_insertion<<<nb, bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, c->csw, W.as<double2>());
+  typedef typename V2of<T>::type V2;
+  k_force_insertion<T><<<nb, bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, (T)c->csw, W.as<V2>());
   MG_LAUNCH();
-  k_force_links<<<dim3(nb, 4), bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, c->gauge<double>(),
-                                                   W.as<double2>(), kind, (double2*)out_abi);
+  k_force_links<T><<<dim3(nb, 4), bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, c->gauge<T>(), W.as<V2>(), kind,
+                                                      (double2*)out_abi);
   MG_LAUNCH();
   c->sync();
+}
+
+void gauge_force(Ctx* c, double* out_abi, const double* lam_abi, const double* psi_abi, int kind) {
+  if (kind & MG_FORCE_FP32)
+    gauge_force_t<float>(c, out_abi, lam_abi, psi_abi, kind & ~MG_FORCE_FP32);
+  else
+    gauge_force_t<double>(c, out_abi, lam_abi, psi_abi, kind);
 }
 }  // namespace mg

@@ -12,10 +12,25 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 #include "mgclover.h"
 
 namespace mg {
+
+// An NVTX range for the duration of a scope (setup, solve, outer iteration,
+// level cycle, coarse solve); free when no tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+// "<what> level <l>" for l < MG_MAX_LEVELS (static strings)
+const char* level_range_name(int what, int l);
+enum { RANGE_CYCLE = 0, RANGE_COARSE_SOLVE = 1, RANGE_NULL_VECTORS = 2, RANGE_COARSE_LINKS = 3 };
+
 
 // --------------------------------------------------------------------------- errors
 struct Error {
@@ -290,6 +305,7 @@ class GCR {
  public:
   using Op = std::function<void(T* out, const T* in)>;
   using Pre = std::function<void(TZ* z, const T* r)>;
+  using LowOp = std::function<void(T* out, const TZ* in)>;   // A applied to a preconditioner output
   struct Result {
     int iterations = 0;
     int restarts = 0;
@@ -301,7 +317,11 @@ class GCR {
   // Checks ||r|| <= tol_abs after every iteration when check is true (one
   // host sync per iteration); with check false it runs exactly maxit
   // iterations without restarts and without host syncs.
-  Result solve(const Op& A, const Pre* M, T* x, const T* b, bool x0_zero, double tol_abs, int maxit, bool check);
+  // Al (optional): the product A z of the Krylov directions inside a restart
+  // cycle, from the preconditioner output z directly (e.g. in lower
+  // precision); A itself still forms every true residual.
+  Result solve(const Op& A, const Pre* M, T* x, const T* b, bool x0_zero, double tol_abs, int maxit, bool check,
+               const LowOp* Al = nullptr);
   T* residual() { return r_.as<T>(); }
 
  private:
@@ -352,6 +372,10 @@ class Krylov {
 };
 
 // MR smoothing: e = MR_nu(A, r) from e = 0 (r is consumed as scratch)
+// nu MR steps on the fine D_r in FP32 with the fused kernels of mr.cu: e = the
+// correction (zeroed first), r the residual (updated), w, s, t scratch half
+// vectors; d_scr receives the last step's inner products
+void mr_smooth_fine(Ctx* c, float* e, float* r, float* w, float* s, float* t, int nu, double* d_scr);
 template <typename T>
 void mr_smooth(Ctx* c, const std::function<void(T*, const T*)>& A, T* e, T* r, T* w, size_t n, int nu,
                double* d_scr);
@@ -415,6 +439,8 @@ double fma_peak_tflops(int prec);
 // times the level-0 restriction (restrict = true) or prolongation on the even
 // sites for nrhs right-hand sides (see mg_benchmark_kernel_nrhs)
 void mg_benchmark_transfer(Ctx* c, bool restrict, int nrhs, int warmup, int iters, double* avg_ms, double* bytes);
+// floors of one coarsest-level GCR iteration (see mg_benchmark_coarse_floor)
+void mg_benchmark_coarse_floor(Ctx* c, double* barrier_us, double* stream_us, double* stream_bytes, int* grid);
 // times `iters` coarsest-level solves (see mg_benchmark_coarse_solve)
 void mg_benchmark_coarse_solve(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes, double* its);
 

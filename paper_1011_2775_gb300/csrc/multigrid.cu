@@ -208,6 +208,7 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b);
 
 // ----- the cycle: z_e ~ D_r^{-1} r_e on level l
 void cycle(Ctx* c, Hierarchy& H, int l, float* z, const float* r) {
+  Range range(level_range_name(RANGE_CYCLE, l));
   const mg_params& p = c->params;
   LevelWork& W = H.work[l];
   const TransferOp& T = H.tr[l];
@@ -240,12 +241,16 @@ void cycle(Ctx* c, Hierarchy& H, int l, float* z, const float* r) {
     Dr(w, z);
     blas_convert<float, float>(res, r, n, s);
     blas_axpby<float>(-1.0, w, 1.0, res, n, s);
-    mr_smooth<float>(c, Dr, e, res, w, n, p.nu_post, scr);
+    if (l == 0)   // fused fine-level steps (three kernels per step)
+      mr_smooth_fine(c, e, res, w, H.F32->t1.as<float>(), H.F32->t2.as<float>(), p.nu_post, scr);
+    else
+      mr_smooth<float>(c, Dr, e, res, w, n, p.nu_post, scr);
     blas_axpby<float>(1.0, e, 1.0, z, n, s);
   }
 }
 
 void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
+  Range range(level_range_name(RANGE_COARSE_SOLVE, l));
   const mg_params& p = c->params;
   const LevelGeom& G = H.geo[l];
   LevelWork& W = H.work[l];
@@ -355,6 +360,7 @@ void fill_start_vector(Ctx* c, Hierarchy& H, int l, int k, float* v) {
 }
 
 void find_null_vectors(Ctx* c, Hierarchy& H, int l, mg_setup_info* info) {
+  Range range(level_range_name(RANGE_NULL_VECTORS, l));
   const mg_params& p = c->params;
   const int nv = p.nv[l];
   const size_t n = full_n(H, l);
@@ -416,6 +422,7 @@ void find_null_vectors(Ctx* c, Hierarchy& H, int l, mg_setup_info* info) {
 }
 
 void build_coarse_links(Ctx* c, Hierarchy& H, int l) {
+  Range range(level_range_name(RANGE_COARSE_LINKS, l));
   const mg_params& p = c->params;
   TransferOp& T = H.tr[l];
   CoarseOp& C = H.cop[l + 1];
@@ -893,6 +900,16 @@ void mg_benchmark_transfer(Ctx* c, bool restrict, int nrhs, int warmup, int iter
   *bytes = neven * 12.0 * T.nv * esz + nrhs * ((double)c->Vh * 24 * sizeof(float) + (double)cn * sizeof(float));
 }
 
+void mg_benchmark_coarse_floor(Ctx* c, double* barrier_us, double* stream_us, double* stream_bytes, int* grid) {
+  if (!c->mg || c->mg->L < 2) raise(MG_ERR_STATE, "multigrid not set up");
+  Hierarchy& H = *c->mg;
+  const int l = H.L - 1;
+  if (!coarse_gcr_stream_ok(H.geo[l], H.cop[l])) raise(MG_ERR_STATE, "the coarsest level has no streamed solver");
+  *grid = coarse_gcr_stream_grids(H.geo[l], H.cop[l])[0];
+  coarse_floor(H.geo[l], H.cop[l], *grid, c->ws.flags.as<int>(), c->stream, barrier_us, stream_us, stream_bytes);
+  if (c->read_flag(FLAG_TIMEOUT, true)) raise(MG_ERR_CUDA, "a wait in the coarse floor benchmark ran out of time");
+}
+
 void mg_benchmark_coarse_solve(Ctx* c, int warmup, int iters, double* avg_ms, double* bytes, double* its) {
   if (!c->mg || c->mg->L < 2) raise(MG_ERR_STATE, "multigrid not set up");
   Hierarchy& H = *c->mg;
@@ -1119,6 +1136,15 @@ void mg_apply_level(Ctx* c, int op, int level, double* out_abi, const double* in
   }
   unpack(level, out, out_abi);
   c->sync();
+}
+
+const char* level_range_name(int what, int l) {
+  static const char* names[4][MG_MAX_LEVELS] = {
+      {"cycle level 0", "cycle level 1", "cycle level 2", "cycle level 3"},
+      {"coarse solve level 0", "coarse solve level 1", "coarse solve level 2", "coarse solve level 3"},
+      {"null vectors level 0", "null vectors level 1", "null vectors level 2", "null vectors level 3"},
+      {"coarse links level 0", "coarse links level 1", "coarse links level 2", "coarse links level 3"}};
+  return names[what & 3][l < 0 ? 0 : (l >= MG_MAX_LEVELS ? MG_MAX_LEVELS - 1 : l)];
 }
 
 }  // namespace mg

@@ -278,7 +278,7 @@ GCR<T, TZ>::GCR(Ctx* c, size_t n, int m) : c_(c), n_(n), m_(m) {
 
 template <typename T, typename TZ>
 typename GCR<T, TZ>::Result GCR<T, TZ>::solve(const Op& A, const Pre* M, T* x, const T* b, bool x0_zero,
-                                                double tol_abs, int maxit, bool check) {
+                                                double tol_abs, int maxit, bool check, const LowOp* Al) {
   cudaStream_t s = c_->stream;
   const int m = m_;
   const size_t n = n_;
@@ -319,13 +319,16 @@ typename GCR<T, TZ>::Result GCR<T, TZ>::solve(const Op& A, const Pre* M, T* x, c
     int k = 0;
     bool done = false;
     while (k < m && res.iterations < maxit) {
+      Range range(std::is_same<T, double>::value ? "outer gcr iteration" : "coarse gcr iteration");
       TZ* z = Z_[k].as<TZ>();
       T* w = W_[k].as<T>();
       if (M)
         (*M)(z, r);
       else
         blas_convert<T, TZ>(z, r, n, s);
-      if (std::is_same<T, TZ>::value) {
+      if (Al) {
+        (*Al)(w, z);
+      } else if (std::is_same<T, TZ>::value) {
         A(w, reinterpret_cast<const T*>(z));
       } else {
         blas_convert<TZ, T>(tmp, z, n, s);
@@ -389,7 +392,7 @@ template void mr_smooth<double>(Ctx*, const std::function<void(double*, const do
 namespace {
 struct SolveBuffers {
   DBuf be, bo, xe, xo, y, br, te, to;
-  DBuf r32, z32;
+  DBuf r32, z32, w32;
   std::unique_ptr<FineOps<double>> F64;
   std::unique_ptr<GCR<double, float>> gcr_mg;
   std::unique_ptr<GCR<double, double>> gcr_eo;
@@ -419,6 +422,7 @@ int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int m
     for (DBuf* d : {&B->be, &B->bo, &B->xe, &B->xo, &B->y, &B->br, &B->te, &B->to}) d->alloc(sizeof(double) * 2 * n);
     B->r32.alloc(sizeof(float) * 2 * n);
     B->z32.alloc(sizeof(float) * 2 * n);
+    B->w32.alloc(sizeof(float) * 2 * n);
     B->F64.reset(new FineOps<double>(c));
     B->restart = restart;
   }
@@ -462,7 +466,15 @@ int solve_fine(Ctx* c, double* psi_abi, const double* eta_abi, double tol, int m
         blas_convert<double, float>(r32, r, n, s);
         mg_precondition(c, z, r32);
       };
-      auto res = B->gcr_mg->solve(Aop, &pre, y, br, first, tol_r, maxit - used, true);
+      // the Krylov directions' product in FP32 (the true residuals stay FP64)
+      if (!B->F32) B->F32.reset(new FineOps<float>(c));
+      float* w32 = B->w32.as<float>();
+      GCR<double, float>::LowOp low = [&](double* w, const float* z) {
+        B->F32->Dr(w32, z);
+        blas_convert<float, double>(w, w32, n, s);
+      };
+      auto res = B->gcr_mg->solve(Aop, &pre, y, br, first, tol_r, maxit - used, true,
+                                  c->params.outer_prec == MG_FP32 ? &low : nullptr);
       used += res.iterations;
       restarts += res.restarts;
     } else if (mode == MG_MODE_EO_GCR) {

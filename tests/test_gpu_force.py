@@ -2,7 +2,7 @@
 
 * mg_force (hop + clover link derivative, FP64) against the oracle's
   link_derivative / su3_force: relative error <= 1e-12 on lattices that span
-  several CTAs with a ragged tail.
+  several CTAs with a ragged tail; its FP32 form (MG_FORCE_FP32) <= 1e-5.
 * mg_solve_dagger: ||chi - D^dag lam|| / ||chi|| <= 1e-10 with the oracle's D.
 * The torch.autograd Function: grad_eta and grad_U against the oracle's
   gradients from dense solves (limited by the solve tolerance), and the su(3)
@@ -12,7 +12,7 @@
 import numpy as np
 import pytest
 
-from gpu_common import TOL64, lib_built, rel
+from gpu_common import TOL32, TOL64, lib_built, rel
 from oracle import force as OF
 from oracle.dirac import WilsonClover, dag, norm2
 from paper_1011_2775_gb300 import inputs as I
@@ -50,6 +50,26 @@ def test_force_parity(case):
         got_f = S.force(lam, psi, kind=B.MG_FORCE_SU3)
     assert rel(got_w, dag(K)) <= TOL64
     assert rel(got_f, OF.su3_force(U, K)) <= TOL64
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c[0])))
+def test_force_parity_fp32(case):
+    """The FP32 form (MG_FORCE_FP32: FP32 links, vectors and arithmetic)
+    against the FP64 oracle at the FP32 kernels' tolerance."""
+    from paper_1011_2775_gb300 import binding as B
+    dims, eps, ape, csw, m0, seed = case
+    U = I.make_gauge(dims, eps, ape, 0.5, seed)
+    W = WilsonClover(U, csw, m0)
+    lam = I.gaussian_source(dims, seed + 1)
+    psi = I.gaussian_source(dims, seed + 2)
+    K = OF.link_derivative(W, lam.reshape(W.shape + (12,)), psi.reshape(W.shape + (12,)))
+    with _solver(dims, U, csw, m0) as S:
+        got_w = S.force(lam, psi, kind=B.MG_FORCE_WIRTINGER | B.MG_FORCE_FP32)
+        got_f = S.force(lam, psi, kind=B.MG_FORCE_SU3 | B.MG_FORCE_FP32)
+        f64 = S.force(lam, psi, kind=B.MG_FORCE_SU3)
+    assert rel(got_w, dag(K)) <= TOL32
+    assert rel(got_f, OF.su3_force(U, K)) <= TOL32
+    assert rel(got_f, f64) > 0   # a separate FP32 computation, not the FP64 one
 
 
 def test_force_device_buffers_match_host():

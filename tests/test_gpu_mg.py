@@ -362,6 +362,32 @@ def test_mg_iterations_match_oracle(qcdlike):
     S.close()
 
 
+@pytest.mark.parametrize("rhs_block", [1, 3])
+def test_outer_products_in_fp32_and_fp64(qcdlike, rhs_block):
+    """mg_params.outer_prec: the outer FGCR's products D_r z in FP32 (the
+    default) or FP64.  Both reach 1e-10 with the oracle's D (the true residuals
+    are FP64 either way) in about as many outer iterations as the oracle, single
+    and block solves alike."""
+    from paper_1011_2775_gb300 import binding as B
+    dims, U, W, V0 = qcdlike
+    mg = Multigrid(W, MGParams(blocks=[(2, 2, 2, 2)], nv=[8]), null_vectors=[V0])
+    eta = I.gaussian_source(dims, 9, nrhs=rhs_block)
+    _, oinfo = mg.solve(eta[0].reshape(W.shape + (12,)), 1e-10)
+    S = _solver(dims, U, 1.0, -0.6)
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[8], rhs_block=rhs_block)
+    S.set_null_vectors(0, np.ascontiguousarray(np.stack(V0)))
+    S.setup()
+    its = {}
+    for prec in (B.MG_FP32, B.MG_FP64):
+        S.set_params(outer_prec=prec)
+        psi, info = S.solve(eta, 1e-10, B.MG_MODE_MG)
+        for q in range(rhs_block):
+            assert _true_residual(W, psi[q], eta[q]) <= 1e-10, (prec, q)
+        its[prec] = info.outer_iterations / rhs_block
+        assert abs(its[prec] - oinfo.outer_iterations) <= max(3, 0.25 * oinfo.outer_iterations), (prec, its)
+    S.close()
+
+
 def test_cycle_graph_replay_matches_direct_launches():
     """The single-rhs solve replays its 2-level cycle as a captured CUDA graph
     (mg_params.cuda_graphs = 1, the default); the same kernels launched one by
