@@ -174,6 +174,15 @@ def oracle_worker(job):
     from paper_1011_2775_gb300 import inputs as I
     U = I.make_gauge(dims, EPS, APE, ALPHA, GAUGE_SEED)
     W = WilsonClover(U, CSW, MASSES[-1])
+    if mode == "dr":   # `steps` applications of the oracle's D_r on even-site vectors
+        y = I.gaussian_source(dims, SOURCE_SEED + seed).reshape(W.shape + (12,)) * W.even
+        W.Dr(y)
+        times = []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            W.Dr(y)
+            times.append(time.perf_counter() - t0)
+        return {"dr_s": statistics.median(times)}
     prm = MGParams(blocks=[(4, 4, 4, 4)], nv=[24], tol_coarse=MG["tol_coarse"], restart_coarse=MG["restart_coarse"],
                    setup_iters=CPU_SETUP_ITERS, seed=NULLVEC_SEED)
     t0 = time.perf_counter()
@@ -219,7 +228,13 @@ def cpu_baseline(gpu_outer: int, gpu_small_ms: float) -> dict:
     per_it = statistics.median(r["solve_s"] / r["outer_iterations"] for r in res)
     vol = (DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]) / (CPU_DIMS[0] * CPU_DIMS[1] * CPU_DIMS[2] * CPU_DIMS[3])
     value = 1e3 * per_it * vol * gpu_outer / n
+    # the oracle's fine D_r on the 16^3x32 workload: one process alone, then one per core at once
+    one = oracle_pool([("dr", 0, 2, DIMS)])[0]["dr_s"]
+    alln = oracle_pool([("dr", q, 2, DIMS) for q in range(n)])
+    per_all = statistics.median(r["dr_s"] for r in alln)
     return {"value": value, "unit": "ms", "cores": n, "kind": "oracle",
+            "dr_16x16x16x32": {"single_core_ms": 1e3 * one, "all_cores_ms_per_apply": 1e3 * per_all / n,
+                               "processes": n},
             "sample": (f"{n} concurrent single-thread processes, each the oracle's complete MG-GCR solve (setup "
                        f"{CPU_SETUP_ITERS} passes per vector, then to 1e-10) of an 8^4 lattice of the same "
                        f"construction and parameters (4^4 blocks, Nv=24); projection: median wall time per outer "
@@ -561,13 +576,15 @@ def run_extras(args, S, U, eta, flush, stream, dev) -> dict:
     p_d = torch.zeros_like(e_d)
     alt = {}
     for name, kw in (("tol_0.3", dict(tol_coarse=ALT_COARSE_TOL)), ("single_system_kernel", dict(coarse_impl=1)),
-                     ("outer_fp64_products", dict(outer_prec=B.MG_FP64))):
+                     ("outer_fp64_products", dict(outer_prec=B.MG_FP64)), ("level_timing", dict(level_timing=1))):
         S.set_params(**kw)
         S.solve(e_d, TOL, B.MG_MODE_MG, out=p_d)
         t_p, (_, qi) = timed(lambda: S.solve(e_d, TOL, B.MG_MODE_MG, out=p_d))
         alt[name] = {"ms": t_p, "outer_iterations": qi.outer_iterations, "coarse_iterations": qi.coarse_iterations[1],
                      "true_residual": qi.true_residual}
-        S.set_params(tol_coarse=MG["tol_coarse"], coarse_impl=0, outer_prec=B.MG_FP32)
+        if name == "level_timing":   # GPU ms inside the level-0 cycles and the level-1 coarse solves
+            alt[name]["level_ms"] = [qi.level_ms[0], qi.level_ms[1]]
+        S.set_params(tol_coarse=MG["tol_coarse"], coarse_impl=0, outer_prec=B.MG_FP32, level_timing=0)
     out["coarse_tolerance"] = alt
     del e_d, p_d
 
@@ -820,6 +837,9 @@ SWEEP_EO_CAP = 2000                  # EO-GCR and BiCGStab iteration cap in the 
 # (odd extent: no even-odd there), 16-bit storage of P and coarse links.
 CONFIG3_DIMS = (24, 24, 24, 64)
 CONFIG3_MG = dict(levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 32])
+# a rougher field whose critical mass lies near -0.75 (24^3x64: m0 = -0.75 no longer converges in 300 outer
+# iterations), at a light subcritical mass: the regime of the paper's 3-level runs
+ROUGH_EPS, ROUGH_M0 = 1.0, -0.7
 
 
 def run_config3(dev: int) -> dict:
@@ -832,15 +852,23 @@ def run_config3(dev: int) -> dict:
     from paper_1011_2775_gb300.solver import Solver
 
     stream = torch.cuda.current_stream(dev)
-    U = I.make_gauge(CONFIG3_DIMS, EPS, APE, ALPHA, 3001)
+    fields = {EPS: I.make_gauge(CONFIG3_DIMS, EPS, APE, ALPHA, 3001)}
     eta = torch.from_numpy(I.gaussian_source(CONFIG3_DIMS, 3002)).to(f"cuda:{dev}")
     psi = torch.zeros_like(eta)
-    out = {"lattice": "24^3x64", "m0": -0.35, "mg": "3-level: 4^4 (Nv=24) then 2^4 (Nv=32), coarsest 3^3x8"}
-    for name, store, mg in (("three_level_bf16", B.MG_STORE_BF16, CONFIG3_MG),
-                            ("two_level_bf16", B.MG_STORE_BF16, MG), ("two_level_fp32", B.MG_STORE_FP32, MG)):
+    out = {"lattice": "24^3x64", "m0": -0.35, "mg": "3-level: 4^4 (Nv=24) then 2^4 (Nv=32), coarsest 3^3x8",
+           "rough": f"the rough ensemble eps = {ROUGH_EPS} + 5 APE at m0 = {ROUGH_M0}, below its critical mass, "
+                    "2 against 3 levels in FP32 storage"}
+    runs = (("three_level_bf16", B.MG_STORE_BF16, CONFIG3_MG, EPS, -0.35),
+            ("two_level_bf16", B.MG_STORE_BF16, MG, EPS, -0.35), ("two_level_fp32", B.MG_STORE_FP32, MG, EPS, -0.35),
+            ("rough_three_level_fp32", B.MG_STORE_FP32, CONFIG3_MG, ROUGH_EPS, ROUGH_M0),
+            ("rough_two_level_fp32", B.MG_STORE_FP32, MG, ROUGH_EPS, ROUGH_M0))
+    for name, store, mg, eps, m0 in runs:
+        if eps not in fields:
+            fields[eps] = I.make_gauge(CONFIG3_DIMS, eps, APE, ALPHA, 3001)
+        U = fields[eps]
         S = Solver(CONFIG3_DIMS, device=dev, stream=stream.cuda_stream)
         S.load_gauge(U)
-        S.set_clover(CSW, -0.35)
+        S.set_clover(CSW, m0)
         S.set_params(seed=3003, maxit_fine=2000, storage=store, **mg)
         t0 = time.perf_counter()
         S.setup()
@@ -858,7 +886,7 @@ def run_config3(dev: int) -> dict:
             ts.append(e0.elapsed_time(e1))
         out[name] = {"solve_ms": min(ts), "setup_ms": setup_ms, "outer_iterations": info.outer_iterations,
                      "level1_iterations": info.coarse_iterations[1], "level2_iterations": info.coarse_iterations[2],
-                     "true_residual": info.true_residual, "levels": mg["levels"]}
+                     "true_residual": info.true_residual, "levels": mg["levels"], "eps": eps, "m0": m0}
         if name == "two_level_fp32":
             ms_k, by = B.mg_benchmark_kernel(S.ctx, B.MG_KERNEL_DSLASH_CLOVER, B.MG_FP32, warmup=10, iters=50)
             out["dslash_clover_fp32"] = {"ms": ms_k, "bytes": by, "gbs": by / ms_k / 1e6}

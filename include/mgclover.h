@@ -157,6 +157,9 @@ typedef struct {
                                   /* output, widened to FP64 for the FP64 orthogonalisation and    */
                                   /* update) or MG_FP64; the true residual at every restart and    */
                                   /* the final check are FP64 either way                           */
+  int level_timing;               /* 1: time every level's work with CUDA events into              */
+                                  /* mg_solve_info.level_ms (the cycle graph is not used then;     */
+                                  /* events add a few microseconds per coarse solve); 0: off       */
 } mg_params;
 
 typedef struct {
@@ -175,6 +178,10 @@ typedef struct {
   double solve_ms;                          /* wall time of the call                          */
   long long dslash_launches;                /* fine hopping-term launches in the call         */
   long long kernel_launches;                /* all library kernel launches in the call        */
+  double level_ms[MG_MAX_LEVELS];           /* with mg_params.level_timing: GPU ms inside the */
+                                            /* level-0 cycles (the whole preconditioner) and  */
+                                            /* inside the level-l coarse solves (l >= 1, each */
+                                            /* including the levels below it); else 0         */
 } mg_solve_info;
 
 /* Kernels for mg_benchmark_kernel. */
@@ -198,7 +205,7 @@ MG_API const char* mg_last_error(void);
  * GCR iterations, RQ tolerance 0.05, nu_post = 4, coarse tolerance 0.1,
  * coarse restart 32 / cap 50, outer restart 16 / cap 500, FP32 storage,
  * Galerkin projection of D_p, seed 3, rhs_block 16, cuda_graphs 1, coarse_impl 0,
- * outer_prec MG_FP32. */
+ * outer_prec MG_FP32, level_timing 0. */
 MG_API int mg_default_params(mg_params* p);
 
 /* Create a context for a lattice of `dims` on CUDA device `device`; kernels

@@ -64,7 +64,8 @@ class mg_params(ctypes.Structure):
                 ("rhs_block", ctypes.c_int),
                 ("cuda_graphs", ctypes.c_int),
                 ("coarse_impl", ctypes.c_int),
-                ("outer_prec", ctypes.c_int)]
+                ("outer_prec", ctypes.c_int),
+                ("level_timing", ctypes.c_int)]
 
 
 class mg_setup_info(ctypes.Structure):
@@ -82,7 +83,8 @@ class mg_solve_info(ctypes.Structure):
                 ("true_residual", ctypes.c_double),
                 ("solve_ms", ctypes.c_double),
                 ("dslash_launches", ctypes.c_longlong),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong),
+                ("level_ms", ctypes.c_double * MG_MAX_LEVELS)]
 
 
 class MGError(RuntimeError):

@@ -103,6 +103,7 @@ int solve_impl(void* ctx, void* psi, const void* eta, int nrhs, double tol, int 
   std::memset(&local, 0, sizeof(local));
   local.true_residual = 0.0;
   mg::mg_reset_counters(c);
+  mg::level_times_reset(c);
   const long long launches0 = c->dslash_launches;
   const long long kernels0 = mg::launches_so_far();
   const size_t per = sizeof(double) * 24 * c->V;
@@ -129,6 +130,7 @@ int solve_impl(void* ctx, void* psi, const void* eta, int nrhs, double tol, int 
   if (dagger) mg::gamma5_abi(so.ptr, c->V * nrhs, c->stream);
   stage_out_finish(c, so, psi, per * nrhs, where);
   mg::mg_read_counters(c, local.coarse_iterations);
+  mg::level_times(c, local.level_ms);
   local.dslash_launches = c->dslash_launches - launches0;
   local.kernel_launches = mg::launches_so_far() - kernels0;
   local.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -188,6 +190,7 @@ int mg_default_params(mg_params* p) {
   p->cuda_graphs = 1;
   p->coarse_impl = 0;
   p->outer_prec = MG_FP32;
+  p->level_timing = 0;
   return MG_OK;
 }
 
@@ -289,6 +292,7 @@ int mg_set_params(void* ctx, const mg_params* p) {
     if (p->cuda_graphs != 0 && p->cuda_graphs != 1) mg::raise(MG_ERR_ARG, "cuda_graphs must be 0 or 1");
     if (p->coarse_impl < 0 || p->coarse_impl > 4) mg::raise(MG_ERR_ARG, "coarse_impl must be in [0, 4]");
     if (p->outer_prec != MG_FP32 && p->outer_prec != MG_FP64) mg::raise(MG_ERR_ARG, "outer_prec must be MG_FP32 or MG_FP64");
+    if (p->level_timing != 0 && p->level_timing != 1) mg::raise(MG_ERR_ARG, "level_timing must be 0 or 1");
     int d[4] = {c->dims[0], c->dims[1], c->dims[2], c->dims[3]};
     int ndof = 12;
     for (int l = 0; l + 1 < p->levels; l++) {

@@ -27,6 +27,19 @@ struct Range {
   Range(const Range&) = delete;
   Range& operator=(const Range&) = delete;
 };
+struct Ctx;
+// With mg_params.level_timing on, records a CUDA event pair on the context
+// stream around its scope into the level's list (level_times() sums them).
+struct LevelTime {
+  LevelTime(Ctx* c, int level);
+  ~LevelTime();
+  Ctx* c;
+  int level;
+  int slot = -1;
+};
+// sums and clears the recorded pairs of every level (synchronises the stream)
+void level_times(Ctx* c, double out_ms[MG_MAX_LEVELS]);
+void level_times_reset(Ctx* c);
 // "<what> level <l>" for l < MG_MAX_LEVELS (static strings)
 const char* level_range_name(int what, int l);
 enum { RANGE_CYCLE = 0, RANGE_COARSE_SOLVE = 1, RANGE_NULL_VECTORS = 2, RANGE_COARSE_LINKS = 3 };
@@ -228,6 +241,16 @@ struct Ctx {
   // host I/O staging
   DBuf stage_in, stage_out;              // complex128 whole-lattice staging
   long long dslash_launches = 0;
+  // mg_params.level_timing: CUDA event pairs around each level's work, per level
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> level_events[MG_MAX_LEVELS];
+  int level_events_used[MG_MAX_LEVELS] = {0, 0, 0, 0};
+  ~Ctx() {
+    for (auto& v : level_events)
+      for (auto& e : v) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+  }
   std::shared_ptr<void> solve_work;      // solve buffers (solver.cu), kept between calls
   std::shared_ptr<void> block_work;      // block-solve buffers (block.cu), kept between calls
 

@@ -209,6 +209,7 @@ void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b);
 // ----- the cycle: z_e ~ D_r^{-1} r_e on level l
 void cycle(Ctx* c, Hierarchy& H, int l, float* z, const float* r) {
   Range range(level_range_name(RANGE_CYCLE, l));
+  LevelTime timer(c, l == 0 ? 0 : -1);
   const mg_params& p = c->params;
   LevelWork& W = H.work[l];
   const TransferOp& T = H.tr[l];
@@ -251,6 +252,7 @@ void cycle(Ctx* c, Hierarchy& H, int l, float* z, const float* r) {
 
 void coarse_solve(Ctx* c, Hierarchy& H, int l, float* x, const float* b) {
   Range range(level_range_name(RANGE_COARSE_SOLVE, l));
+  LevelTime timer(c, l);
   const mg_params& p = c->params;
   const LevelGeom& G = H.geo[l];
   LevelWork& W = H.work[l];
@@ -695,6 +697,7 @@ void mg_batch_systems(Ctx* c, int nb, std::vector<CoarseSystem>& out) {
 CoarseGCRBuffers& mg_batch_buffers(Ctx* c) { return c->mg->work[1].cg; }
 
 void mg_batch_coarse(Ctx* c, int nb) {
+  LevelTime timer(c, 1);
   BatchCtx b(c, nb);
   if (b.H.L == 2) {
     const int restart = b.p.restart_coarse > 0 ? b.p.restart_coarse : 32;
@@ -742,6 +745,7 @@ void mg_batch_post(Ctx* c, float* z, const float* r, int nb) {
 }
 
 void mg_precondition_batch(Ctx* c, float* z, const float* r, int nb) {
+  LevelTime timer(c, 0);
   mg_batch_pre(c, z, r, nb);
   mg_batch_coarse(c, nb);
   mg_batch_post(c, z, r, nb);
@@ -774,7 +778,7 @@ void mg_cycle_batch(Ctx* c, double* out_abi, const double* in_abi, int nb) {
 // synchronises), or after a failed capture -- and the caller runs the cycle
 // directly.
 bool mg_precondition_graph(Ctx* c, float* z_e, const double* r_e, float* r32) {
-  if (!c->mg || !c->params.cuda_graphs) return false;
+  if (!c->mg || !c->params.cuda_graphs || c->params.level_timing) return false;
   Hierarchy& H = *c->mg;
   CycleGraph& G = H.graph;
   if (H.L != 2 || G.failed || H.work[1].coarse_impl < 0) return false;
@@ -1145,6 +1149,44 @@ const char* level_range_name(int what, int l) {
       {"null vectors level 0", "null vectors level 1", "null vectors level 2", "null vectors level 3"},
       {"coarse links level 0", "coarse links level 1", "coarse links level 2", "coarse links level 3"}};
   return names[what & 3][l < 0 ? 0 : (l >= MG_MAX_LEVELS ? MG_MAX_LEVELS - 1 : l)];
+}
+
+LevelTime::LevelTime(Ctx* ctx, int l) : c(ctx), level(l) {
+  if (!c->params.level_timing || level < 0 || level >= MG_MAX_LEVELS) {
+    level = -1;
+    return;
+  }
+  auto& v = c->level_events[level];
+  slot = c->level_events_used[level]++;
+  if (slot >= (int)v.size()) {
+    cudaEvent_t a, b;
+    MG_CUDA(cudaEventCreate(&a));
+    MG_CUDA(cudaEventCreate(&b));
+    v.emplace_back(a, b);
+  }
+  MG_CUDA(cudaEventRecord(v[slot].first, c->stream));
+}
+
+LevelTime::~LevelTime() {
+  if (level >= 0) cudaEventRecord(c->level_events[level][slot].second, c->stream);
+}
+
+void level_times_reset(Ctx* c) {
+  for (int l = 0; l < MG_MAX_LEVELS; l++) c->level_events_used[l] = 0;
+}
+
+void level_times(Ctx* c, double out_ms[MG_MAX_LEVELS]) {
+  for (int l = 0; l < MG_MAX_LEVELS; l++) out_ms[l] = 0.0;
+  if (!c->params.level_timing) return;
+  MG_CUDA(cudaStreamSynchronize(c->stream));
+  for (int l = 0; l < MG_MAX_LEVELS; l++) {
+    for (int k = 0; k < c->level_events_used[l]; k++) {
+      float ms = 0.f;
+      MG_CUDA(cudaEventElapsedTime(&ms, c->level_events[l][k].first, c->level_events[l][k].second));
+      out_ms[l] += ms;
+    }
+  }
+  level_times_reset(c);
 }
 
 }  // namespace mg

@@ -434,32 +434,12 @@ __global__ void __launch_bounds__(128) k_dslash(Geom g, int par, T* out, const T
   dslash_site<T, EPI>(g, par, i, out, in, gauge, clov, x, a, dirmask);
 }
 
-// Multi-RHS form: nrhs vectors at a fixed stride (in elements of T).  A
-// thread owns one site and NR right-hand sides (the block index selects the
-// site block and the group of NR, group fastest): every link is loaded once
-// into registers and applied to the NR
-// neighbour spinors, so link bytes are paid once per site and NR rhs while
-// the spinor loads stay coalesced over consecutive sites.
-template <typename T, int EPI, int NR, int BS, int MINB>
-__global__ void __launch_bounds__(BS, MINB) k_dslash_mrhs(Geom g, int par, int nrhs, size_t stride, T* out,
-                                                    const T* __restrict__ in, const T* __restrict__ gauge,
-                                                    const T* __restrict__ clov, const T* __restrict__ x, T a,
-                                                    int dirmask) {
-  // 1-D grid, rhs group fastest: CTAs that run together share the sites
-  // (and so the link and clover lines in L2) of consecutive rhs groups
-  const int ngroups = (nrhs + NR - 1) / NR;
-  const int i = (int)(blockIdx.x / ngroups) * BS + threadIdx.x;
-  if (i >= g.Vh) return;
-  const int r0 = (int)(blockIdx.x % ngroups) * NR;
-  const int nr = nrhs - r0 < NR ? nrhs - r0 : NR;
-  int c[4];
-  cb_coords(g, i, par, c);
-  cx<T> acc[NR][12];
-#pragma unroll
-  for (int r = 0; r < NR; r++)
-#pragma unroll
-    for (int k = 0; k < 12; k++) acc[r][k] = mkc<T>(0, 0);
-  hop_sum_nr<T, NR>(g, in + (size_t)r0 * stride, stride, nr, gauge, par, i, c, dirmask, acc);
+// The epilogues of the multi-RHS kernels for the nr <= NR right-hand sides
+// r0 .. r0 + nr - 1 of site i (acc: the hop sums without the -1/2).
+template <typename T, int EPI, int NR>
+__device__ __forceinline__ void mrhs_epilogue(const Geom& g, int i, cx<T> (&acc)[NR][12], int nr, int r0,
+                                              size_t stride, T* out, const T* __restrict__ clov,
+                                              const T* __restrict__ x, T a) {
   const T half = (T)-0.5;
 #pragma unroll
   for (int r = 0; r < NR; r++) {
@@ -496,6 +476,35 @@ __global__ void __launch_bounds__(BS, MINB) k_dslash_mrhs(Geom g, int par, int n
     }
     SpinorIO<T>::store(out + o, g.Vh, i, res);
   }
+}
+
+// Multi-RHS form: nrhs vectors at a fixed stride (in elements of T).  A
+// thread owns one site and NR right-hand sides (the block index selects the
+// site block and the group of NR, group fastest): every link is loaded once
+// into registers and applied to the NR
+// neighbour spinors, so link bytes are paid once per site and NR rhs while
+// the spinor loads stay coalesced over consecutive sites.
+template <typename T, int EPI, int NR, int BS, int MINB>
+__global__ void __launch_bounds__(BS, MINB) k_dslash_mrhs(Geom g, int par, int nrhs, size_t stride, T* out,
+                                                    const T* __restrict__ in, const T* __restrict__ gauge,
+                                                    const T* __restrict__ clov, const T* __restrict__ x, T a,
+                                                    int dirmask) {
+  // 1-D grid, rhs group fastest: CTAs that run together share the sites
+  // (and so the link and clover lines in L2) of consecutive rhs groups
+  const int ngroups = (nrhs + NR - 1) / NR;
+  const int i = (int)(blockIdx.x / ngroups) * BS + threadIdx.x;
+  if (i >= g.Vh) return;
+  const int r0 = (int)(blockIdx.x % ngroups) * NR;
+  const int nr = nrhs - r0 < NR ? nrhs - r0 : NR;
+  int c[4];
+  cb_coords(g, i, par, c);
+  cx<T> acc[NR][12];
+#pragma unroll
+  for (int r = 0; r < NR; r++)
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[r][k] = mkc<T>(0, 0);
+  hop_sum_nr<T, NR>(g, in + (size_t)r0 * stride, stride, nr, gauge, par, i, c, dirmask, acc);
+  mrhs_epilogue<T, EPI, NR>(g, i, acc, nr, r0, stride, out, clov, x, a);
 }
 
 template <typename T>

@@ -388,6 +388,33 @@ def test_outer_products_in_fp32_and_fp64(qcdlike, rhs_block):
     S.close()
 
 
+def test_level_timing():
+    """mg_params.level_timing: CUDA-event times of every level's work in
+    mg_solve_info.level_ms, nested (the level-l coarse solves run inside the
+    level-(l-1) work), the same solution as an untimed solve, and zeros when off."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (8, 8, 8, 16)
+    U = I.make_gauge(dims, 1.0, 5, 0.5, 5201)
+    W = WilsonClover(U, 1.0, -0.6)
+    eta = I.gaussian_source(dims, 5202)
+    for levels, blocks, nv in ((2, [(4, 4, 4, 4)], [12]), (3, [(2, 2, 2, 2), (2, 2, 2, 2)], [8, 8])):
+        S = _solver(dims, U, 1.0, -0.6)
+        S.set_params(levels=levels, blocks=blocks, nv=nv, seed=5203, maxit_fine=2000)
+        S.setup()
+        psi0, info0 = S.solve(eta, 1e-10, B.MG_MODE_MG)
+        assert all(t == 0.0 for t in info0.level_ms)
+        S.set_params(level_timing=1)
+        psi1, info1 = S.solve(eta, 1e-10, B.MG_MODE_MG)
+        assert _true_residual(W, psi1, eta) <= 1e-10
+        assert info1.outer_iterations == info0.outer_iterations
+        t = list(info1.level_ms)
+        assert t[0] > 0 and 0 < t[1] <= t[0], t
+        if levels == 3:
+            assert 0 < t[2] <= t[1], t
+        assert t[0] <= info1.solve_ms
+        S.close()
+
+
 def test_cycle_graph_replay_matches_direct_launches():
     """The single-rhs solve replays its 2-level cycle as a captured CUDA graph
     (mg_params.cuda_graphs = 1, the default); the same kernels launched one by
