@@ -157,15 +157,28 @@ __device__ void gather(const SArgs& a, int i0, int i1, int ips, int site_base, c
     const int nc = a.nc, K = 8 * nc;
     const int s0 = i0 / ips, s1 = (i1 - 1) / ips;
     const int total = (s1 - s0 + 1) * K;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int sl = t / K, rem = t % K, d = rem / nc, j = rem % nc;
-      const int s = site_base + s0 + sl;   // storage index of the site
-      float2 v = __ldcg(in + (size_t)a.nbr[(size_t)s * 8 + d] * nc + j);
-      if (scale) {
-        const float sc = scale[(size_t)(s0 + sl) * 8 + d];
-        v = make_float2(sc * v.x, sc * v.y);
+    // four elements per thread and round: their neighbour indices, then their
+    // loads, are in flight together (two L2 round trips per round)
+    constexpr int U = 4;
+    for (int t0 = threadIdx.x; t0 < total; t0 += U * blockDim.x) {
+      int src[U];
+      float sc[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int t = t0 + u * blockDim.x;
+        const int tt = t < total ? t : 0;
+        const int sl = tt / K, rem = tt % K, d = rem / nc, j = rem % nc;
+        src[u] = a.nbr[(size_t)(site_base + s0 + sl) * 8 + d] * nc + j;
+        sc[u] = scale ? scale[(size_t)(s0 + sl) * 8 + d] : 1.f;
       }
-      gv[t] = v;
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; u++) v[u] = __ldcg(in + (size_t)src[u]);
+#pragma unroll
+      for (int u = 0; u < U; u++) {
+        const int t = t0 + u * blockDim.x;
+        if (t < total) gv[t] = make_float2(sc[u] * v[u].x, sc[u] * v[u].y);
+      }
     }
   }
   __syncthreads();
@@ -192,6 +205,29 @@ __device__ __forceinline__ float reduce_values(float v[V]) {
   float t = v[0];
 #pragma unroll
   for (int o = 16 / V; o >= 1; o /= 2) t += __shfl_xor_sync(0xffffffffu, t, o);
+  return t;
+}
+
+// reduce_values for double-float sums: lane l ends with the warp total of
+// v[(l >> (5 - log2 V)) & (V - 1)], added in a fixed order.
+template <int V>
+__device__ __forceinline__ df reduce_df(df v[V]) {
+  const int lane = threadIdx.x & 31;
+  int off = 16;
+#pragma unroll
+  for (int half = V / 2; half >= 1; half /= 2, off /= 2) {
+    const bool up = (lane & off) != 0;
+#pragma unroll
+    for (int i = 0; i < half; i++) {
+      const df send = up ? v[i] : v[i + half];
+      const df keep = up ? v[i + half] : v[i];
+      v[i] = df_add(keep, df{__shfl_xor_sync(0xffffffffu, send.h, off), __shfl_xor_sync(0xffffffffu, send.l, off)});
+    }
+  }
+  df t = v[0];
+#pragma unroll
+  for (int o = 16 / V; o >= 1; o /= 2)
+    t = df_add(t, df{__shfl_xor_sync(0xffffffffu, t.h, o), __shfl_xor_sync(0xffffffffu, t.l, o)});
   return t;
 }
 
@@ -310,18 +346,20 @@ __device__ void block_partials(const SArgs& a, const float* v, int nq, int q0, d
 }
 
 // totals of slots [q0, q0 + nq) after a grid barrier, identical in every
-// block.  Warp w sums slots w, w + 8, ...; each round issues the loads of four
-// slots (up to kTotG / 32 per lane and slot) before adding any, so that a
-// round costs one L2 round trip.
+// block.  Warp w sums slots w, w + 8, ...; each round issues the loads of
+// kTotU slots (up to kTotG / 32 per lane and slot) before adding any, so that a
+// round costs one L2 round trip; the kTotU sums leave the warp through one
+// transposing reduction.
 constexpr int kTotG = 160;   // grids up to this size take the one-pass path
+constexpr int kTotU = 4;     // slots per warp and round
 __device__ void grid_totals(const SArgs& a, int q0, int nq, df* out) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int G = gridDim.x;
   if (G <= kTotG) {
-    for (int qb = wid; qb < nq; qb += 4 * kWarps) {
-      float2 t[4][kTotG / 32];
+    for (int qb = wid; qb < nq; qb += kTotU * kWarps) {
+      float2 t[kTotU][kTotG / 32];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
+      for (int u = 0; u < kTotU; u++) {
         const int q = qb + u * kWarps;
         const float2* p = a.partials + (size_t)(q0 + (q < nq ? q : 0)) * G;
 #pragma unroll
@@ -330,15 +368,16 @@ __device__ void grid_totals(const SArgs& a, int q0, int nq, df* out) {
           t[u][i] = (q < nq && g < G) ? __ldcg(p + g) : make_float2(0.f, 0.f);
         }
       }
+      df sv[kTotU];
 #pragma unroll
-      for (int u = 0; u < 4; u++) {
-        df s{t[u][0].x, t[u][0].y};
+      for (int u = 0; u < kTotU; u++) {
+        sv[u] = df{t[u][0].x, t[u][0].y};
 #pragma unroll
-        for (int i = 1; i < kTotG / 32; i++) s = df_add(s, df{t[u][i].x, t[u][i].y});
-        s = df_wsum(s);
-        const int q = qb + u * kWarps;
-        if (lane == 0 && q < nq) out[q] = s;
+        for (int i = 1; i < kTotG / 32; i++) sv[u] = df_add(sv[u], df{t[u][i].x, t[u][i].y});
       }
+      const df s = reduce_df<kTotU>(sv);   // lane l: slot qb + (l >> 3) * kWarps
+      const int q = qb + (lane >> 3) * kWarps;
+      if ((lane & 7) == 0 && q < nq) out[q] = s;
     }
   } else {
     for (int q = wid; q < nq; q += kWarps) {
@@ -427,15 +466,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
     a.r[i] = o;
     a.y[i] = make_float2(0.f, 0.f);
   }, &s_fail);
+  // ||b_r||^2 over the owned rows (written by this block's own items)
+  v[0] = 0.f;
+  for (size_t e = E0 + threadIdx.x; e < E1; e += blockDim.x) {
+    const float2 rr = a.r[e];
+    v[0] = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, v[0]));
+  }
+  block_partials(a, v, 1, RC, sred);
   if (ok) ok = grid_barrier(a.bar, a.abort, target);
   long long its = 0;
   bool done = true;
   df tol2 = df_of(0.f);
   if (ok) {
-    grid_totals(a, RD, 1, tot);
+    grid_totals(a, RC, 2, tot + RC);   // ||b_r||^2 (the running ||r||^2) and ||b||^2
     const df tr = df_of((float)a.tol_rel);
-    tol2 = df_mul(df_mul(tr, tr), tot[0]);
-    done = !(tot[0].h > 0.f);
+    tol2 = df_mul(df_mul(tr, tr), tot[RD]);
+    done = !(tot[RD].h > 0.f);
   }
   while (ok && !done && its < a.maxit) {
     int k = 0;
@@ -455,6 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
       // beta_j = <w_j, w> (warp wid owns j = wid + 8 u, u < 4), ||w||^2, <w, r>
       for (int jb = wid; jb < k; jb += 4 * kWarps) {
         float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
         for (int e = lane; e < E; e += 32) {
           const float2 x = wk[e];
 #pragma unroll
@@ -465,15 +512,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
             im[u] = fmaf(p.x, x.y, fmaf(-p.y, x.x, im[u]));
           }
         }
+        df sv[8];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
-          const int j = jb + u * kWarps;
-          const df sr = df_wsum(df_of(re[u])), si = df_wsum(df_of(im[u]));
-          if (lane == 0 && j < k) {
-            a.partials[(size_t)(RA + 2 * j) * G + bid] = make_float2(sr.h, sr.l);
-            a.partials[(size_t)(RA + 2 * j + 1) * G + bid] = make_float2(si.h, si.l);
-          }
+          sv[2 * u] = df_of(re[u]);
+          sv[2 * u + 1] = df_of(im[u]);
         }
+        const df sr = reduce_df<8>(sv);   // lane l: sum (l >> 2) = 2 u + {re, im}
+        const int j = jb + (lane >> 3) * kWarps;
+        if ((lane & 3) == 0 && j < k) a.partials[(size_t)(RA + 2 * j + ((lane >> 2) & 1)) * G + bid] = make_float2(sr.h, sr.l);
       }
       v[0] = v[1] = v[2] = 0.f;
       for (size_t e = E0 + threadIdx.x; e < E1; e += blockDim.x) {
@@ -482,10 +529,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
         v[1] = fmaf(x.x, rr.x, fmaf(x.y, rr.y, v[1]));
         v[2] = fmaf(x.x, rr.y, fmaf(-x.y, rr.x, v[2]));
       }
-      block_partials(a, v, 3, RB, sred);
+      block_partials(a, v, 3, RA + 2 * k, sred);   // after the beta slots: one pass reads all of them
       if (!(ok = grid_barrier(a.bar, a.abort, target))) break;
-      if (k) grid_totals(a, RA, 2 * k, tot);
-      grid_totals(a, RB, 3, tot + RB);
+      grid_totals(a, RA, 2 * k + 3, tot);
+      {  // move them to their own slots (the ranges may overlap: read all, then write)
+        df moved = df_of(0.f);
+        if (threadIdx.x < 3) moved = tot[2 * k + threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x < 3) tot[RB + threadIdx.x] = moved;
+        __syncthreads();
+      }
       // sum_j |beta_j|^2 (warp 0, lanes over j) and the beta_j as floats
       if (wid == 0) {
         df bb = df_of(0.f);
@@ -508,6 +561,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
         const int gi = threadIdx.x / E, ei = threadIdx.x - gi * E;
         if (gi < ngrp) {
           float swr = 0.f, swi = 0.f, szr = 0.f, szi = 0.f;
+#pragma unroll 4
           for (int j = gi; j < k; j += ngrp) {
             const float2 bj = s_beta[j];
             const float2 p = Wj(j)[ei], q = Zj(j)[ei];
@@ -532,6 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
             x.y -= u.y;
           }
         } else {
+#pragma unroll 4
           for (int j = 0; j < k; j++) {
             const float2 bj = s_beta[j], p = Wj(j)[ei];
             x.x -= bj.x * p.x - bj.y * p.y;
@@ -553,7 +608,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
         if (threadIdx.x == 0) tot[RE] = tot[RB];
         __syncthreads();
       }
-      // gamma = ||w''||, alpha = <w'', r> / gamma
+      // gamma = ||w''||, alpha = <w'', r> / gamma; with w_k = w'' / gamma of
+      // unit norm, ||r - alpha w_k||^2 = ||r||^2 - |alpha|^2 (the running norm)
       if (threadIdx.x == 0) {
         const df g = df_sqrt(tot[RE]);
         const bool gz = !(g.h > 0.f);
@@ -562,6 +618,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
         const df ai = gz ? tot[RB + 2] : df_div(tot[RB + 2], g);
         s_coef[1] = ar.h + ar.l;
         s_coef[2] = ai.h + ai.l;
+        if (!gz) {
+          const df rn = df_add(tot[RC], df_neg(df_add(df_mul(ar, ar), df_mul(ai, ai))));
+          tot[RC] = rn.h > 0.f ? rn : df_of(0.f);
+        }
       }
       __syncthreads();
       // w_k = w'' / gamma, z_k = (r - S_z) / gamma, y += alpha z_k, r -= alpha w_k
@@ -582,6 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
             z.y -= u.y;
           }
         } else {
+#pragma unroll 4
           for (int j = 0; j < k; j++) {
             const float2 bj = s_beta[j], q = Zj(j)[ei];
             z.x -= bj.x * q.x - bj.y * q.y;
@@ -598,11 +659,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
         rr.x -= far * x.x - fai * x.y;
         rr.y -= far * x.y + fai * x.x;
         a.r[e] = rr;
-        v[0] = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, v[0]));
       }
-      block_partials(a, v, 1, RC, sred);
+      // r complete on every block before the next iteration's phase A reads it
       if (!(ok = grid_barrier(a.bar, a.abort, target))) break;
-      grid_totals(a, RC, 1, tot + RC);
       k++;
       its++;
       const df rn2 = tot[RC];
@@ -630,10 +689,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_coarse_gcr_stream(SArgs a) {
       const float2 rr = a.r[e];
       v[0] = fmaf(rr.x, rr.x, fmaf(rr.y, rr.y, v[0]));
     }
-    block_partials(a, v, 1, RD, sred);
+    block_partials(a, v, 1, RC, sred);
     if (!(ok = grid_barrier(a.bar, a.abort, target))) break;
-    grid_totals(a, RD, 1, tot + RD);
-    const df rn2 = tot[RD];
+    grid_totals(a, RC, 1, tot + RC);   // the true ||r||^2 restarts the running norm
+    const df rn2 = tot[RC];
     if (rn2.h <= tol2.h || !(rn2.h == rn2.h)) done = true;
   }
   if (!ok && threadIdx.x == 0) {
