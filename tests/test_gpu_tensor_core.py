@@ -163,3 +163,35 @@ def test_tensor_core_block_solve():
         assert np.linalg.norm((psi[q] - seq[q]).ravel()) / np.linalg.norm(seq[q].ravel()) < 1e-7, q
     assert info.outer_iterations <= 1.3 * sinfo.outer_iterations + 3
     S.close()
+
+
+@pytest.mark.parametrize("store", [1, 2], ids=["fp16", "bf16"])
+@pytest.mark.parametrize("nrhs", [8, 13])
+def test_batched_transfers_match_single(store, nrhs):
+    """The fine-level restriction and prolongation of nrhs right-hand sides in
+    one launch each (one batched cycle, groups of 4 with a ragged last group)
+    against the same cycle done one right-hand side at a time, and against
+    the oracle's cycle on the dequantised operands, with 16-bit P (Nv = 8 on
+    2^4 blocks, even sites) and a right-hand side scaled by 1e-6."""
+    from paper_1011_2775_gb300 import binding as B
+    dims = (8, 8, 8, 8)
+    U = I.make_gauge(dims, 0.25, 5, 0.5, 9401)
+    m0 = -0.3
+    W = WilsonClover(U, 1.0, m0)
+    V0 = [gaussian_vector(9402, 0, k, W.shape, 12) for k in range(8)]
+    cp = dict(tol_coarse=1e-6, maxit_coarse=400, restart_coarse=64, nu_post=0)
+    S = _solver(dims, U, 1.0, m0)
+    S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[8], storage=store, coarse_impl=1, **cp)
+    S.set_null_vectors(0, np.ascontiguousarray(np.stack(V0)))
+    S.setup()
+    mg = Multigrid(W, MGParams(blocks=[(2, 2, 2, 2)], nv=[8], **cp), null_vectors=[V0])
+    mg = _dequantised(S, W, [(2, 2, 2, 2)], [8], [(4, 4, 4, 4)], mg)
+    r = I.gaussian_source(dims, 9403, nrhs=nrhs)
+    r[2] *= 1e-6
+    got = S.apply(B.MG_OP_CYCLE, r, level=0, nrhs=nrhs)
+    for q in range(nrhs):
+        one = S.apply(B.MG_OP_CYCLE, np.ascontiguousarray(r[q]), level=0)
+        assert rel(got[q], one) <= 1e-5, q
+        ref = mg.cycle(0, r[q].reshape(W.shape + (12,)) * W.even).reshape(r[q].shape)
+        assert rel(got[q], ref) <= 1e-4, q
+    S.close()
