@@ -139,6 +139,10 @@ void precondition_all(std::vector<Run*>& runs, int k) {
                     a.restart_coarse == b.restart_coarse && a.maxit_coarse == b.maxit_coarse;
     (ok ? shared : alone).push_back(R);
   }
+  if (shared.size() == 1) {   // one context: its own batched coarse solve (timed against one-by-one solves)
+    alone.push_back(shared[0]);
+    shared.clear();
+  }
   for (Run* R : runs) {
     float* zk = R->B->Z[k].as<float>();
     float* r32 = R->B->r32.as<float>();

@@ -204,15 +204,30 @@ __device__ void msites(const MArgs& A, unsigned mask, int* plist, int links, int
     const float* scale = folded ? nullptr : g.Ys;
     const int per = nb * nc;
     const int rpw = (nc + nw - 1) / nw;
-    for (int t = threadIdx.x; t < np * per; t += blockDim.x) {
-      const int q = t / per, rem = t % per, d = rem / nc, j = rem % nc;
-      const float2* inp = vec_ptr(A, in, plist[q]);
-      float2 x = d < 8 ? inp[(size_t)g.nbr[(size_t)s * 8 + d] * nc + j] : inp[(size_t)s * nc + j];
-      if (scale) {
-        const float sc = scale[(size_t)s * 8 + d];
-        x = make_float2(sc * x.x, sc * x.y);
+    {  // four elements per thread and round: indices, then loads, in flight together
+      constexpr int U = 4;
+      const int total = np * per;
+      for (int t0 = threadIdx.x; t0 < total; t0 += U * blockDim.x) {
+        const float2* src[U];
+        float sc[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int t = t0 + u * blockDim.x;
+          const int tt = t < total ? t : 0;
+          const int q = tt / per, rem = tt % per, d = rem / nc, j = rem % nc;
+          const float2* inp = vec_ptr(A, in, plist[q]);
+          src[u] = d < 8 ? inp + (size_t)g.nbr[(size_t)s * 8 + d] * nc + j : inp + (size_t)s * nc + j;
+          sc[u] = scale ? scale[(size_t)s * 8 + d] : 1.f;
+        }
+        float2 x[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) x[u] = *src[u];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          const int t = t0 + u * blockDim.x;
+          if (t < total) sm[t] = make_float2(sc[u] * x[u].x, sc[u] * x[u].y);
+        }
       }
-      sm[t] = x;
     }
     __syncthreads();
     for (int q0 = 0; q0 < np; q0 += kPB) {

@@ -155,21 +155,41 @@ __device__ void gather(const TArgs& a, int site, const float2* in, size_t instri
                        unsigned* gv) {
   const int nc = a.nc, K = 8 * nc;
   const int total = NB * K;
-  for (int q = threadIdx.x; q < total; q += blockDim.x) {
-    const int p = q / K, rem = q - p * K, d = rem / nc, j = rem - d * nc;
-    unsigned hi = 0u, lo = 0u;
-    if (p < a.nb) {
-      float2 v = __ldcg(in + (size_t)p * instride + (size_t)(a.nbr[(size_t)site * 8 + d] - nbase) * nc + j);
-      const float f = a.Ys[(size_t)site * 8 + d] * sc[p];
-      v.x *= f;
-      v.y *= f;
-      const __half2 h = __floats2half2_rn(v.x, v.y);
-      const float2 hf = __half22float2(h);
-      hi = h2_bits(h);
-      lo = h2_bits(__floats2half2_rn(v.x - hf.x, v.y - hf.y));
+  // four elements per thread and round: their indices and scales, then their
+  // loads, are in flight together
+  constexpr int U = 4;
+  for (int q0 = threadIdx.x; q0 < total; q0 += U * blockDim.x) {
+    size_t src[U];
+    float f[U];
+    bool live[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int q = q0 + u * blockDim.x;
+      const int qq = q < total ? q : 0;
+      const int p = qq / K, rem = qq - p * K, d = rem / nc, j = rem - d * nc;
+      live[u] = q < total && p < a.nb;
+      src[u] = live[u] ? (size_t)p * instride + (size_t)(a.nbr[(size_t)site * 8 + d] - nbase) * nc + j : 0;
+      f[u] = live[u] ? a.Ys[(size_t)site * 8 + d] * sc[p] : 0.f;
     }
-    gv[(size_t)p * a.pitch + rem] = hi;
-    gv[((size_t)NB + p) * a.pitch + rem] = lo;
+    float2 v[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) v[u] = live[u] ? __ldcg(in + src[u]) : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int q = q0 + u * blockDim.x;
+      if (q >= total) continue;
+      const int p = q / K, rem = q - p * K;
+      unsigned hi = 0u, lo = 0u;
+      if (live[u]) {
+        const float2 x = make_float2(v[u].x * f[u], v[u].y * f[u]);
+        const __half2 h = __floats2half2_rn(x.x, x.y);
+        const float2 hf = __half22float2(h);
+        hi = h2_bits(h);
+        lo = h2_bits(__floats2half2_rn(x.x - hf.x, x.y - hf.y));
+      }
+      gv[(size_t)p * a.pitch + rem] = hi;
+      gv[((size_t)NB + p) * a.pitch + rem] = lo;
+    }
   }
   __syncthreads();
 }

@@ -89,6 +89,9 @@ struct LevelWork {
   DBuf res, w, e, z0;      // this level's half vectors for smoothing
   int coarse_impl = -1;    // coarsest level: persistent solver chosen by the autotuner (-1: not yet)
   DBuf tune_iters;         // iteration counter of the tuning runs
+  // coarsest level of a batched cycle of nb systems: 0 the batched launches,
+  // 1 one single-system solve after another (-1: not yet timed)
+  int batch_impl[17] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 };
 
 // level-0 temporaries of the batched cycle (allocated for up to `cap` rhs)
@@ -707,13 +710,44 @@ void mg_batch_coarse(Ctx* c, int nb) {
     const LevelGeom& G1 = b.H.geo[1];
     const CoarseOp& C1 = b.H.cop[1];
     const bool tc = b.p.coarse_impl == 0 || b.p.coarse_impl == 4;
-    for (int q0 = 0; q0 < nb; q0 += gmax) {
-      std::vector<CoarseSystem> part(sys.begin() + q0, sys.begin() + std::min(nb, q0 + gmax));
-      // tensor cores for FP16 links (the group's systems are consecutive vectors of this context)
-      if (tc && coarse_gcr_tc_try(part, b.H.work[1].cg, restart, b.p.maxit_coarse, c->ws.flags.as<int>(), b.s))
-        continue;
-      coarse_gcr_solve_multi(part, b.H.work[1].cg, restart, b.p.maxit_coarse, c->ws.flags.as<int>(), b.s);
+    auto batched = [&]() {
+      for (int q0 = 0; q0 < nb; q0 += gmax) {
+        std::vector<CoarseSystem> part(sys.begin() + q0, sys.begin() + std::min(nb, q0 + gmax));
+        // tensor cores for FP16 links (the group's systems are consecutive vectors of this context)
+        if (tc && coarse_gcr_tc_try(part, b.H.work[1].cg, restart, b.p.maxit_coarse, c->ws.flags.as<int>(), b.s))
+          continue;
+        coarse_gcr_solve_multi(part, b.H.work[1].cg, restart, b.p.maxit_coarse, c->ws.flags.as<int>(), b.s);
+      }
+    };
+    auto one_by_one = [&]() {   // the single-system solver the autotuner chose for this level
+      for (int q = 0; q < nb; q++)
+        coarse_solve(c, b.H, 1, b.H.bw.ec.as<float>() + q * b.cs, b.H.bw.rc.as<float>() + q * b.cs);
+    };
+    int& choice = b.H.work[1].batch_impl[std::min(nb, 16)];
+    if (choice < 0) {
+      if (b.p.coarse_impl != 0) {
+        choice = 0;   // a forced implementation keeps the batched launches
+      } else {
+        // time both on the real systems; the tuning runs leave the iteration counters as they were
+        long long* d_it = b.H.d_iters.as<long long>();
+        DBuf keep(sizeof(long long) * MG_MAX_LEVELS);
+        MG_CUDA(cudaMemcpyAsync(keep.get(), d_it, sizeof(long long) * MG_MAX_LEVELS, cudaMemcpyDeviceToDevice, b.s));
+        choice = tuned_block(TuneKey{"coarse_batch", {G1.L[0], G1.L[1], G1.L[2], G1.L[3]}, nb, C1.store}, {0, 1},
+                             [&](int which) {
+                               if (which)
+                                 one_by_one();
+                               else
+                                 batched();
+                             },
+                             b.s);
+        MG_CUDA(cudaMemcpyAsync(d_it, keep.get(), sizeof(long long) * MG_MAX_LEVELS, cudaMemcpyDeviceToDevice, b.s));
+        MG_CUDA(cudaStreamSynchronize(b.s));
+      }
     }
+    if (choice == 1)
+      one_by_one();
+    else
+      batched();
   } else {
     for (int q = 0; q < nb; q++)
       coarse_solve(c, b.H, 1, b.H.bw.ec.as<float>() + q * b.cs, b.H.bw.rc.as<float>() + q * b.cs);
@@ -831,7 +865,10 @@ bool mg_precondition_graph(Ctx* c, float* z_e, const double* r_e, float* r32) {
 
 void mg_solve_params_changed(Ctx* c) {
   if (!c->mg) return;
-  for (LevelWork& W : c->mg->work) W.coarse_impl = -1;   // choose (or force) the coarsest solver again
+  for (LevelWork& W : c->mg->work) {   // choose (or force) the coarsest solver again
+    W.coarse_impl = -1;
+    for (int& v : W.batch_impl) v = -1;
+  }
   if (!c->mg->graph.exec) return;
   MG_CUDA(cudaStreamSynchronize(c->stream));   // no replay in flight
   c->mg->graph.drop();
