@@ -64,7 +64,7 @@ REFERENCE_OUTER_PER_SOLVE = 42
 DSLASH_TRAFFIC_BYTES = 1.125e9
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the streamed
 # coarsest-level solve on this workload (None whenever that kernel changes)
-COARSE_TRAFFIC_BYTES = 79.52e6        # profiles/coarse_gcr_stream_4x4x4x8.md: 76.88 MB read + 2.64 MB written
+COARSE_TRAFFIC_BYTES = 79.13e6        # profiles/coarse_gcr_stream_4x4x4x8.md: 76.46 MB read + 2.67 MB written
                                       # per launch of COARSE_PROFILE_ITERS iterations (the links' first touch
                                       # after the fine-level work; L2 hits afterwards)
 DSLASH_FLOPS_PER_SITE = 1824        # fused hop + clover inverse, per output site
