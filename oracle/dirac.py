@@ -196,8 +196,22 @@ def field_strength(U: np.ndarray, mu: int, nu: int) -> np.ndarray:
     return f - tr[..., None, None] * np.eye(3)
 
 
-def clover_matrix(U: np.ndarray, csw: float, m0: float) -> np.ndarray:
-    """``A(x)`` as a 12x12 matrix per site, index ``3*spin + colour``."""
+def plane_csw(mu: int, nu: int, csw: float, csw_t: float) -> float:
+    """Clover coefficient of the (mu, nu) plane: ``csw_t`` when it contains t
+    (direction 3), ``csw`` for the spatial planes."""
+    return csw_t if 3 in (mu, nu) else csw
+
+
+def clover_matrix(U: np.ndarray, csw: float, m0: float, weights=(1.0, 1.0, 1.0, 1.0), csw_t=None) -> np.ndarray:
+    """``A(x)`` as a 12x12 matrix per site, index ``3*spin + colour``.
+
+    Isotropic: ``A = (4 + m0) + csw (i/4) sum_{mu != nu} sigma_{mu nu} F_{mu nu}``.
+    Anisotropic reading (the paper's lattices are anisotropic but it writes no
+    operator down): the mass term becomes ``sum_mu w_mu + m0`` with the hopping
+    weights ``w_mu`` of the directions, and the planes containing t take
+    ``csw_t`` instead of ``csw``; both reduce to the isotropic form at
+    ``w = 1``, ``csw_t = csw``."""
+    csw_t = csw if csw_t is None else csw_t
     shp = U.shape[:4]
     A = np.zeros(shp + (4, 3, 4, 3), dtype=np.complex128)
     for mu in range(4):
@@ -205,27 +219,35 @@ def clover_matrix(U: np.ndarray, csw: float, m0: float) -> np.ndarray:
             if mu == nu:
                 continue
             F = field_strength(U, mu, nu)
-            A += (csw * 0.25j) * np.einsum("st,...ab->...satb", sigma(mu, nu), F)
+            A += (plane_csw(mu, nu, csw, csw_t) * 0.25j) * np.einsum("st,...ab->...satb", sigma(mu, nu), F)
     A = A.reshape(shp + (12, 12))
-    A += (4.0 + m0) * np.eye(12)
+    A += (sum(weights) + m0) * np.eye(12)
     return A
 
 
 # ----------------------------------------------------------------------------- fine level
 class WilsonClover(LatticeLevel):
     """The fine Wilson-clover operator for gauge field ``U`` (library layout
-    ``(Lt, Lz, Ly, Lx, 4, 3, 3)``), clover coefficient ``csw`` and bare mass ``m0``."""
+    ``(Lt, Lz, Ly, Lx, 4, 3, 3)``), clover coefficient ``csw`` and bare mass ``m0``.
+
+    ``weights`` (hopping weight per direction x, y, z, t) and ``csw_t`` (clover
+    coefficient of the planes containing t) give the anisotropic reading of
+    ``clover_matrix``: every hop in direction mu carries ``w_mu``; the defaults
+    are the isotropic operator."""
 
     ndof = 12
 
-    def __init__(self, U: np.ndarray, csw: float, m0: float, antiperiodic_t: bool = True):
+    def __init__(self, U: np.ndarray, csw: float, m0: float, antiperiodic_t: bool = True, weights=None,
+                 csw_t=None):
         lt, lz, ly, lx = U.shape[:4]
         super().__init__((lx, ly, lz, lt))
         self.U = U
         self.csw = float(csw)
+        self.csw_t = float(csw) if csw_t is None else float(csw_t)
+        self.w = (1.0, 1.0, 1.0, 1.0) if weights is None else tuple(float(v) for v in weights)
         self.m0 = float(m0)
         self.apbc = antiperiodic_t
-        self.A = clover_matrix(U, csw, m0)
+        self.A = clover_matrix(U, csw, m0, self.w, self.csw_t)
         self.Ainv = np.linalg.inv(self.A)
         one = np.eye(4, dtype=np.complex128)
         self.proj_minus = [one - GAMMA[mu] for mu in range(4)]
@@ -238,11 +260,11 @@ class WilsonClover(LatticeLevel):
         if d < 4:
             nb = shift(psi, mu, +1, self.apbc)
             c = np.einsum("...ab,...sb->...sa", self.U[..., mu, :, :], nb)
-            out = -0.5 * np.einsum("st,...ta->...sa", self.proj_minus[mu], c)
+            out = (-0.5 * self.w[mu]) * np.einsum("st,...ta->...sa", self.proj_minus[mu], c)
         else:
             nb = shift(psi, mu, -1, self.apbc)
             c = np.einsum("...ba,...sb->...sa", np.conj(self.Ub[mu]), nb)
-            out = -0.5 * np.einsum("st,...ta->...sa", self.proj_plus[mu], c)
+            out = (-0.5 * self.w[mu]) * np.einsum("st,...ta->...sa", self.proj_plus[mu], c)
         return out.reshape(self.shape + (12,))
 
     def M(self, v):

@@ -36,7 +36,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .dirac import GAMMA, WilsonClover, dag, shift, sigma
+from .dirac import GAMMA, WilsonClover, dag, plane_csw, shift, sigma
 
 
 def _at(f: np.ndarray, disp) -> np.ndarray:
@@ -111,7 +111,7 @@ def link_derivative(W: WilsonClover, lam: np.ndarray, psi: np.ndarray) -> np.nda
         M = np.einsum("...tb,st,...sa->...ba", nb, one - GAMMA[mu], np.conj(lam4))
         nbm = shift(psi4, mu, -1, W.apbc)                      # psi(y-mu) with the boundary sign
         N = np.einsum("...sa,st,...tb->...ab", lam4, np.conj(one + GAMMA[mu]), np.conj(nbm))
-        K[..., mu, :, :] += 0.5 * M + 0.5 * shift(N, mu, +1)
+        K[..., mu, :, :] += (0.5 * W.w[mu]) * M + (0.5 * W.w[mu]) * shift(N, mu, +1)   # the direction's weight
 
     # Clover term: -Re lam^dag dA psi with dA = csw (i/4) sum_{mu != nu} sigma_{mu nu} x dF_{mu nu}.
     #   lam^dag (sigma x dF) psi = tr(dF S),  S_ba = sum_st sigma_st psi_{t b} conj(lam_{s a}),
@@ -126,7 +126,7 @@ def link_derivative(W: WilsonClover, lam: np.ndarray, psi: np.ndarray) -> np.nda
             if mu == nu:
                 continue
             S = np.einsum("st,...tb,...sa->...ba", sigma(mu, nu), psi4, np.conj(lam4))
-            C = -(0.25j * W.csw) * S
+            C = -(0.25j * plane_csw(mu, nu, W.csw, W.csw_t)) * S
             C0 = C - (np.trace(C, axis1=-2, axis2=-1) / 3.0)[..., None, None] * eye3
             Wm = (C0 - dag(C0)) / 8.0
             for factors in leaf_factors(mu, nu):

@@ -209,3 +209,84 @@ def test_dr_adjoint_through_gamma5_and_clover():
     assert np.abs(got.ravel()[ev] - ref).max() < 1e-12 * np.abs(ref).max()
     # and D_r itself is not normal here, so the check has teeth
     assert np.abs(Dr @ Dr.conj().T - Dr.conj().T @ Dr).max() > 1e-3
+
+
+# ----------------------------------------------------------------------------- anisotropic reading
+AW = (0.45, 0.7, 1.25, 2.0)   # hopping weights x, y, z, t (all different: a transposed index fails)
+
+
+def test_anisotropic_free_field_plane_wave():
+    """The anisotropic reading at U = 1: D e^{ipx} u = [m0 + sum_mu w_mu (1 - cos p_mu)
+    + i sum_mu w_mu gamma_mu sin p_mu] e^{ipx} u (the clover term vanishes)."""
+    dims = (4, 6, 2, 8)
+    lx, ly, lz, lt = dims
+    m0 = -0.15
+    W = WilsonClover(I.unit_gauge(dims), 1.1, m0, weights=AW, csw_t=0.6)
+    rng = np.random.default_rng(5)
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in (lt, lz, ly, lx)], indexing="ij")
+    for n in [(0, 0, 0, 0), (1, 2, 1, 3), (3, 5, 1, 6)]:
+        p = [2 * np.pi * n[0] / lx, 2 * np.pi * n[1] / ly, 2 * np.pi * n[2] / lz, 2 * np.pi * (n[3] + 0.5) / lt]
+        u = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        phase = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+        psi = phase[..., None, None] * u
+        Dk = (m0 + sum(AW[m] * (1 - np.cos(p[m])) for m in range(4))) * np.eye(4) + \
+            1j * sum(AW[m] * GT[m] * np.sin(p[m]) for m in range(4))
+        expect = phase[..., None, None] * (Dk @ u)
+        got = W.D(psi.reshape(W.shape + (12,))).reshape(expect.shape)
+        assert np.abs(got - expect).max() < 1e-13
+
+
+def test_anisotropic_reading_reduces_to_isotropic():
+    """Unit weights and csw_t = csw give exactly the isotropic operator."""
+    dims = (4, 4, 4, 4)
+    U = I.make_gauge(dims, 0.4, 1, 0.5, 51)
+    W = WilsonClover(U, 1.3, -0.2)
+    Wa = WilsonClover(U, 1.3, -0.2, weights=(1.0, 1.0, 1.0, 1.0), csw_t=1.3)
+    psi = _vec(dims, 52)
+    assert np.array_equal(W.A, Wa.A)
+    assert np.array_equal(W.D(psi), Wa.D(psi))
+    # and a non-trivial anisotropy changes it
+    Wb = WilsonClover(U, 1.3, -0.2, weights=AW, csw_t=0.7)
+    assert np.abs(Wb.D(psi) - W.D(psi)).max() > 1e-2
+
+
+def test_anisotropic_gamma5_hermiticity_and_covariance():
+    """gamma_5-hermiticity and gauge covariance hold for the anisotropic reading."""
+    dims = (4, 4, 2, 6)
+    U = I.make_gauge(dims, 0.5, 0, 0.5, 53)
+    W = WilsonClover(U, 1.2, -0.3, weights=AW, csw_t=0.8)
+    phi, psi = _vec(dims, 54), _vec(dims, 55)
+    lhs = inner(phi, W.D(psi))
+    assert abs(lhs - inner(W.gamma5(W.D(W.gamma5(phi))), psi)) / abs(lhs) < 1e-14
+    G = I.random_gauge_transform(dims, 56)
+    UG = np.empty_like(U)
+    for mu in range(4):
+        Gp = np.roll(G, -1, axis=3 - mu)
+        UG[..., mu, :, :] = G @ U[..., mu, :, :] @ np.conj(np.swapaxes(Gp, -1, -2))
+    WG = WilsonClover(UG, 1.2, -0.3, weights=AW, csw_t=0.8)
+    p4 = psi.reshape(psi.shape[:-1] + (4, 3))
+    Gpsi = np.einsum("...ab,...sb->...sa", G, p4)
+    lhs = WG.D(Gpsi.reshape(W.shape + (12,))).reshape(p4.shape)
+    rhs = np.einsum("...ab,...sb->...sa", G, W.D(psi).reshape(p4.shape))
+    assert np.abs(lhs - rhs).max() < 1e-13
+
+
+@pytest.mark.parametrize("plane", [(0, 1), (2, 3)])
+def test_anisotropic_clover_constant_abelian_field(plane):
+    """The constant-flux closed form with the plane's own coefficient and the
+    weighted mass term: A = (sum w + m0) - (c/2) sin(B) sigma_{mu nu} x diag(1, -1, 0),
+    c = csw for a spatial plane and csw_t for a plane containing t."""
+    mu, nu = plane
+    dims = (4, 4, 4, 4)
+    m0, csw, csw_t = -0.1, 1.3, 0.55
+    B = 2 * np.pi / dims[mu]
+    U = I.unit_gauge(dims)
+    t, z, y, x = np.meshgrid(*[np.arange(n) for n in I.lattice_shape(dims)], indexing="ij")
+    th = B * (x, y, z, t)[mu]
+    U[..., nu, 0, 0] = np.exp(1j * th)
+    U[..., nu, 1, 1] = np.exp(-1j * th)
+    W = WilsonClover(U, csw, m0, weights=AW, csw_t=csw_t)
+    c = csw_t if 3 in plane else csw
+    sig = 0.5j * (GT[mu] @ GT[nu] - GT[nu] @ GT[mu])
+    expect = (sum(AW) + m0) * np.eye(12) - 0.5 * c * np.sin(B) * np.kron(sig, np.diag([1.0, -1.0, 0.0]))
+    assert np.abs(W.A - expect).max() < 1e-14

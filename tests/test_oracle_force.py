@@ -40,13 +40,19 @@ def test_leaf_factors_match_plaquette_leaves(mu, nu):
     assert np.abs(got - plaquette_leaves(U, mu, nu)).max() < 1e-13
 
 
+ANISO = dict(weights=(0.45, 0.7, 1.25, 2.0), csw_t=0.6)
+
+
+@pytest.mark.parametrize("aniso", [False, True], ids=["iso", "aniso"])
 @pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 2, 6)])
-def test_link_derivative_exact_single_link(dims):
+def test_link_derivative_exact_single_link(dims, aniso):
     """-Re<lam, (D(U + dU) - D(U)) psi> = Re tr(dU K) for a change of one link,
-    for arbitrary complex dU (not only su(3) directions), every term of D."""
+    for arbitrary complex dU (not only su(3) directions), every term of D; also
+    for the anisotropic reading (weighted hops, csw_t on the planes with t)."""
     U = I.make_gauge(dims, 0.6, 1, 0.5, 41)
     csw, m0 = 1.3, -0.15
-    W = WilsonClover(U, csw, m0)
+    kw = ANISO if aniso else {}
+    W = WilsonClover(U, csw, m0, **kw)
     lam, psi = _lv(dims, 42), _lv(dims, 43)
     K = F.link_derivative(W, lam, psi)
     base = W.D(psi)
@@ -59,7 +65,7 @@ def test_link_derivative_exact_single_link(dims):
         dU = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
         U2 = U.copy()
         U2[site + (mu,)] += dU
-        W2 = WilsonClover(U2, csw, m0)
+        W2 = WilsonClover(U2, csw, m0, **kw)
         lhs = -np.vdot(lam.ravel(), (W2.D(psi) - base).ravel()).real
         rhs = np.trace(dU @ K[site + (mu,)]).real
         worst = max(worst, abs(lhs - rhs) / max(abs(lhs), 1e-300))
