@@ -227,6 +227,21 @@ MG_API int mg_load_gauge(void* ctx, const void* U, int where);
  * 1e-12 of its largest entry). */
 MG_API int mg_set_clover(void* ctx, double csw, double m0);
 
+/* The anisotropic Wilson-clover operator (section "Results": the lattices
+ * are anisotropic clover lattices; the paper gives no formula, so this is a
+ * stated reading).  Every hop in direction mu is scaled by the weight w[mu]
+ * (x, y, z, t), the diagonal mass term becomes w[0]+w[1]+w[2]+w[3] + m0 in
+ * place of 4 + m0, and the clover coefficient is csw_t on the three planes
+ * that contain t and csw_s on the three spatial planes.  At w = (1,1,1,1)
+ * and csw_t = csw_s the operator is the isotropic one of mg_set_clover, bit
+ * for bit (mg_set_clover calls this).  The solver, the setup, the
+ * multigrid hierarchy (built by Galerkin projection of this operator) and
+ * mg_force (the weighted hops and per-plane coefficients differentiated)
+ * all use the result.  `w` is host memory, four doubles, copied.  Errors:
+ * MG_ERR_ARG (w NULL, a weight not finite or not > 0, csw or m0 not
+ * finite), MG_ERR_STATE (no gauge), MG_ERR_SINGULAR_CLOVER. */
+MG_API int mg_set_clover_aniso(void* ctx, const double w[4], double csw_s, double csw_t, double m0);
+
 /* Set multigrid parameters (copied).  Invalidates the setup (and any
  * injected null vectors) when a field the setup depends on changes: levels,
  * block, nv, setup_iters, setup_inner, setup_rq_tol, restart_coarse, storage,

@@ -37,7 +37,7 @@ MG_FORCE_SU3, MG_FORCE_WIRTINGER, MG_FORCE_FP32 = 0, 1, 16
 MG_KERNEL_DSLASH_CLOVER, MG_KERNEL_DSLASH_XPAY, MG_KERNEL_DR, MG_KERNEL_COARSE_DR, MG_KERNEL_RESTRICT, MG_KERNEL_PROLONG = range(6)
 
 EXPORTED = ["mg_strerror", "mg_last_error", "mg_default_params", "mg_create", "mg_destroy", "mg_load_gauge",
-            "mg_set_clover", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
+            "mg_set_clover", "mg_set_clover_aniso", "mg_set_params", "mg_get_params", "mg_setup", "mg_set_null_vectors", "mg_get_null_vectors",
             "mg_get_coarse_links", "mg_save_setup", "mg_load_setup", "mg_update_mass", "mg_adapt_setup", "mg_solve", "mg_solve_batch",
             "mg_solve_dagger", "mg_force", "mg_apply", "mg_apply_noalloc", "mg_benchmark_kernel", "mg_benchmark_kernel_nrhs",
             "mg_benchmark_coarse_solve", "mg_benchmark_coarse_floor", "mg_benchmark_fma",
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
             "mg_destroy": [vp],
             "mg_load_gauge": [vp, vp, ip],
             "mg_set_clover": [vp, dp, dp],
+            "mg_set_clover_aniso": [vp, ctypes.POINTER(dp), dp, dp, dp],
             "mg_set_params": [vp, ctypes.POINTER(mg_params)],
             "mg_get_params": [vp, ctypes.POINTER(mg_params)],
             "mg_setup": [vp, ctypes.POINTER(mg_setup_info)],
@@ -206,6 +207,11 @@ def mg_load_gauge(ctx, U) -> None:
 
 def mg_set_clover(ctx, csw: float, m0: float) -> None:
     _check(lib().mg_set_clover(ctx, float(csw), float(m0)), "mg_set_clover")
+
+
+def mg_set_clover_aniso(ctx, weights, csw_s: float, csw_t: float, m0: float) -> None:
+    w = (ctypes.c_double * 4)(*[float(x) for x in weights])
+    _check(lib().mg_set_clover_aniso(ctx, w, float(csw_s), float(csw_t), float(m0)), "mg_set_clover_aniso")
 
 
 def mg_set_params(ctx, params: mg_params) -> None:

@@ -215,6 +215,7 @@ int mg_create(void** ctx_out, const int dims[4], int device, void* cuda_stream) 
     c->g.Vh = (int)c->Vh;
     c->g.xh = dims[0] / 2;
     c->g.apbc = 1;
+    for (int m = 0; m < 4; m++) c->g.w[m] = 1.0;
     c->ws.init();
     mg_default_params(&c->params);
     *ctx_out = c.release();
@@ -254,10 +255,19 @@ int mg_load_gauge(void* ctx, const void* U, int where) {
 }
 
 int mg_set_clover(void* ctx, double csw, double m0) {
+  const double w[4] = {1.0, 1.0, 1.0, 1.0};
+  return mg_set_clover_aniso(ctx, w, csw, csw, m0);
+}
+
+int mg_set_clover_aniso(void* ctx, const double* w, double csw_s, double csw_t, double m0) {
   return guarded([&]() {
     mg::Ctx* c = as_ctx(ctx);
     if (!c->have_gauge) mg::raise(MG_ERR_STATE, "load the gauge field first");
-    if (!std::isfinite(csw) || !std::isfinite(m0)) mg::raise(MG_ERR_ARG, "non-finite csw or m0");
+    if (!w) mg::raise(MG_ERR_ARG, "null hopping weights");
+    for (int m = 0; m < 4; m++)
+      if (!(std::isfinite(w[m]) && w[m] > 0)) mg::raise(MG_ERR_ARG, "hopping weights must be positive and finite");
+    if (!std::isfinite(csw_s) || !std::isfinite(csw_t) || !std::isfinite(m0)) mg::raise(MG_ERR_ARG, "non-finite csw or m0");
+    const double csw = csw_s;
     if (!c->clov64.get()) {
       c->clov64.alloc(sizeof(double) * 144 * c->Vh);
       c->clovinv64.alloc(sizeof(double) * 144 * c->Vh);
@@ -266,10 +276,13 @@ int mg_set_clover(void* ctx, double csw, double m0) {
     }
     c->mg.reset();
     c->have_clover = false;
-    mg::build_clover(c->g, c->gauge64.as<double>(), csw, m0, c->clov64.as<double>(), c->clovinv64.as<double>(),
-                     c->clov32.as<float>(), c->clovinv32.as<float>(), c->ws.flags.as<int>(), c->stream);
+    for (int m = 0; m < 4; m++) c->g.w[m] = w[m];   // every later hop of this context carries the weights
+    mg::build_clover(c->g, c->gauge64.as<double>(), mg::CloverCoef{csw_s, csw_t}, m0, c->clov64.as<double>(),
+                     c->clovinv64.as<double>(), c->clov32.as<float>(), c->clovinv32.as<float>(),
+                     c->ws.flags.as<int>(), c->stream);
     if (c->read_flag(mg::FLAG_SINGULAR, true)) mg::raise(MG_ERR_SINGULAR_CLOVER, "singular clover block");
     c->csw = csw;
+    c->csw_t = csw_t;
     c->m0 = m0;
     c->have_clover = true;
     return MG_OK;
@@ -398,7 +411,7 @@ int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where) {
 
 // ---- setup reuse (the paper saves null vectors and coarse operators for later use)
 namespace {
-constexpr char kSetupMagic[8] = {'M', 'G', 'C', 'L', 'S', 'E', 'T', '2'};
+constexpr char kSetupMagic[8] = {'M', 'G', 'C', 'L', 'S', 'E', 'T', '3'};
 
 struct SetupHeader {
   char magic[8];
@@ -406,6 +419,7 @@ struct SetupHeader {
   mg_params params;
   double csw, m0;
   int32_t levels;
+  double w[4], csw_t;   // hopping weights and the temporal clover coefficient
 };
 
 // the raw null vectors of every transfer of the current setup, complex128 on the host
@@ -443,6 +457,8 @@ int mg_save_setup(void* ctx, const char* path) {
     h.params = c->params;
     h.csw = c->csw;
     h.m0 = c->m0;
+    for (int m = 0; m < 4; m++) h.w[m] = c->g.w[m];
+    h.csw_t = c->csw_t;
     h.levels = c->params.levels;
     std::vector<std::vector<double>> vecs = current_vectors(c);
     std::FILE* f = std::fopen(path, "wb");
@@ -526,7 +542,8 @@ int mg_update_mass(void* ctx, double m0, mg_setup_info* info) {
     if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
     if (!std::isfinite(m0)) mg::raise(MG_ERR_ARG, "non-finite m0");
     std::vector<std::vector<double>> vecs = current_vectors(c);
-    const int st = mg_set_clover(ctx, c->csw, m0);
+    const double w[4] = {c->g.w[0], c->g.w[1], c->g.w[2], c->g.w[3]};
+    const int st = mg_set_clover_aniso(ctx, w, c->csw, c->csw_t, m0);
     if (st != MG_OK) return st;
     rebuild_from(c, vecs, info);
     if (info)

@@ -76,10 +76,11 @@ __device__ __forceinline__ cx<T> cfma_conj(cx<T> a, cx<T> b, cx<T> acc) {
 
 // --------------------------------------------------------------------------- geometry
 struct Geom {
-  int L[4];   // Lx, Ly, Lz, Lt (all even on the fine level)
-  int Vh;     // half volume
-  int xh;     // Lx / 2
-  int apbc;   // 1: antiperiodic fermion boundary in t
+  int L[4];      // Lx, Ly, Lz, Lt (all even on the fine level)
+  int Vh;        // half volume
+  int xh;        // Lx / 2
+  int apbc;      // 1: antiperiodic fermion boundary in t
+  double w[4];   // hopping weight of each direction (1 everywhere: the isotropic operator)
 };
 
 // Coordinates of checkerboard index `cb` of parity `par`.

@@ -23,7 +23,9 @@
 // every site ([parity][plane][9][Vh]); k_force_links computes K (or the
 // force) of every link and writes it in the ABI gauge layout (complex128).
 // Both run in FP64 or, on request, in FP32 (FP32 gauge copy, vectors and W,
-// FP32 arithmetic; the result is widened to complex128 on output).
+// FP32 arithmetic; the result is widened to complex128 on output).  With the
+// anisotropic reading every hop carries its direction's weight w_mu and the
+// planes containing t their own clover coefficient csw_t.
 #include <cstring>
 
 #include "internal.h"
@@ -144,7 +146,7 @@ __device__ __forceinline__ void w_at(const Geom& g, const typename V2of<T>::type
 // W_{mu nu}(x) for the six planes mu < nu of every site.
 template <typename T>
 __global__ void __launch_bounds__(128) k_force_insertion(Geom g, const T* lam_e, const T* lam_o, const T* psi_e,
-                                                         const T* psi_o, T csw, typename V2of<T>::type* W) {
+                                                         const T* psi_o, T csw, T csw_t, typename V2of<T>::type* W) {
   typedef cx<T> cd;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * g.Vh) return;
@@ -153,9 +155,9 @@ __global__ void __launch_bounds__(128) k_force_insertion(Geom g, const T* lam_e,
   cd lam[12], psi[12];
   SpinorIO<T>::load(par ? lam_o : lam_e, g.Vh, i, lam);
   SpinorIO<T>::load(par ? psi_o : psi_e, g.Vh, i, psi);
-  const T q = (T)-0.25 * csw;   // C = -(i csw/4) S = q * (i S)
   for (int mu = 0; mu < 4; mu++)
     for (int nu = mu + 1; nu < 4; nu++) {
+      const T q = (T)-0.25 * (nu == 3 ? csw_t : csw);   // C = -(i c_{mu nu}/4) S = q * (i S)
       cd gn[12], gmn[12];
       gamma_dyn(nu, psi, gn);
       gamma_dyn(mu, gn, gmn);            // sigma_{mu nu} psi = i gamma_mu gamma_nu psi
@@ -206,7 +208,8 @@ __global__ void __launch_bounds__(128) k_force_links(Geom g, const T* lam_e, con
     int y[4] = {x[0], x[1], x[2], x[3]};
     step(g, y, mu, +1);
     const int j = cb_index(g, y);
-    const T sgn = (mu == 3 && g.apbc && x[3] == g.L[3] - 1) ? (T)-1 : (T)1;
+    // boundary sign times the direction's hopping weight
+    const T sgn = ((mu == 3 && g.apbc && x[3] == g.L[3] - 1) ? (T)-1 : (T)1) * (T)g.w[mu];
     cd a[12], b[12], ga[12];
     // first outer product: psi(x+mu) against (1 - gamma) lam(x)
     SpinorIO<T>::load(par ? lam_o : lam_e, g.Vh, i, a);
@@ -361,7 +364,7 @@ void gauge_force_t(Ctx* c, double* out_abi, const double* lam_abi, const double*
   const int bs = 128;
   const int nb = (int)((2 * c->Vh + bs - 1) / bs);
   typedef typename V2of<T>::type V2;
-  k_force_insertion<T><<<nb, bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, (T)c->csw, W.as<V2>());
+  k_force_insertion<T><<<nb, bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, (T)c->csw, (T)c->csw_t, W.as<V2>());
   MG_LAUNCH();
   k_force_links<T><<<dim3(nb, 4), bs, 0, c->stream>>>(g, lam_e, lam_o, psi_e, psi_o, c->gauge<T>(), W.as<V2>(), kind,
                                                       (double2*)out_abi);

@@ -121,7 +121,11 @@ enum Epilogue { EPI_H = 0, EPI_CH = 1, EPI_XPAY = 2, EPI_CX_PAY = 3, EPI_C_XPAY 
 void pack_spinor(const Geom& g, const double* abi, void* even, void* odd, bool fp32, cudaStream_t s);
 void unpack_spinor(const Geom& g, const void* even, const void* odd, bool fp32, double* abi, cudaStream_t s);
 void pack_gauge(const Geom& g, const double* abi, double* g64, float* g32, cudaStream_t s);
-void build_clover(const Geom& g, const double* g64, double csw, double m0, double* A64, double* Ainv64,
+// clover coefficients of the spatial planes and of the planes that contain t
+struct CloverCoef {
+  double csw_s, csw_t;
+};
+void build_clover(const Geom& g, const double* g64, CloverCoef cf, double m0, double* A64, double* Ainv64,
                   float* A32, float* Ainv32, int* flags, cudaStream_t s);
 template <typename T>
 void clover_apply(const Geom& g, T* out, const T* in, const T* clov, cudaStream_t s);
@@ -231,6 +235,8 @@ struct Ctx {
   DBuf clov32, clovinv32;                // [2][72 Vh] floats
   bool have_gauge = false, have_clover = false;
   double csw = 0, m0 = 0;
+  double csw_t = 0;                      // clover coefficient of the planes that contain t (= csw when isotropic)
+  bool anisotropic() const { return g.w[0] != 1.0 || g.w[1] != 1.0 || g.w[2] != 1.0 || g.w[3] != 1.0 || csw_t != csw; }
 
   mg_params params{};
   bool have_params = false;

@@ -1,7 +1,9 @@
 // Fine-level Wilson-clover kernels for sm_103a.
 //
 //  * ABI <-> internal packing of spinors and gauge links
-//  * clover construction A = (4+m0) + csw (i/4) sum_{mu!=nu} sigma_{mu nu} F_{mu nu}
+//  * clover construction A = (4+m0) + csw (i/4) sum_{mu!=nu} sigma_{mu nu} F_{mu nu}; anisotropic
+//    reading: (sum_mu w_mu + m0) + (i/4) sum_{mu!=nu} c_{mu nu} sigma F with the hopping weights w_mu of the
+//    directions and c = csw_t (planes containing t) or csw_s (spatial planes)
 //    and its site inverse (FP64), the D_ee / D_oo of the paper's even-odd
 //    split ("Red-black preconditioning": D_ee, D_oo are site-diagonal)
 //  * the fused hopping kernel ("dslash") with clover / axpy epilogues, from
@@ -292,7 +294,7 @@ __device__ void pack_herm(const cd m[36], double r[36]) {
 }
 }  // namespace
 
-__global__ void k_build_clover(Geom g, const double* __restrict__ gauge, double csw, double m0, double* A64,
+__global__ void k_build_clover(Geom g, const double* __restrict__ gauge, CloverCoef cf, double m0, double* A64,
                                double* Ainv64, float* A32, float* Ainv32, int* flags) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid >= 2 * g.Vh) return;
@@ -313,8 +315,9 @@ __global__ void k_build_clover(Geom g, const double* __restrict__ gauge, double 
       cd tr = mkc((F[0].re + F[4].re + F[8].re) / 3.0, (F[0].im + F[4].im + F[8].im) / 3.0);
       F[0] = F[0] - tr; F[4] = F[4] - tr; F[8] = F[8] - tr;
       // sum over mu != nu of both orders gives 2x the mu < nu term:
-      // A += (i csw / 2) sigma_{mu nu} (x) F_{mu nu}
-      const cd pre = mkc(0.0, 0.5 * csw);
+      // A += (i c_{mu nu} / 2) sigma_{mu nu} (x) F_{mu nu}, c = csw_t for the planes
+      // that contain t, csw_s for the spatial ones (one csw when isotropic)
+      const cd pre = mkc(0.0, 0.5 * (nu == 3 ? cf.csw_t : cf.csw_s));
       for (int b = 0; b < 2; b++)
         for (int ii = 0; ii < 6; ii++)
           for (int jj = 0; jj <= ii; jj++) {
@@ -328,7 +331,7 @@ __global__ void k_build_clover(Geom g, const double* __restrict__ gauge, double 
     for (int ii = 0; ii < 6; ii++)
       for (int jj = 0; jj <= ii; jj++) {
         cd v = L[b][ii * (ii + 1) / 2 + jj];
-        if (ii == jj) v = mkc(v.re + 4.0 + m0, 0.0);
+        if (ii == jj) v = mkc(v.re + (g.w[0] + g.w[1] + g.w[2] + g.w[3]) + m0, 0.0);   // 4 + m0 when isotropic
         M[ii * 6 + jj] = v;
         M[jj * 6 + ii] = conj(v);
       }
@@ -352,11 +355,11 @@ __global__ void k_build_clover(Geom g, const double* __restrict__ gauge, double 
   }
 }
 
-void build_clover(const Geom& g, const double* g64, double csw, double m0, double* A64, double* Ainv64, float* A32,
-                  float* Ainv32, int* flags, cudaStream_t s) {
+void build_clover(const Geom& g, const double* g64, CloverCoef cf, double m0, double* A64, double* Ainv64,
+                  float* A32, float* Ainv32, int* flags, cudaStream_t s) {
   upload_sigma();
   const int n = 2 * g.Vh, bs = 64;
-  k_build_clover<<<(n + bs - 1) / bs, bs, 0, s>>>(g, g64, csw, m0, A64, Ainv64, A32, Ainv32, flags);
+  k_build_clover<<<(n + bs - 1) / bs, bs, 0, s>>>(g, g64, cf, m0, A64, Ainv64, A32, Ainv32, flags);
   MG_LAUNCH();
 }
 

@@ -68,7 +68,7 @@ __device__ __forceinline__ void hop_term(const Geom& g, const T* __restrict__ in
     load_link<T>(gauge, g.Vh, par, MU, i, u);      // U_mu(x)
   else
     load_link<T>(gauge, g.Vh, 1 - par, MU, j, u);  // U_mu(x - mu)
-  const T s = (T)sgn;
+  const T s = (T)sgn * (T)g.w[MU];   // boundary sign and the direction's hopping weight
   cx<T> h0[3], h1[3];
 #pragma unroll
   for (int col = 0; col < 3; col++) {
@@ -142,7 +142,7 @@ __device__ __forceinline__ void hop_term_nr(const Geom& g, const T* __restrict__
     load_link<T>(gauge, g.Vh, par, MU, i, u);
   else
     load_link<T>(gauge, g.Vh, 1 - par, MU, j, u);
-  const T s = (T)sgn;
+  const T s = (T)sgn * (T)g.w[MU];   // boundary sign and the direction's hopping weight
 #pragma unroll
   for (int r = 0; r < NR; r++) {
     if (r >= nr) break;

@@ -60,6 +60,11 @@ class Solver:
     def set_clover(self, csw: float, m0: float):
         B.mg_set_clover(self.ctx, csw, m0)
 
+    def set_clover_aniso(self, weights, csw_s: float, csw_t: float, m0: float):
+        """Anisotropic operator: hop weights ``(w_x, w_y, w_z, w_t)``, mass term
+        ``sum(w) + m0``, clover coefficient ``csw_t`` on the planes containing t."""
+        B.mg_set_clover_aniso(self.ctx, weights, csw_s, csw_t, m0)
+
     def set_params(self, levels=None, blocks=None, nv=None, **kw):
         p = self.params
         if levels is not None:
