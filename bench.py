@@ -361,7 +361,7 @@ def profile_main(args):
                           "true_residual": info.true_residual}))
         S.close()
     else:
-        nrhs = 1 if args.profile == "dslash" else PROFILE_MRHS
+        nrhs = 1 if args.profile == "dslash" else args.profile_nrhs
         dims = HBM_DIMS if args.profile == "dslash" else PROFILE_MRHS_DIMS
         reps = [h // d for h, d in zip(dims, DIMS)]
         H = Solver(dims)
@@ -979,6 +979,8 @@ def main():
                     help="also solve the 28 batched sources one at a time (about 30 s)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched, FP16-storage, gradient and multi-RHS D_r measurements")
+    ap.add_argument("--profile-nrhs", type=int, default=PROFILE_MRHS,
+                    help="right-hand sides per launch of --profile dslash_mrhs")
     ap.add_argument("--profile", choices=["solve", "block", "block_tc", "dslash", "dslash_mrhs", "coarse", "transfer"],
                     help="for ncu --profile-from-start off: bracket `steps` solves (after setup and warm-up), "
                          "`steps` block solves of the batched right-hand sides, or `steps` launches of the FP32 fused "

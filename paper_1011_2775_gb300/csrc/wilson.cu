@@ -561,6 +561,206 @@ void dslash_mrhs_y(const Geom& g, Epilogue epi, int parity, int nrhs, size_t str
   MG_LAUNCH();
 }
 
+// Third mapping (FP32): the CTA stages the links of its S consecutive output
+// sites -- both hops of every dimension, 8 x 9 complex per site -- and, when
+// the epilogue multiplies by a clover term, that term (18 float4 per site) in
+// shared memory once, and then runs every right-hand side over them: thread
+// (s, q) owns site s and the right-hand sides q, q + NQ, ...  Link and clover
+// bytes leave L2 once per site for all nrhs (not once per rhs group), the
+// neighbour spinors are read per rhs exactly as by the single-RHS kernel, and
+// each thread keeps the single-RHS register footprint.
+constexpr bool epi_has_clover(int epi) { return epi == EPI_CH || epi == EPI_CX_PAY || epi == EPI_C_XPAY; }
+
+template <int S>
+__device__ __forceinline__ void clover_mul_smem(const float4* sc, int s, const cx<float> x[12], cx<float> y[12]) {
+#pragma unroll
+  for (int b = 0; b < 2; b++) {
+    float r[36];
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+      const float4 v = sc[(9 * b + k) * S + s];
+      r[4 * k] = v.x;
+      r[4 * k + 1] = v.y;
+      r[4 * k + 2] = v.z;
+      r[4 * k + 3] = v.w;
+    }
+    herm6_apply<float>(r, x + 6 * b, y + 6 * b);
+  }
+}
+
+// hop D (D = 2 mu + 1 for the backward hop) of one rhs with its link from shared memory
+template <int D, int S>
+__device__ __forceinline__ void smem_hop(const Geom& g, const float* __restrict__ in, const float2* sl, int s, int j,
+                                         float sgw, cx<float> acc[12]) {
+  cx<float> psi[12];
+  SpinorIO<float>::load(in, g.Vh, j, psi);
+  cx<float> u[9];
+#pragma unroll
+  for (int e = 0; e < 9; e++) {
+    const float2 v = sl[(D * 9 + e) * S + s];
+    u[e] = mkc(v.x, v.y);
+  }
+  hop_apply<float, D / 2, (D & 1) == 0>(psi, u, sgw, acc);
+}
+
+template <int D>
+__device__ __forceinline__ int dir_bit() { return (D & 1) ? 16 << (D / 2) : 1 << (D / 2); }
+
+// Site block of the CTA launched as `b`.  Natural order (tt == 0): block b.
+// Tiled order (tt > 0, which needs S to divide the xh Ly sites of a (z, t)
+// plane -- nyb blocks per plane -- and tt to divide Lt): the lattice is cut
+// into slabs of tt time slices, taken one after the other; inside a slab the
+// blocks of a plane come first, then the next time slice, then the next z.
+// A neighbour in t is then nyb launches away and one in z nyb * tt launches
+// away, instead of a whole time slice (Vh / Lt sites) for t: with all
+// right-hand sides of a site in flight at once, the spinors of a time slice
+// no longer fit in L2 between their uses, those of a slab's window do.
+__device__ __forceinline__ int mrhs_block(const Geom& g, int b, int nyb, int tt) {
+  if (tt <= 0) return b;
+  const int yb = b % nyb;
+  int r = b / nyb;
+  const int tin = r % tt;
+  r /= tt;
+  const int z = r % g.L[2];
+  const int t = (r / g.L[2]) * tt + tin;
+  return yb + nyb * (z + g.L[2] * t);
+}
+
+template <int EPI, int S, int NQ, int MINB>
+__global__ void __launch_bounds__(S * NQ, MINB) k_dslash_mrhs_smem(Geom g, int par, int nrhs, size_t stride,
+                                                                    float* out, const float* __restrict__ in,
+                                                                    const float* __restrict__ gauge,
+                                                                    const float* __restrict__ clov,
+                                                                    const float* __restrict__ x, float a, int dirmask,
+                                                                    int nyb, int tt) {
+  extern __shared__ float4 dsm[];
+  float2* sl = reinterpret_cast<float2*>(dsm);   // [8 hops][9][S]
+  float4* sc = dsm + 36 * S;                      // [18][S], after the 72 S float2 of links
+  __shared__ int snb[8][S];                       // neighbour index of every hop of the CTA's sites
+  __shared__ float ssg[8][S];                     // boundary sign x hopping weight of every hop
+  const int s = (int)threadIdx.x % S, q = (int)threadIdx.x / S;
+  const int i = mrhs_block(g, (int)blockIdx.x, nyb, tt) * S + s;
+  const bool valid = i < g.Vh;
+  if (valid) {
+    int c[4];
+    cb_coords(g, i, par, c);
+    int nb[8];
+    float sg[8];
+    int sgn;
+#define MG_SMEM_NB(D, MU, FWD)                \
+  nb[D] = neighbour<MU, FWD>(g, c, sgn);        \
+  sg[D] = (float)sgn * (float)g.w[MU];
+    MG_SMEM_NB(0, 0, true) MG_SMEM_NB(1, 0, false) MG_SMEM_NB(2, 1, true) MG_SMEM_NB(3, 1, false)
+    MG_SMEM_NB(4, 2, true) MG_SMEM_NB(5, 2, false) MG_SMEM_NB(6, 3, true) MG_SMEM_NB(7, 3, false)
+#undef MG_SMEM_NB
+    if (q == 0) {
+#pragma unroll
+      for (int d = 0; d < 8; d++) {
+        snb[d][s] = nb[d];
+        ssg[d][s] = sg[d];
+      }
+    }
+    // links: U_mu(x) of this parity for the forward hops, U_mu(x - mu) of the
+    // other parity for the backward ones
+    const float2* gl = reinterpret_cast<const float2*>(gauge);
+#pragma unroll
+    for (int d = 0; d < 8; d++) {
+      const int bit = (d & 1) ? 16 << (d / 2) : 1 << (d / 2);
+      if (d % NQ != q || !(dirmask & bit)) continue;
+      const int site = (d & 1) ? nb[d] : i;
+      const float2* p = gl + (size_t)((((d & 1) ? 1 - par : par) * 4) + d / 2) * 9 * g.Vh;
+#pragma unroll
+      for (int e = 0; e < 9; e++) sl[(d * 9 + e) * S + s] = p[(size_t)e * g.Vh + site];
+    }
+    if (epi_has_clover(EPI)) {
+      const float4* cp = reinterpret_cast<const float4*>(clov);
+      for (int k = q; k < 18; k += NQ) sc[k * S + s] = cp[(size_t)k * g.Vh + i];
+    }
+  }
+  __syncthreads();
+  if (!valid) return;
+  const float half = -0.5f;
+  for (int r = q; r < nrhs; r += NQ) {
+    const size_t o = (size_t)r * stride;
+    const float* inr = in + o;
+    cx<float> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) acc[k] = mkc<float>(0, 0);
+    if (dirmask & dir_bit<0>()) smem_hop<0, S>(g, inr, sl, s, snb[0][s], ssg[0][s], acc);
+    if (dirmask & dir_bit<1>()) smem_hop<1, S>(g, inr, sl, s, snb[1][s], ssg[1][s], acc);
+    if (dirmask & dir_bit<2>()) smem_hop<2, S>(g, inr, sl, s, snb[2][s], ssg[2][s], acc);
+    if (dirmask & dir_bit<3>()) smem_hop<3, S>(g, inr, sl, s, snb[3][s], ssg[3][s], acc);
+    if (dirmask & dir_bit<4>()) smem_hop<4, S>(g, inr, sl, s, snb[4][s], ssg[4][s], acc);
+    if (dirmask & dir_bit<5>()) smem_hop<5, S>(g, inr, sl, s, snb[5][s], ssg[5][s], acc);
+    if (dirmask & dir_bit<6>()) smem_hop<6, S>(g, inr, sl, s, snb[6][s], ssg[6][s], acc);
+    if (dirmask & dir_bit<7>()) smem_hop<7, S>(g, inr, sl, s, snb[7][s], ssg[7][s], acc);
+    cx<float> res[12];
+    if (EPI == EPI_H) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = half * acc[k];
+    } else if (EPI == EPI_CH) {
+#pragma unroll
+      for (int k = 0; k < 12; k++) acc[k] = half * acc[k];
+      clover_mul_smem<S>(sc, s, acc, res);
+    } else if (EPI == EPI_XPAY) {
+      cx<float> xv[12];
+      SpinorIO<float>::load(x + o, g.Vh, i, xv);
+      const float f = half * a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = xv[k] + f * acc[k];
+    } else if (EPI == EPI_CX_PAY) {
+      cx<float> xv[12];
+      SpinorIO<float>::load(x + o, g.Vh, i, xv);
+      clover_mul_smem<S>(sc, s, xv, res);
+      const float f = half * a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) res[k] = res[k] + f * acc[k];
+    } else {  // EPI_C_XPAY
+      cx<float> xv[12];
+      SpinorIO<float>::load(x + o, g.Vh, i, xv);
+      const float f = half * a;
+#pragma unroll
+      for (int k = 0; k < 12; k++) xv[k] = xv[k] + f * acc[k];
+      clover_mul_smem<S>(sc, s, xv, res);
+    }
+    SpinorIO<float>::store(out + o, g.Vh, i, res);
+  }
+}
+
+template <int EPI, int S, int NQ, int MINB>
+void launch_mrhs_smem(const Geom& g, int parity, int nrhs, size_t stride, float* out, const float* in,
+                      const float* gauge, const float* clov, const float* x, double a, int dirmask, int tt,
+                      cudaStream_t s) {
+  const int plane = g.xh * g.L[1];   // sites of one (z, t) plane of a parity
+  if (plane % S != 0 || tt <= 0 || g.L[3] % tt != 0) tt = 0;   // tiled order needs whole blocks and slabs
+  const int nyb = plane / S;
+  const size_t smem = sizeof(float2) * 72 * S + (epi_has_clover(EPI) ? sizeof(float4) * 18 * S : 0);
+  auto kern = k_dslash_mrhs_smem<EPI, S, NQ, MINB>;
+  static unsigned attr_set = 0;   // devices on which this instantiation may take `smem` bytes
+  int dev = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  if (dev >= 32 || !(attr_set & (1u << dev))) {
+    MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (dev < 32) attr_set |= 1u << dev;
+  }
+  kern<<<(unsigned)((g.Vh + S - 1) / S), S * NQ, smem, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (float)a,
+                                                           dirmask, nyb, tt);
+  MG_LAUNCH();
+}
+
+template <int S, int NQ, int MINB>
+void dslash_mrhs_smem(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, float* out, const float* in,
+                      const float* gauge, const float* clov, const float* x, double a, int dirmask, int tt,
+                      cudaStream_t s) {
+  switch (epi) {
+    case EPI_H: launch_mrhs_smem<EPI_H, S, NQ, MINB>(g, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s); break;
+    case EPI_CH: launch_mrhs_smem<EPI_CH, S, NQ, MINB>(g, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s); break;
+    case EPI_XPAY: launch_mrhs_smem<EPI_XPAY, S, NQ, MINB>(g, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s); break;
+    case EPI_CX_PAY: launch_mrhs_smem<EPI_CX_PAY, S, NQ, MINB>(g, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s); break;
+    case EPI_C_XPAY: launch_mrhs_smem<EPI_C_XPAY, S, NQ, MINB>(g, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s); break;
+  }
+}
+
 template <typename T, int NR, int BS, int MINB = 1>
 void dslash_mrhs_cfg(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
                      const T* gauge, const T* clov, const T* x, double a, int dirmask, cudaStream_t s) {
@@ -578,12 +778,14 @@ void dslash_mrhs_cfg(const Geom& g, Epilogue epi, int parity, int nrhs, size_t s
 // config = NR * 1000 + CTA size (NR right-hand sides per thread; FP32: NR in
 // {2, 4}, FP64: NR in {1, 2}) [+ 10000, FP32 only: register cap for more
 // resident CTAs, __launch_bounds__ minimum of 4 (NR = 2) or 3 (NR = 4) CTAs of 128], or
-// 100000 + NY (rhs in threadIdx.y, NY in {4, 8})
+// 100000 + NY (rhs in threadIdx.y, NY in {4, 8}), or (FP32 only) 200000 +
+// 100 S + NQ [+ 10: tiled CTA order] (links staged in shared memory: S sites
+// x NQ rhs lanes per CTA; 203204, 203208, 206404, and 203214, 206414 tiled)
 template <typename T>
 void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t stride, T* out, const T* in,
                  const T* gauge, const T* clov, const T* x, double a, int dirmask, int config, cudaStream_t s) {
   if (nrhs < 1) raise(MG_ERR_ARG, "nrhs must be positive");
-  if (config >= 100000) {
+  if (config >= 100000 && config < 200000) {
     if (config % 100 == 8)
       dslash_mrhs_y<T, 8>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
     else
@@ -592,7 +794,19 @@ void dslash_mrhs(const Geom& g, Epilogue epi, int parity, int nrhs, size_t strid
   }
   constexpr bool f32 = std::is_same<T, float>::value;
   constexpr int NA = f32 ? 2 : 1, NB = f32 ? 4 : 2;
+  if (!f32 && config >= 200000) raise(MG_ERR_ARG, "the shared-memory multi-RHS dslash is FP32 only");
   if constexpr (f32) {
+    if (config >= 200000) {   // links (and clover) staged in shared memory once for all rhs
+      const int tt = (config / 10) % 10 == 1 ? 8 : 0;   // tiled CTA order, slabs of 8 time slices
+      const int base = config - 10 * ((config / 10) % 10);
+      if (base == 203208)
+        dslash_mrhs_smem<32, 8, 3>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s);
+      else if (base == 206404)
+        dslash_mrhs_smem<64, 4, 3>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s);
+      else
+        dslash_mrhs_smem<32, 4, 5>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, tt, s);
+      return;
+    }
     if (config >= 10000) {   // register-capped variants (FP32 only: FP64 would spill), CTA of 128
       if ((config - 10000) / 1000 == 4)
         dslash_mrhs_cfg<T, 4, 128, 3>(g, epi, parity, nrhs, stride, out, in, gauge, clov, x, a, dirmask, s);
@@ -620,7 +834,7 @@ template void dslash_mrhs<double>(const Geom&, Epilogue, int, int, size_t, doubl
                                   const double*, const double*, double, int, int, cudaStream_t);
 
 std::vector<int> dslash_mrhs_configs(bool fp32) {
-  return fp32 ? std::vector<int>{2064, 2128, 4064, 4128, 12128, 14128, 100004, 100008}
+  return fp32 ? std::vector<int>{2064, 2128, 4064, 4128, 12128, 14128, 100004, 100008, 203204, 203208, 206404, 203214, 206414}
               : std::vector<int>{1064, 1128, 2064, 2128, 100004, 100008};
 }
 int dslash_mrhs_default(bool fp32) { (void)fp32; return 100004; }

@@ -52,23 +52,11 @@ __device__ __forceinline__ int neighbour(const Geom& g, const int c[4], int& sgn
   return cb_index(g, n);
 }
 
-// acc += (1 -/+ gamma_mu) U psi(neighbour), without the -1/2.
-//  in:    spinor half of parity 1-par (the neighbours' parity)
-//  gauge: full internal gauge field
-//  par,i,c: parity, checkerboard index and coordinates of the output site
+// The arithmetic of one hop term: acc += (1 -/+ gamma_mu) U psi for the
+// neighbour spinor psi and the link u (U_mu(x) for FWD, U_mu(x - mu) to be
+// used daggered otherwise), s = boundary sign x hopping weight.
 template <typename T, int MU, bool FWD>
-__device__ __forceinline__ void hop_term(const Geom& g, const T* __restrict__ in, const T* __restrict__ gauge,
-                                         int par, int i, const int c[4], cx<T> acc[12]) {
-  int sgn;
-  const int j = neighbour<MU, FWD>(g, c, sgn);
-  cx<T> psi[12];
-  SpinorIO<T>::load(in, g.Vh, j, psi);
-  cx<T> u[9];
-  if (FWD)
-    load_link<T>(gauge, g.Vh, par, MU, i, u);      // U_mu(x)
-  else
-    load_link<T>(gauge, g.Vh, 1 - par, MU, j, u);  // U_mu(x - mu)
-  const T s = (T)sgn * (T)g.w[MU];   // boundary sign and the direction's hopping weight
+__device__ __forceinline__ void hop_apply(const cx<T> psi[12], const cx<T> u[9], T s, cx<T> acc[12]) {
   cx<T> h0[3], h1[3];
 #pragma unroll
   for (int col = 0; col < 3; col++) {
@@ -112,6 +100,25 @@ __device__ __forceinline__ void hop_term(const Geom& g, const T* __restrict__ in
       acc[9 + col] = acc[9 + col] + b1;
     }
   }
+}
+
+// acc += (1 -/+ gamma_mu) U psi(neighbour), without the -1/2.
+//  in:    spinor half of parity 1-par (the neighbours' parity)
+//  gauge: full internal gauge field
+//  par,i,c: parity, checkerboard index and coordinates of the output site
+template <typename T, int MU, bool FWD>
+__device__ __forceinline__ void hop_term(const Geom& g, const T* __restrict__ in, const T* __restrict__ gauge,
+                                         int par, int i, const int c[4], cx<T> acc[12]) {
+  int sgn;
+  const int j = neighbour<MU, FWD>(g, c, sgn);
+  cx<T> psi[12];
+  SpinorIO<T>::load(in, g.Vh, j, psi);
+  cx<T> u[9];
+  if (FWD)
+    load_link<T>(gauge, g.Vh, par, MU, i, u);      // U_mu(x)
+  else
+    load_link<T>(gauge, g.Vh, 1 - par, MU, j, u);  // U_mu(x - mu)
+  hop_apply<T, MU, FWD>(psi, u, (T)sgn * (T)g.w[MU], acc);   // boundary sign and the direction's hopping weight
 }
 
 // Sum of the hop terms selected by `dirmask` (bit d: d < 4 forward mu = d,

@@ -193,3 +193,55 @@ def test_solve_batch_rejects_bad_input():
         B.mg_solve_batch([S.ctx, S.ctx], [psi, psi.copy()], [eta, eta], [1, 1], 1e-10)
     assert e.value.status == B.MG_ERR_ARG
     S.close()
+
+
+_FORCED_DR_SCRIPT = r"""
+import sys
+import numpy as np
+from oracle.dirac import WilsonClover
+from paper_1011_2775_gb300 import binding as B
+from paper_1011_2775_gb300 import inputs as I
+from paper_1011_2775_gb300.solver import Solver
+dims, nrhs, w = tuple(int(v) for v in sys.argv[1].split(",")), 5, (0.45, 0.7, 1.25, 2.0)
+U = I.make_gauge(dims, 0.4, 1, 0.5, 7011)
+W = WilsonClover(U, 1.3, -0.2, weights=w, csw_t=0.6)
+x = I.gaussian_source(dims, 7012, nrhs=nrhs)
+with Solver(dims) as S:
+    S.load_gauge(U)
+    S.set_clover_aniso(w, 1.3, 0.6, -0.2)
+    got = S.apply(B.MG_OP_DR, x, prec=B.MG_FP32, nrhs=nrhs)
+worst = 0.0
+for q in range(nrhs):
+    ref = W.Dr(x[q].reshape(W.shape + (12,)) * W.even).reshape(x[q].shape)
+    worst = max(worst, float(np.abs(got[q] - ref).max() / np.abs(ref).max()))
+print(worst)
+sys.exit(0 if worst <= 1e-5 else 1)
+"""
+
+
+@pytest.mark.parametrize("config,dims", [(203204, (6, 4, 8, 10)), (203208, (6, 4, 8, 10)), (206404, (6, 4, 8, 10)),
+                                         (203214, (8, 16, 4, 16)), (206414, (8, 16, 4, 16))])
+def test_shared_memory_multi_rhs_dslash_parity(tmp_path, config, dims):
+    """The multi-RHS D_r with its two dslash launches forced (through the tuning
+    cache) onto the shared-memory kernel -- S sites x NQ rhs lanes per CTA, 5
+    right-hand sides so that the lanes hold different counts, four distinct
+    hopping weights -- against the oracle per rhs: natural CTA order with a
+    ragged last CTA on 6x4x8x10, tiled order (two slabs of 8 time slices,
+    one or two blocks per plane) on 8x16x4x16."""
+    import os
+    import subprocess
+    import sys
+    torch = pytest.importorskip("torch")
+    lib_built()
+    gpu = torch.cuda.get_device_name(0).replace(" ", "_")
+    cache = tmp_path / "tune.txt"
+    d = " ".join(map(str, dims))
+    lines = "".join(f"{k} {d} 5 1 {gpu} {config} 0\n" for k in ("dslash_ch", "dslash_xpay"))
+    cache.write_text(lines)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, MGCLOVER_TUNE_CACHE=str(cache),
+               PYTHONPATH=root + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    r = subprocess.run([sys.executable, "-c", _FORCED_DR_SCRIPT, ",".join(map(str, dims))], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert cache.read_text() == lines   # the forced entries were used: the tuner appended nothing
