@@ -213,6 +213,30 @@ def oracle_pool(jobs):
         return pool.map(oracle_worker, jobs)
 
 
+def gauge_worker(spec):
+    """One synthetic gauge field, make_gauge(dims, eps, ape_steps, alpha, seed), in a spawned process."""
+    from paper_1011_2775_gb300 import inputs as I
+    return I.make_gauge(*spec)
+
+
+def big_fields(specs) -> dict:
+    """The large synthetic gauge fields of the extra configurations, generated
+    at once in spawned processes (one field each; the same function and seeds,
+    so the same fields as one after another), keyed by their spec."""
+    import multiprocessing as mp
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    specs = list(dict.fromkeys(specs))
+    with mp.get_context("spawn").Pool(min(len(specs), host_cores())) as pool:
+        return dict(zip(specs, pool.map(gauge_worker, specs)))
+
+
+def extra_field_specs() -> list:
+    """Specs (dims, eps, ape_steps, alpha, seed) of the fields run_multi and run_config3 use."""
+    return ([(dims, EPS, APE, ALPHA, 4001 + 10 * k) for k, (dims, _, _) in enumerate(MULTI)] +
+            [(CONFIG3_DIMS, eps, APE, ALPHA, 3001) for eps in (EPS, ROUGH_EPS)])
+
+
 def host_cores(limit: int = 0) -> int:
     n = max(1, min(CPU_MAX_PROCS, os.cpu_count() or 1))
     return min(n, limit) if limit > 0 else n
@@ -842,7 +866,7 @@ CONFIG3_MG = dict(levels=3, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], nv=[24, 32])
 ROUGH_EPS, ROUGH_M0 = 1.0, -0.7
 
 
-def run_config3(dev: int) -> dict:
+def run_config3(dev: int, pre: dict | None = None) -> dict:
     """The 24^3x64 configuration: the 3-level solve with BF16 storage of P and
     the coarse links, the 2-level solve with BF16 and with FP32 storage, and
     the FP32 dslash on this lattice (467 MB per launch, beyond L2)."""
@@ -852,7 +876,13 @@ def run_config3(dev: int) -> dict:
     from paper_1011_2775_gb300.solver import Solver
 
     stream = torch.cuda.current_stream(dev)
-    fields = {EPS: I.make_gauge(CONFIG3_DIMS, EPS, APE, ALPHA, 3001)}
+    pre = pre or {}
+
+    def field(eps):
+        spec = (CONFIG3_DIMS, eps, APE, ALPHA, 3001)
+        return pre[spec] if spec in pre else I.make_gauge(*spec)
+
+    fields = {EPS: field(EPS)}
     eta = torch.from_numpy(I.gaussian_source(CONFIG3_DIMS, 3002)).to(f"cuda:{dev}")
     psi = torch.zeros_like(eta)
     out = {"lattice": "24^3x64", "m0": -0.35, "mg": "3-level: 4^4 (Nv=24) then 2^4 (Nv=32), coarsest 3^3x8",
@@ -864,7 +894,7 @@ def run_config3(dev: int) -> dict:
             ("rough_two_level_fp32", B.MG_STORE_FP32, MG, ROUGH_EPS, ROUGH_M0))
     for name, store, mg, eps, m0 in runs:
         if eps not in fields:
-            fields[eps] = I.make_gauge(CONFIG3_DIMS, eps, APE, ALPHA, 3001)
+            fields[eps] = field(eps)
         U = fields[eps]
         S = Solver(CONFIG3_DIMS, device=dev, stream=stream.cuda_stream)
         S.load_gauge(U)
@@ -894,7 +924,7 @@ def run_config3(dev: int) -> dict:
     return out
 
 
-def run_multi(dev: int, sequential: bool = False) -> dict:
+def run_multi(dev: int, sequential: bool = False, pre: dict | None = None) -> dict:
     """All 28 right-hand sides through mg_solve_batch (lock-step, shared coarsest
     launches) against each lattice's own block solve and against 28 solves one
     after another; every time is CUDA events on the one stream all contexts use."""
@@ -907,7 +937,8 @@ def run_multi(dev: int, sequential: bool = False) -> dict:
     stream = torch.cuda.current_stream(dev)
     solvers, etas, outs, setup_ms = [], [], [], []
     for k, (dims, kind, nrhs) in enumerate(MULTI):
-        U = I.make_gauge(dims, EPS, APE, ALPHA, 4001 + 10 * k)
+        spec = (dims, EPS, APE, ALPHA, 4001 + 10 * k)
+        U = pre.pop(spec) if pre and spec in pre else I.make_gauge(*spec)
         S = Solver(dims, device=dev, stream=stream.cuda_stream)
         S.load_gauge(U)
         del U
@@ -956,6 +987,27 @@ def run_multi(dev: int, sequential: bool = False) -> dict:
     for S in solvers:
         S.close()
     return out
+
+
+def run_extra_configs(args, dist, r: dict) -> None:
+    """The multi-lattice batch and the 24^3x64 configuration, at N = 1 only
+    (they are no part of the step), their gauge fields generated in parallel
+    first; results go to r["extra"]."""
+    do_multi, do_config3 = dist.world == 1 and not args.no_multi, dist.world == 1 and not args.no_config3
+    pre = {}
+    if do_multi or do_config3:
+        t_f = time.perf_counter()
+        pre = big_fields([sp for sp in extra_field_specs()
+                          if (do_multi and sp[0] != CONFIG3_DIMS) or (do_config3 and sp[0] == CONFIG3_DIMS)])
+        SECTIONS["extra_fields"] = time.perf_counter() - t_f
+    if do_multi:
+        t_m = time.perf_counter()
+        r["extra"]["multi_lattice"] = run_multi(dist.local, args.multi_sequential, pre)
+        SECTIONS["multi_lattice"] = time.perf_counter() - t_m
+    if do_config3:
+        t_c = time.perf_counter()
+        r["extra"]["config3_24x64"] = run_config3(dist.local, pre)
+        SECTIONS["config3"] = time.perf_counter() - t_c
 
 
 def main():
@@ -1025,14 +1077,7 @@ def main():
         return
 
     r = run_gpu(args, dist)
-    if not args.no_multi:
-        t_m = time.perf_counter()
-        r["extra"]["multi_lattice"] = run_multi(dist.local, args.multi_sequential)
-        SECTIONS["multi_lattice"] = time.perf_counter() - t_m
-    if not args.no_config3:
-        t_c = time.perf_counter()
-        r["extra"]["config3_24x64"] = run_config3(dist.local)
-        SECTIONS["config3"] = time.perf_counter() - t_c
+    run_extra_configs(args, dist, r)
     info = r["info"]
     dr_per_solve = info.dslash_launches / 2.0
     c = r["coarse"]
