@@ -213,22 +213,53 @@ def oracle_pool(jobs):
         return pool.map(oracle_worker, jobs)
 
 
-def gauge_worker(spec):
-    """One synthetic gauge field, make_gauge(dims, eps, ape_steps, alpha, seed), in a spawned process."""
+def links_worker(job):
+    """exp(i eps H) on one block of time slices (site-local), in a spawned process."""
     from paper_1011_2775_gb300 import inputs as I
-    return I.make_gauge(*spec)
+    h, eps = job
+    return I.links_from_normals(h, eps)
 
 
-def big_fields(specs) -> dict:
-    """The large synthetic gauge fields of the extra configurations, generated
-    at once in spawned processes (one field each; the same function and seeds,
-    so the same fields as one after another), keyed by their spec."""
+def ape_worker(job):
+    """One APE step on a block of time slices carrying one halo slice on each
+    side; returns the block's own slices."""
+    from paper_1011_2775_gb300 import inputs as I
+    u, alpha = job
+    return I.ape_step(u, alpha)[1:-1]
+
+
+def parallel_gauge(pool, nproc: int, spec) -> "np.ndarray":
+    """make_gauge(*spec) with the site-local link construction and every APE
+    step split into blocks of time slices over the pool's processes: the same
+    operations on the same numbers, so the same field."""
+    import numpy as np
+    from paper_1011_2775_gb300 import inputs as I
+    dims, eps, ape_steps, alpha, seed = spec
+    lt = dims[3]
+    cuts = np.linspace(0, lt, min(nproc, lt) + 1).astype(int)
+    blocks = [(a, b) for a, b in zip(cuts[:-1], cuts[1:]) if b > a]
+    h = I.gauge_normals(dims, seed)
+    u = np.concatenate(pool.map(links_worker, [(h[a:b], eps) for a, b in blocks]), axis=0)
+    del h
+    for _ in range(int(ape_steps)):
+        jobs = [(np.take(u, np.arange(a - 1, b + 1), axis=0, mode="wrap"), alpha) for a, b in blocks]
+        u = np.concatenate(pool.map(ape_worker, jobs), axis=0)
+    return np.ascontiguousarray(u)
+
+
+def big_fields(specs, nproc: int = 0) -> dict:
+    """The large synthetic gauge fields of the extra configurations, each built
+    by parallel_gauge over spawned processes (the fields make_gauge gives),
+    keyed by their spec."""
     import multiprocessing as mp
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         os.environ[v] = "1"
-    specs = list(dict.fromkeys(specs))
-    with mp.get_context("spawn").Pool(min(len(specs), host_cores())) as pool:
-        return dict(zip(specs, pool.map(gauge_worker, specs)))
+    n = nproc or host_cores()
+    out = {}
+    with mp.get_context("spawn").Pool(n) as pool:
+        for sp in dict.fromkeys(specs):
+            out[sp] = parallel_gauge(pool, n, sp)
+    return out
 
 
 def extra_field_specs() -> list:

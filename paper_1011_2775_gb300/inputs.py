@@ -89,35 +89,52 @@ def unit_gauge(dims) -> np.ndarray:
     return u
 
 
-def random_gauge(dims, eps: float, seed: int) -> np.ndarray:
-    """``U = exp(i eps H)``, ``H = sum_a h_a lambda_a/2``, by eigendecomposition of ``H``."""
+def gauge_normals(dims, seed: int) -> np.ndarray:
+    """The Gaussian coefficients ``h[t][z][y][x][mu][a]`` of ``random_gauge``."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    shp = lattice_shape(dims)
-    h = rng.standard_normal(shp + (4, 8))
+    return rng.standard_normal(lattice_shape(dims) + (4, 8))
+
+
+def links_from_normals(h: np.ndarray, eps: float) -> np.ndarray:
+    """``exp(i eps H)`` with ``H = sum_a h_a lambda_a/2`` per link (site-local,
+    so any block of sites can be done on its own)."""
     H = np.einsum("...a,aij->...ij", h, gell_mann() / 2.0)
     e, q = np.linalg.eigh(H)
     u = (q * np.exp(1j * eps * e)[..., None, :]) @ _dag(q)
     return _project_su3(u)
 
 
+def random_gauge(dims, eps: float, seed: int) -> np.ndarray:
+    """``U = exp(i eps H)``, ``H = sum_a h_a lambda_a/2``, by eigendecomposition of ``H``."""
+    return links_from_normals(gauge_normals(dims, seed), eps)
+
+
+def ape_step(u: np.ndarray, alpha: float) -> np.ndarray:
+    """One 4D APE step with all six staples per link, periodic on the array's
+    own site axes.  A site's new links read only sites one step away, so for a
+    block of time slices with one slice of halo on each side the interior
+    slices of the result are those of the step on the whole lattice."""
+    new = np.empty_like(u)
+    for mu in range(4):
+        umu = u[..., mu, :, :]
+        staple = np.zeros_like(umu)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            unu = u[..., nu, :, :]
+            # upper: U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+            staple += unu @ _shift(umu, nu, +1) @ _dag(_shift(unu, mu, +1))
+            # lower: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+            unu_m = _shift(unu, nu, -1)
+            staple += _dag(unu_m) @ _shift(umu, nu, -1) @ _shift(unu_m, mu, +1)
+        new[..., mu, :, :] = _project_su3((1.0 - alpha) * umu + (alpha / 6.0) * staple)
+    return new
+
+
 def ape_smear(u: np.ndarray, steps: int, alpha: float) -> np.ndarray:
     """4D APE smearing with all six staples per link, ``steps`` times."""
     for _ in range(int(steps)):
-        new = np.empty_like(u)
-        for mu in range(4):
-            umu = u[..., mu, :, :]
-            staple = np.zeros_like(umu)
-            for nu in range(4):
-                if nu == mu:
-                    continue
-                unu = u[..., nu, :, :]
-                # upper: U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
-                staple += unu @ _shift(umu, nu, +1) @ _dag(_shift(unu, mu, +1))
-                # lower: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
-                unu_m = _shift(unu, nu, -1)
-                staple += _dag(unu_m) @ _shift(umu, nu, -1) @ _shift(unu_m, mu, +1)
-            new[..., mu, :, :] = _project_su3((1.0 - alpha) * umu + (alpha / 6.0) * staple)
-        u = new
+        u = ape_step(u, alpha)
     return u
 
 

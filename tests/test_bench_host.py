@@ -13,13 +13,16 @@ from paper_1011_2775_gb300 import inputs as I  # noqa: E402
 
 
 def test_big_fields_equal_the_serial_fields():
-    """The parallel generation in spawned processes gives bitwise the fields of
-    make_gauge called one after another, keyed by their spec."""
-    specs = [((4, 4, 4, 4), 0.25, 1, 0.5, 3), ((4, 4, 4, 8), 1.0, 2, 0.5, 5), ((4, 4, 4, 4), 0.25, 1, 0.5, 3)]
-    got = bench.big_fields(specs)
-    assert len(got) == 2
-    for sp in specs:
-        assert np.array_equal(got[sp], I.make_gauge(*sp))
+    """The generation split into blocks of time slices over spawned processes
+    (uneven blocks, blocks of one slice, more processes than slices) gives
+    bitwise the fields of make_gauge, keyed by their spec."""
+    specs = [((4, 4, 4, 4), 0.25, 1, 0.5, 3), ((4, 2, 4, 10), 1.0, 3, 0.5, 5), ((4, 4, 4, 4), 0.25, 1, 0.5, 3),
+             ((2, 4, 2, 6), 0.4, 0, 0.5, 9)]
+    for nproc in (3, 4, 16):
+        got = bench.big_fields(specs, nproc)
+        assert len(got) == 3
+        for sp in specs:
+            assert np.array_equal(got[sp], I.make_gauge(*sp)), (nproc, sp)
 
 
 def test_extra_field_specs_cover_the_extra_configurations():
