@@ -375,7 +375,8 @@ MG_API int mg_solve_dagger(void* ctx, void* psi, const void* eta, int nrhs, doub
  * derivative of L = Re <chi, D^{-1} eta> with respect to the gauge field --
  * an extension: the paper does not differentiate the solve.  Both the hopping
  * term and the clover term (through its plaquette leaves, with the csw of the
- * last mg_set_clover) are differentiated, in FP64 -- or in FP32 when `kind`
+ * last mg_set_clover, or the hopping weights and per-plane coefficients of
+ * the last mg_set_clover_aniso) are differentiated, in FP64 -- or in FP32 when `kind`
  * carries the MG_FORCE_FP32 flag (FP32 gauge copy, vectors and arithmetic).
  *   MG_FORCE_SU3:       F_mu(x) = sum_a F^a T_a with F^a = df/d omega^a for
  *                       U_mu(x) -> exp(i omega^a T_a) U_mu(x), T_a = lambda_a/2;
