@@ -205,7 +205,7 @@ MG_API const char* mg_last_error(void);
  * GCR iterations, RQ tolerance 0.05, nu_post = 4, coarse tolerance 0.1,
  * coarse restart 32 / cap 50, outer restart 16 / cap 500, FP32 storage,
  * Galerkin projection of D_p, seed 3, rhs_block 16, cuda_graphs 1, coarse_impl 0,
- * outer_prec MG_FP32, level_timing 0. */
+ * outer_prec MG_FP32, level_timing 0.  Errors: MG_ERR_ARG (p NULL). */
 MG_API int mg_default_params(mg_params* p);
 
 /* Create a context for a lattice of `dims` on CUDA device `device`; kernels
@@ -213,11 +213,14 @@ MG_API int mg_default_params(mg_params* p);
  * Errors: MG_ERR_ARG, MG_ERR_DIMS (an extent is odd or < 2), MG_ERR_CUDA. */
 MG_API int mg_create(void** ctx_out, const int dims[4], int device, void* cuda_stream);
 
-/* Release the context and all device memory it owns.  NULL is a no-op. */
+/* Release the context and all device memory it owns.  NULL is a no-op.
+ * Errors: MG_ERR_CUDA (a failed release; the context is gone either way). */
 MG_API int mg_destroy(void* ctx);
 
-/* Copy in the gauge field (layout above).  Invalidates the clover field and
- * any multigrid setup. */
+/* Copy in the gauge field (layout above; host or device memory as `where`
+ * says, read once, not kept).  Invalidates the clover field and any multigrid
+ * setup.  Errors: MG_ERR_ARG (NULL context or field, bad `where`),
+ * MG_ERR_CUDA. */
 MG_API int mg_load_gauge(void* ctx, const void* U, int where);
 
 /* Set the clover coefficient csw and the bare mass m0 and build A and A^{-1}
@@ -265,7 +268,11 @@ MG_API int mg_setup(void* ctx, mg_setup_info* info);
 /* Inject (set) or read (get) the nv raw null vectors of transfer `level`:
  * complex128 [k][level-l lattice vector layout].  Injected vectors replace
  * the inverse iteration of that level at the next mg_setup (used by tests
- * and to reuse a setup).  get returns the vectors of the last setup. */
+ * and to reuse a setup).  get returns the vectors of the last setup.  `V`
+ * is host or device memory as `where` says, copied.  Errors: MG_ERR_ARG (V
+ * NULL, bad `where`, `level` not a transfer: 0 <= level < levels - 1),
+ * MG_ERR_NV (nv is not nv[level] of the parameters), MG_ERR_STATE (get: no
+ * setup yet), MG_ERR_CUDA. */
 MG_API int mg_set_null_vectors(void* ctx, int level, const void* V, int nv, int where);
 MG_API int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where);
 
@@ -494,7 +501,9 @@ MG_API int mg_benchmark_coarse_floor(void* ctx, double* barrier_us, double* stre
                                      int* grid);
 
 /* Lattice size of level `level` after setup (dims_out[4] = {Lx,Ly,Lz,Lt})
- * and its dof per site (12 on the fine level, 2*nv[level-1] on coarse ones). */
+ * and its dof per site (12 on the fine level, 2*nv[level-1] on coarse ones).
+ * Computed from the parameters, so it also answers before mg_setup.
+ * Errors: MG_ERR_ARG (NULL outputs, level outside 0 .. levels - 1). */
 MG_API int mg_level_info(void* ctx, int level, int dims_out[4], int* ndof_out);
 
 #ifdef __cplusplus

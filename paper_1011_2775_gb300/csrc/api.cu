@@ -399,7 +399,9 @@ int mg_get_null_vectors(void* ctx, int level, void* V, int nv, int where) {
     mg::Ctx* c = as_ctx(ctx);
     check_where(where);
     if (!V) mg::raise(MG_ERR_ARG, "null vectors");
+    if (level < 0 || level + 1 >= c->params.levels) mg::raise(MG_ERR_ARG, "no transfer from this level");
     if (!c->mg) mg::raise(MG_ERR_STATE, "run mg_setup first");
+    if (nv != c->params.nv[level]) mg::raise(MG_ERR_NV, "nv does not match the setup");
     const size_t bytes = sizeof(double) * 2 * level_vec_complex(c, level, nullptr) * nv;
     Staged st;
     stage_out_alloc(st, V, bytes, where);

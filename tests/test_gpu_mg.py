@@ -296,6 +296,12 @@ def test_error_paths():
         S.set_params(levels=2, blocks=[(1, 1, 1, 2)], nv=[13])  # a block's chiral subspace has dim 12
     assert e.value.status == B.MG_ERR_NV
     S.set_params(levels=2, blocks=[(2, 2, 2, 2)], nv=[4])
+    buf = np.zeros((4, 4, 4, 4, 4, 12), dtype=np.complex128)
+    for lvl in (-1, 1):                    # no transfer from these levels
+        for call in (B.mg_get_null_vectors, B.mg_set_null_vectors):
+            with pytest.raises(B.MGError) as e:
+                call(S.ctx, lvl, buf, 4)
+            assert e.value.status == B.MG_ERR_ARG
     V = np.stack([gaussian_vector(3, 0, k, (4, 4, 4, 4), 12) for k in range(4)])
     V[3] = 2.0 * V[1] - 0.5 * V[0]        # locally dependent (to FP32 rounding)
     S.set_null_vectors(0, np.ascontiguousarray(V))
