@@ -15,6 +15,7 @@
 // One thread per lattice site; spinors, links and clover are read as
 // 16-byte (float4 / double2) or 8-byte chunks in structure-of-chunks order so
 // that a warp reads contiguous 512-byte spans.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <type_traits>
@@ -736,12 +737,12 @@ void launch_mrhs_smem(const Geom& g, int parity, int nrhs, size_t stride, float*
   const int nyb = plane / S;
   const size_t smem = sizeof(float2) * 72 * S + (epi_has_clover(EPI) ? sizeof(float4) * 18 * S : 0);
   auto kern = k_dslash_mrhs_smem<EPI, S, NQ, MINB>;
-  static unsigned attr_set = 0;   // devices on which this instantiation may take `smem` bytes
+  static std::atomic<unsigned> attr_set{0u};   // devices on which this instantiation may take `smem` bytes
   int dev = 0;
   MG_CUDA(cudaGetDevice(&dev));
-  if (dev >= 32 || !(attr_set & (1u << dev))) {
+  if (dev >= 32 || !(attr_set.load() & (1u << dev))) {
     MG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (dev < 32) attr_set |= 1u << dev;
+    if (dev < 32) attr_set.fetch_or(1u << dev);
   }
   kern<<<(unsigned)((g.Vh + S - 1) / S), S * NQ, smem, s>>>(g, parity, nrhs, stride, out, in, gauge, clov, x, (float)a,
                                                            dirmask, nyb, tt);
