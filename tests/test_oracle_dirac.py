@@ -290,3 +290,20 @@ def test_anisotropic_clover_constant_abelian_field(plane):
     sig = 0.5j * (GT[mu] @ GT[nu] - GT[nu] @ GT[mu])
     expect = (sum(AW) + m0) * np.eye(12) - 0.5 * c * np.sin(B) * np.kron(sig, np.diag([1.0, -1.0, 0.0]))
     assert np.abs(W.A - expect).max() < 1e-14
+
+
+def test_uniform_weights_scale_the_isotropic_operator():
+    """With every weight equal to w and csw_t = csw the reading is w times the
+    isotropic operator of coefficient csw / w and mass m0 / w (the mass term
+    4 w + m0 and the clover term, linear in its coefficient, both scale): this
+    ties the weights of the hops, of the mass term and of the clover
+    coefficient to one another on a rough field."""
+    dims = (4, 4, 2, 6)
+    U = I.make_gauge(dims, 0.6, 1, 0.5, 57)
+    w, csw, m0 = 1.7, 1.2, -0.3
+    Wa = WilsonClover(U, csw, m0, weights=(w, w, w, w), csw_t=csw)
+    Wi = WilsonClover(U, csw / w, m0 / w)
+    psi = _vec(dims, 58)
+    ref = w * Wi.D(psi)
+    assert np.abs(Wa.D(psi) - ref).max() < 1e-13 * np.abs(ref).max()
+    assert np.abs(Wa.A - w * Wi.A).max() < 1e-13 * np.abs(Wa.A).max()
